@@ -1,0 +1,257 @@
+/*
+ * escher.h -- C ABI of the GB300 dynamic-hypergraph triad-count engine.
+ *
+ * The engine keeps hypergraphs resident on one GPU as a two-way incidence
+ * store (hyperedge -> vertices, "h2v", and vertex -> hyperedges, "v2h"; paper
+ * Section III, "Enabling Multiple Formats" and Table II), applies batches of
+ * hyperedge insertions and deletions to it (Section III-B, vertical
+ * operations), and after every batch refreshes three families of exact triad
+ * counts incrementally from the hyperedges the batch touched (Algorithm 3):
+ *
+ *   ESC_TRIAD_HYPEREDGE  30 uint64: hyperedge triads by Venn pattern class
+ *                        (Section II; the 26 classes of MoCHy, plus 4
+ *                        classes that only arise when two hyperedges hold the
+ *                        same vertex set).
+ *   ESC_TRIAD_VERTEX     3 uint64: incident-vertex triads of types 1, 2, 3
+ *                        (Section II): a vertex triple plus one witnessing
+ *                        hyperedge per vertex pair, typed by the number of
+ *                        distinct witnesses.
+ *   ESC_TRIAD_TEMPORAL   96 uint64: temporal triads (Section II) -- three
+ *                        connected hyperedges ordered by timestamp, equal
+ *                        timestamps ordered by hyperedge ID, with
+ *                        t_last - t_first <= delta -- by ordered pattern.
+ *
+ * Class numbering.  Venn region bits of an ordered triple (a,b,c): 0 a only,
+ * 1 b only, 2 c only, 3 a&b not c, 4 b&c not a, 5 a&c not b, 6 a&b&c.  A
+ * hyperedge class is the orbit of the 7-bit pattern under relabelling;
+ * classes 0..25 are the orbits without two identical hyperedges ranked by
+ * their smallest pattern, 26..29 the orbits with two identical hyperedges
+ * ranked the same way.  A temporal class is the rank of the ordered pattern
+ * (earliest hyperedge as a) among the 96 valid patterns.
+ *
+ * All counts are uint64 and wrap modulo 2^64.
+ *
+ * IDs.  Initial hyperedges get IDs 0..n-1 in input order.  In every batch the
+ * deletions apply first; then the j-th inserted hyperedge (input order) takes
+ * the j-th smallest free ID -- an ID below the high-water mark holding no
+ * live hyperedge, including IDs freed by this batch -- and, once those run
+ * out, fresh IDs upward from the high-water mark (Section III-B, insertion
+ * Case 1 and Algorithm 2: a new hyperedge reuses a freed hyperedge's ID).
+ * Vertex IDs lie in [0, n_vertices).  A hyperedge is a vertex set: repeated
+ * members of an inserted hyperedge collapse to one (Section II).
+ *
+ * Pointers.  Every array argument may be a host pointer or a device pointer
+ * of the graph's device; the library tells them apart itself.  Inputs are
+ * borrowed for the duration of the call only.  Output arrays belong to the
+ * caller.  A graph (or group) owns all the device memory it allocates until
+ * it is destroyed.
+ *
+ * Errors.  Functions return an esc_status and never throw.  Every batch is
+ * validated in full on the device before anything is changed: a failed
+ * esc_apply_batch / esc_group_apply leaves the store and all counts as they
+ * were.  esc_last_error() gives a one-line reason for the last failure.
+ *
+ * Threads.  A graph or group may be used by one host thread at a time.
+ */
+#ifndef ESCHER_H
+#define ESCHER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ESC_OK = 0,
+    ESC_ERR_INVALID_ARG = 1,   /* malformed input: bad sizes, vertex out of
+                                  range, empty hyperedge, duplicate delete  */
+    ESC_ERR_NOT_FOUND = 2,     /* delete of an ID that holds no live hyperedge */
+    ESC_ERR_OUT_OF_MEMORY = 3, /* a preallocated capacity would be exceeded  */
+    ESC_ERR_UNSUPPORTED = 4,   /* a size beyond a documented engine limit, a
+                                  family not maintained, another window   */
+    ESC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out              */
+    ESC_ERR_CUDA = 6           /* a CUDA runtime call failed                 */
+} esc_status;
+
+typedef enum {
+    ESC_TRIAD_HYPEREDGE = 0,
+    ESC_TRIAD_VERTEX = 1,
+    ESC_TRIAD_TEMPORAL = 2
+} esc_triad_type;
+
+#define ESC_FAMILY_HYPEREDGE 1u
+#define ESC_FAMILY_VERTEX 2u
+#define ESC_FAMILY_TEMPORAL 4u
+
+#define ESC_N_HYPEREDGE_CLASSES 30
+#define ESC_N_VERTEX_TYPES 3
+#define ESC_N_TEMPORAL_CLASSES 96
+
+/* Largest hyperedge cardinality the engine accepts (after duplicate members
+ * are removed). */
+#define ESC_MAX_CARDINALITY 16384
+
+/* Capacities are preallocated once (paper Section IV: GPU memory is
+ * preallocated with a tunable amount of slack so that updates need no
+ * host-device round trips). */
+typedef struct {
+    int32_t n_vertices;             /* vertex universe [0, n_vertices)             */
+    int64_t capacity_hyperedges;    /* IDs available: [0, capacity_hyperedges)     */
+    int64_t capacity_incidences;    /* live (hyperedge, vertex) pairs, at most     */
+    int64_t max_batch_hyperedges;   /* n_ins + n_del of one call, at most          */
+    int64_t max_batch_incidences;   /* inserted members of one call, at most       */
+    uint32_t families;              /* ESC_FAMILY_* bits of the families to keep   */
+    int64_t delta;                  /* temporal window (timestamp units)           */
+    int32_t debug;                  /* 0; reserved                                  */
+} esc_config;
+
+typedef struct esc_graph esc_graph;
+typedef struct esc_group esc_group;
+
+/* Create a graph on the current CUDA device from an initial hypergraph of
+ * n_he hyperedges in CSR form: the members of hyperedge i are
+ * members[offsets[i] .. offsets[i+1]), offsets[0] == 0 (offsets int64[n_he+1],
+ * members int32[offsets[n_he]], any order, repeats allowed).  timestamps is
+ * int64[n_he] and required when ESC_FAMILY_TEMPORAL is kept, otherwise it
+ * may be NULL.  All device work runs on cuda_stream (a cudaStream_t; NULL
+ * for the legacy default stream).  The initial counts are computed on the
+ * device by the same incremental kernels (every initial hyperedge counts as
+ * inserted).  Paper Section III-B, "Hypergraph initialization".
+ * Errors: INVALID_ARG (config or input malformed), OUT_OF_MEMORY (device
+ * allocation or capacity), UNSUPPORTED (cardinality above
+ * ESC_MAX_CARDINALITY), CUDA. */
+esc_status esc_create(const esc_config* cfg, int64_t n_he, const int64_t* offsets,
+                      const int32_t* members, const int64_t* timestamps, void* cuda_stream,
+                      esc_graph** out);
+
+/* Apply one batch: delete n_del hyperedges (del_ids int32[n_del], distinct,
+ * live) and insert n_ins hyperedges (CSR as in esc_create; ins_timestamps
+ * int64[n_ins], required when the temporal family is kept), then refresh
+ * every kept count (Algorithm 3: counts of triads holding a deleted
+ * hyperedge are removed on the old graph, counts of triads holding an
+ * inserted hyperedge are added on the new graph).  If out_ins_ids is not
+ * NULL it receives the n_ins assigned IDs (int32, input order).  The call
+ * returns once the store and counts are updated.  Either count may be 0.
+ * Errors: INVALID_ARG, NOT_FOUND, OUT_OF_MEMORY, UNSUPPORTED, CUDA; on any
+ * error the graph is unchanged. */
+esc_status esc_apply_batch(esc_graph* g, int64_t n_ins, const int64_t* ins_offsets,
+                           const int32_t* ins_members, const int64_t* ins_timestamps,
+                           int64_t n_del, const int32_t* del_ids, int32_t* out_ins_ids);
+
+/* Copy the current counts of one family into out (uint64[n_out]; n_out must be
+ * at least 30, 3 or 96).  window is the temporal window and must equal the
+ * configured delta for ESC_TRIAD_TEMPORAL; it is ignored otherwise.
+ * Errors: INVALID_ARG (n_out too small, bad type), UNSUPPORTED (family not
+ * kept, other window). */
+esc_status esc_triads(esc_graph* g, esc_triad_type type, int64_t window, uint64_t* out,
+                      int32_t n_out);
+
+/* Counts of the triads of the current graph that hold at least one of the
+ * given live hyperedges (ids int32[n_ids], distinct), for every kept family;
+ * out_hyperedge uint64[30], out_vertex uint64[3], out_temporal uint64[96]
+ * (each may be NULL).  The type-1 and type-2 vertex counts attribute vertex
+ * triples to the hyperedges and hyperedge pairs that witness them.  Passing
+ * every live ID recounts the whole graph from scratch.  The graph is not
+ * changed.  This is the counting step of Algorithm 3 on its own.
+ * Errors: INVALID_ARG, NOT_FOUND, UNSUPPORTED, CUDA. */
+esc_status esc_local_triads(esc_graph* g, int64_t n_ids, const int32_t* ids,
+                            uint64_t* out_hyperedge, uint64_t* out_vertex,
+                            uint64_t* out_temporal);
+
+/* Release every resource of the graph.  NULL is accepted. */
+esc_status esc_destroy(esc_graph* g);
+
+/* One-line description of the last failure on this graph (or of the last
+ * failed esc_create on this thread when g is NULL).  Owned by the library. */
+const char* esc_last_error(const esc_graph* g);
+
+/* Sizes needed by esc_export. */
+esc_status esc_export_sizes(esc_graph* g, int64_t* n_live, int64_t* n_incidences);
+
+/* Copy the incidence store to host arrays: for the n_live live hyperedges in
+ * ascending ID order, ids int32[n_live], timestamps int64[n_live] (may be
+ * NULL), offsets int64[n_live+1] and sorted members int32[n_incidences]; and,
+ * for every vertex, v_offsets int64[n_vertices+1] and v_members
+ * int32[n_incidences] holding the IDs of the hyperedges that contain it, in
+ * ascending order.  Any pointer may be NULL to skip that part.  Meant for
+ * tests and checkpoints (Table II: the h2v and v2h views). */
+esc_status esc_export(esc_graph* g, int32_t* ids, int64_t* timestamps, int64_t* offsets,
+                      int32_t* members, int64_t* v_offsets, int32_t* v_members);
+
+/* Per-batch measurements of the last esc_apply_batch, filled when
+ * esc_set_profiling(g, 1) is on.  Stage times are device times measured with
+ * CUDA events on the graph's stream (the time split of the paper's Fig. 11b:
+ * data-structure management versus count update). */
+typedef struct {
+    float ms_total;          /* whole batch                                   */
+    float ms_ingest;         /* gather, sort/dedup, validation                 */
+    float ms_count_del;      /* counting on the old graph (deleted side)       */
+    float ms_store;          /* store update (delete + insert)                 */
+    float ms_count_ins;      /* counting on the new graph (inserted side)      */
+    int64_t launches;        /* kernels launched by the call                   */
+    int64_t count_launches;  /* triad-count kernel launches                    */
+    int64_t v2h_reads;       /* vertex->hyperedge entries read by the counter  */
+    int64_t h2v_reads;       /* hyperedge->vertex entries read by the counter  */
+    int64_t meta_reads;      /* per-neighbour metadata lookups by the counter  */
+    int64_t triads;          /* triads classified by the counter               */
+} esc_batch_stats;
+
+esc_status esc_set_profiling(esc_graph* g, int32_t on);
+esc_status esc_last_stats(esc_graph* g, esc_batch_stats* out);
+
+/* Total kernel launches of this graph so far (a monotone counter). */
+int64_t esc_launch_count(const esc_graph* g);
+
+/* ------------------------------------------------------------------------
+ * Groups: many independent hypergraphs behind one store, updated together.
+ *
+ * A group holds n_graphs hypergraphs with the same families and delta.  One
+ * esc_group_apply call takes update batches for any subset of them and runs
+ * the whole pipeline -- validation, store update, triad counting -- for all
+ * of them in the same kernel launches, the counting work of every graph
+ * balanced across the GPU together.  Triads never span two graphs.  Each
+ * graph has its own ID space, vertex universe, high-water mark and counts,
+ * exactly as if it were an esc_graph of its own.  Batches are all-or-nothing
+ * per call: if any batch is invalid, no graph changes.
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t graph;                  /* which graph of the group                    */
+    int64_t n_ins;
+    const int64_t* ins_offsets;     /* int64[n_ins+1], offsets[0] == 0            */
+    const int32_t* ins_members;
+    const int64_t* ins_timestamps;  /* int64[n_ins] or NULL when not temporal     */
+    int64_t n_del;
+    const int32_t* del_ids;         /* int32[n_del], this graph's IDs             */
+    int32_t* out_ins_ids;           /* int32[n_ins] or NULL                       */
+} esc_batch;
+
+/* Create a group of empty graphs; graph_cfg[i] gives graph i's n_vertices,
+ * capacity_hyperedges and capacity_incidences; families, delta and the
+ * per-call batch limits come from shared_cfg.  Errors: INVALID_ARG,
+ * OUT_OF_MEMORY, CUDA. */
+esc_status esc_group_create(const esc_config* shared_cfg, int32_t n_graphs,
+                            const esc_config* graph_cfg, void* cuda_stream, esc_group** out);
+
+/* Apply n batches (each graph at most once per call) in one pass.  Returns
+ * when every store and count is updated.  Errors as esc_apply_batch; the
+ * failing batch is named by esc_group_last_error. */
+esc_status esc_group_apply(esc_group* grp, int32_t n, const esc_batch* batches);
+
+esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window,
+                            uint64_t* out, int32_t n_out);
+esc_status esc_group_destroy(esc_group* grp);
+const char* esc_group_last_error(const esc_group* grp);
+esc_status esc_group_set_profiling(esc_group* grp, int32_t on);
+esc_status esc_group_last_stats(esc_group* grp, esc_batch_stats* out);
+int64_t esc_group_launch_count(const esc_group* grp);
+
+/* Library version string. */
+const char* esc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESCHER_H */

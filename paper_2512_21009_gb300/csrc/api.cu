@@ -1,0 +1,809 @@
+// api.cu -- the C ABI declared in include/escher.h.
+//
+// Host code here only sizes and allocates device memory, stages host-pointer
+// inputs to the device, launches the kernels of store.cu and count.cu in
+// order on the graph's stream, and reads back status and counts.  Every step
+// of the update and of the counting runs in those kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "escher.h"
+#include "escher_internal.cuh"
+#include "store_api.cuh"
+
+namespace esc {
+
+namespace {
+
+thread_local std::string t_create_error;
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct Engine {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    int sm_count = 0;
+    esc_config shared{};
+    int32_t G = 0;
+    std::vector<int64_t> vbase, ebase, ecap;
+    std::vector<int32_t> nv;
+    Store S{};
+    std::vector<void*> allocs;
+    // call staging
+    Call C{};
+    int64_t max_ins = 0, max_nnz = 0;
+    BatchIn* d_batches = nullptr;
+    int64_t* d_bins_lo = nullptr;
+    int64_t* d_bdel_lo = nullptr;
+    BatchIn* h_batches = nullptr;      // pinned
+    int64_t* h_lo = nullptr;           // pinned [2*(G+1)]
+    Scalars* d_sc = nullptr;
+    Scalars* h_sc = nullptr;           // pinned
+    uint64_t* h_counts = nullptr;      // pinned [kCStride]
+    int32_t* h_ids = nullptr;          // pinned [max_ins]
+    // device staging for host-pointer inputs
+    int64_t* st_off = nullptr;
+    int32_t* st_mem = nullptr;
+    int64_t* st_ts = nullptr;
+    int32_t* st_del = nullptr;
+    CountScratch cs{};
+    int64_t max_u = 0;
+    bool profiling = false;
+    cudaEvent_t ev[6] = {};
+    esc_batch_stats last{};
+    LaunchCounter lc;
+    std::string err;
+
+    template <typename T>
+    cudaError_t alloc(T** p, size_t n, int fill = 0) {
+        size_t bytes = n * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        *p = static_cast<T*>(q);
+        return cudaMemsetAsync(q, fill, bytes, st);
+    }
+
+    ~Engine() {
+        if (st) cudaStreamSynchronize(st);
+        for (void* p : allocs) cudaFree(p);
+        if (h_batches) cudaFreeHost(h_batches);
+        if (h_lo) cudaFreeHost(h_lo);
+        if (h_sc) cudaFreeHost(h_sc);
+        if (h_counts) cudaFreeHost(h_counts);
+        if (h_ids) cudaFreeHost(h_ids);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+
+    esc_status fail(esc_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    esc_status cuda_fail(cudaError_t e, const char* where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return ESC_ERR_CUDA;
+    }
+};
+
+#define ESC_CU(expr, where)                          \
+    do {                                             \
+        cudaError_t e__ = (expr);                    \
+        if (e__ != cudaSuccess) return E->cuda_fail(e__, where); \
+    } while (0)
+
+static esc_status check_cfg(const esc_config* c, bool per_graph_only) {
+    if (!c) return ESC_ERR_INVALID_ARG;
+    if (c->n_vertices <= 0 || c->capacity_hyperedges <= 0 || c->capacity_incidences <= 0)
+        return ESC_ERR_INVALID_ARG;
+    if (c->capacity_hyperedges > (int64_t(1) << 30)) return ESC_ERR_UNSUPPORTED;
+    if (per_graph_only) return ESC_OK;
+    if (c->max_batch_hyperedges <= 0 || c->max_batch_incidences <= 0) return ESC_ERR_INVALID_ARG;
+    if (c->max_batch_incidences > 0x7fffffffLL) return ESC_ERR_UNSUPPORTED;
+    if (c->families == 0 || (c->families & ~7u)) return ESC_ERR_INVALID_ARG;
+    if (c->delta < 0) return ESC_ERR_INVALID_ARG;
+    return ESC_OK;
+}
+
+static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, const esc_config* per,
+                               cudaStream_t st) {
+    E->shared = shared;
+    E->G = G;
+    E->st = st;
+    ESC_CU(cudaGetDevice(&E->dev), "cudaGetDevice");
+    ESC_CU(cudaDeviceGetAttribute(&E->sm_count, cudaDevAttrMultiProcessorCount, E->dev), "attribute");
+    E->vbase.resize(G);
+    E->ebase.resize(G);
+    E->ecap.resize(G);
+    E->nv.resize(G);
+    int64_t V = 0, Ecap = 0, inc = 0;
+    for (int g = 0; g < G; ++g) {
+        E->vbase[g] = V;
+        E->nv[g] = per[g].n_vertices;
+        E->ebase[g] = Ecap;
+        E->ecap[g] = round_up(per[g].capacity_hyperedges, 32);
+        V += per[g].n_vertices;
+        Ecap += E->ecap[g];
+        inc += per[g].capacity_incidences;
+    }
+    if (V > 0x7fffffffLL || Ecap > 0x7fffffffLL) return E->fail(ESC_ERR_UNSUPPORTED, "ID spaces exceed int32");
+    Store& S = E->S;
+    S.n_graphs = G;
+    S.nv_total = V;
+    S.e_total = Ecap;
+    S.fam = shared.families;
+    S.delta = shared.delta;
+    int64_t *vb, *eb, *ec;
+    int32_t* nvp;
+    ESC_CU(E->alloc(&vb, G), "alloc");
+    ESC_CU(E->alloc(&eb, G), "alloc");
+    ESC_CU(E->alloc(&ec, G), "alloc");
+    ESC_CU(E->alloc(&nvp, G), "alloc");
+    ESC_CU(cudaMemcpyAsync(vb, E->vbase.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaMemcpyAsync(eb, E->ebase.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaMemcpyAsync(ec, E->ecap.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaMemcpyAsync(nvp, E->nv.data(), G * 4, cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaStreamSynchronize(st), "sync");
+    S.vbase = vb;
+    S.ebase = eb;
+    S.ecap = ec;
+    S.nv = nvp;
+    ESC_CU(E->alloc(&S.hw, G), "alloc");
+    ESC_CU(E->alloc(&S.n_live, G), "alloc");
+    ESC_CU(E->alloc(&S.counts, int64_t(G) * kCStride), "alloc");
+    ESC_CU(E->alloc(&S.dcounts, int64_t(2) * G * kCStride), "alloc");
+    ESC_CU(E->alloc(&S.h_off, Ecap), "alloc");
+    ESC_CU(E->alloc(&S.h_card, Ecap), "alloc");
+    ESC_CU(E->alloc(&S.h_ts, Ecap), "alloc");
+    ESC_CU(E->alloc(&S.live, Ecap / 32), "alloc");
+    ESC_CU(E->alloc(&S.delb, Ecap / 32), "alloc");
+    ESC_CU(E->alloc(&S.insb, Ecap / 32), "alloc");
+    ESC_CU(E->alloc(&S.v_off, V), "alloc");
+    ESC_CU(E->alloc(&S.v_deg, V), "alloc");
+    ESC_CU(E->alloc(&S.v_cap, V), "alloc");
+    ESC_CU(E->alloc(&S.v_ndel, V), "alloc");
+    ESC_CU(E->alloc(&S.v_nins, V), "alloc");
+    ESC_CU(E->alloc(&S.v_touch, V), "alloc");
+    ESC_CU(E->alloc(&S.v_base, V), "alloc");
+    ESC_CU(E->alloc(&S.v_newoff, V), "alloc");
+    ESC_CU(E->alloc(&S.v_newcap, V), "alloc");
+    ESC_CU(E->alloc(&S.realloc_v, V), "alloc");
+    // slab arenas: power-of-two classes at most double a list, plus the
+    // smallest slab per hyperedge / vertex; v2h gets extra room because a
+    // vertex that outgrows its slab leaves the old one on a free stack
+    auto make_pool = [&](SlabPool& P, int64_t cap) -> esc_status {
+        P.cap = cap;
+        ESC_CU(E->alloc(&P.arena, cap), "alloc arena");
+        ESC_CU(E->alloc(&P.tail, 1), "alloc");
+        ESC_CU(E->alloc(&P.top, kNumClasses), "alloc");
+        int64_t tot = 0;
+        for (int c = 0; c < kNumClasses; ++c) {
+            P.base[c] = tot;
+            tot += cap / slab_size(c) + 1;
+        }
+        P.base[kNumClasses] = tot;
+        ESC_CU(E->alloc(&P.stack, tot), "alloc stack");
+        return ESC_OK;
+    };
+    esc_status s;
+    if ((s = make_pool(S.hp, 2 * inc + 8 * Ecap)) != ESC_OK) return s;
+    if ((s = make_pool(S.vp, 3 * inc + 8 * V)) != ESC_OK) return s;
+    // call staging
+    E->max_ins = shared.max_batch_hyperedges;
+    E->max_nnz = shared.max_batch_incidences;
+    Call& C = E->C;
+    C.max_nnz = E->max_nnz;
+    ESC_CU(E->alloc(&E->d_batches, G), "alloc");
+    ESC_CU(E->alloc(&E->d_bins_lo, G + 1), "alloc");
+    ESC_CU(E->alloc(&E->d_bdel_lo, G + 1), "alloc");
+    ESC_CU(E->alloc(&C.nnz_lo, G + 1), "alloc");
+    ESC_CU(E->alloc(&C.ins_off, E->max_ins + 1), "alloc");
+    ESC_CU(E->alloc(&C.raw, E->max_nnz), "alloc");
+    ESC_CU(E->alloc(&C.sorted, E->max_nnz), "alloc");
+    ESC_CU(E->alloc(&C.slot, E->max_nnz), "alloc");
+    ESC_CU(E->alloc(&C.ts, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.ins_g, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.card, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.ids, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.out_local, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.big, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.del, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.del_g, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&C.touched, V), "alloc");
+    ESC_CU(E->alloc(&E->d_sc, 1), "alloc");
+    C.sc = E->d_sc;
+    C.batches = E->d_batches;
+    ESC_CU(E->alloc(&E->st_off, E->max_ins + G + 1), "alloc");
+    ESC_CU(E->alloc(&E->st_mem, E->max_nnz), "alloc");
+    ESC_CU(E->alloc(&E->st_ts, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&E->st_del, E->max_ins), "alloc");
+    ESC_CU(cudaMallocHost(&E->h_batches, sizeof(BatchIn) * G), "pinned");
+    ESC_CU(cudaMallocHost(&E->h_lo, sizeof(int64_t) * 2 * (G + 1)), "pinned");
+    ESC_CU(cudaMallocHost(&E->h_sc, sizeof(Scalars)), "pinned");
+    ESC_CU(cudaMallocHost(&E->h_counts, sizeof(uint64_t) * kCStride), "pinned");
+    ESC_CU(cudaMallocHost(&E->h_ids, sizeof(int32_t) * E->max_ins), "pinned");
+    // counter scratch: overflow tables large enough for the biggest
+    // neighbourhood the capacities allow, within [2^15, 2^18] slots per table
+    int64_t slots = int64_t(1) << 15;
+    int64_t want = 2 * int64_t(inc < (int64_t(1) << 20) ? inc : (int64_t(1) << 20));
+    while (slots < want && slots < (int64_t(1) << 18)) slots <<= 1;
+    if (const char* env = getenv("ESC_COUNT_TABLE_SLOTS")) {
+        long long v = atoll(env);
+        if (v >= 1024 && (v & (v - 1)) == 0) slots = v;
+    }
+    int n_cta = E->sm_count * 2;
+    int64_t cap = E->max_ins;
+    void* csmem = nullptr;
+    ESC_CU(cudaMalloc(&csmem, count_scratch_bytes(cap, slots, n_cta)), "alloc count scratch");
+    E->allocs.push_back(csmem);
+    ESC_CU(count_scratch_init(&E->cs, csmem, cap, slots, n_cta, st), "scratch init");
+    E->max_u = count_max_u(slots);
+    // test knob: shrink the shared-memory tables so that the global-table
+    // and partitioned paths run on small inputs
+    if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
+        long long v = atoll(env);
+        if (v >= 64 && (v & (v - 1)) == 0) E->cs.smem_slots = v;
+    }
+    ESC_CU(upload_tables(st), "tables");
+    for (auto& e : E->ev) ESC_CU(cudaEventCreate(&e), "event");
+    ESC_CU(cudaStreamSynchronize(st), "sync");
+    return ESC_OK;
+}
+
+static std::string describe(const Scalars& s) {
+    char buf[256];
+    const int b = s.detail[0], i = s.detail[1], v = s.detail[2];
+    switch (s.status) {
+        case kErrInvalid:
+            if (b >= 0) snprintf(buf, sizeof buf, "batch %d: invalid input at element %d (value %d)", b, i, v);
+            else snprintf(buf, sizeof buf, "duplicate delete of hyperedge %d", v);
+            break;
+        case kErrNotFound:
+            snprintf(buf, sizeof buf, "delete of hyperedge %d, which is not live", v);
+            break;
+        case kErrNoMem:
+            if (b == -1) snprintf(buf, sizeof buf, "inserted members (%d) exceed max_batch_incidences (%d)", i, v);
+            else if (b == -2) snprintf(buf, sizeof buf, "h2v arena full");
+            else if (b == -3) snprintf(buf, sizeof buf, "v2h arena full");
+            else snprintf(buf, sizeof buf, "batch %d: hyperedge ID capacity exceeded", b);
+            break;
+        case kErrUnsupported:
+            if (b == -4 || b == -8)
+                snprintf(buf, sizeof buf,
+                         "a changed hyperedge meets %d vertex-hyperedge entries, above the counter's limit", v);
+            else if (b >= 0) snprintf(buf, sizeof buf, "batch %d: hyperedge %d has %d members (max %d)", b, i, v, kMaxCard);
+            else snprintf(buf, sizeof buf, "counter hash table overflow (%d)", b);
+            break;
+        default:
+            snprintf(buf, sizeof buf, "device error %d (%d, %d, %d)", s.status, b, i, v);
+    }
+    return buf;
+}
+
+// Stage one input array to the device if it is a host pointer.
+template <typename T>
+static esc_status stage(Engine* E, const T* src, size_t n, T* dst_area, size_t& used, size_t cap, const T** out) {
+    if (n == 0 || src == nullptr) {
+        *out = src;
+        return ESC_OK;
+    }
+    if (is_device_ptr(src)) {
+        *out = src;
+        return ESC_OK;
+    }
+    if (used + n > cap) return E->fail(ESC_ERR_OUT_OF_MEMORY, "batch larger than the staging capacity");
+    ESC_CU(cudaMemcpyAsync(dst_area + used, src, n * sizeof(T), cudaMemcpyHostToDevice, E->st), "stage");
+    *out = dst_area + used;
+    used += n;
+    return ESC_OK;
+}
+
+static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
+    if (n == 0) return ESC_OK;
+    if (n < 0 || n > E->G || !bs) return E->fail(ESC_ERR_INVALID_ARG, "bad batch list");
+    std::vector<char> seen(E->G, 0);
+    int64_t tot_ins = 0, tot_del = 0;
+    for (int b = 0; b < n; ++b) {
+        const esc_batch& x = bs[b];
+        if (x.graph < 0 || x.graph >= E->G || seen[x.graph]) return E->fail(ESC_ERR_INVALID_ARG, "bad or repeated graph");
+        seen[x.graph] = 1;
+        if (x.n_ins < 0 || x.n_del < 0) return E->fail(ESC_ERR_INVALID_ARG, "negative count");
+        if (x.n_ins > 0 && (!x.ins_offsets || !x.ins_members))
+            return E->fail(ESC_ERR_INVALID_ARG, "missing insert arrays");
+        if (x.n_ins > 0 && (E->shared.families & kFamT) && !x.ins_timestamps)
+            return E->fail(ESC_ERR_INVALID_ARG, "timestamps required by the temporal family");
+        if (x.n_del > 0 && !x.del_ids) return E->fail(ESC_ERR_INVALID_ARG, "missing delete IDs");
+        tot_ins += x.n_ins;
+        tot_del += x.n_del;
+    }
+    if (tot_ins + tot_del > E->max_ins)
+        return E->fail(ESC_ERR_OUT_OF_MEMORY, "batch larger than max_batch_hyperedges");
+    cudaStream_t st = E->st;
+    // stage host inputs
+    size_t u_off = 0, u_mem = 0, u_ts = 0, u_del = 0;
+    int64_t* bins = E->h_lo;
+    int64_t* bdel = E->h_lo + (E->G + 1);
+    bins[0] = bdel[0] = 0;
+    for (int b = 0; b < n; ++b) {
+        const esc_batch& x = bs[b];
+        BatchIn& B = E->h_batches[b];
+        B.graph = x.graph;
+        B.n_ins = x.n_ins;
+        B.n_del = x.n_del;
+        B.ins_lo = bins[b];
+        B.del_lo = bdel[b];
+        bins[b + 1] = bins[b] + x.n_ins;
+        bdel[b + 1] = bdel[b] + x.n_del;
+        esc_status s;
+        B.off = nullptr;
+        B.mem = nullptr;
+        B.ts = nullptr;
+        B.del = nullptr;
+        if (x.n_ins > 0) {
+            bool off_dev = is_device_ptr(x.ins_offsets);
+            if ((s = stage(E, x.ins_offsets, size_t(x.n_ins + 1), E->st_off, u_off, size_t(E->max_ins + E->G + 1),
+                           &B.off)) != ESC_OK)
+                return s;
+            if (!off_dev) {
+                int64_t nnz = x.ins_offsets[x.n_ins] - x.ins_offsets[0];
+                if (x.ins_offsets[0] != 0 || nnz < 0) return E->fail(ESC_ERR_INVALID_ARG, "offsets must start at 0");
+                if (nnz > E->max_nnz) return E->fail(ESC_ERR_OUT_OF_MEMORY, "batch members exceed max_batch_incidences");
+                if ((s = stage(E, x.ins_members, size_t(nnz), E->st_mem, u_mem, size_t(E->max_nnz), &B.mem)) != ESC_OK)
+                    return s;
+            } else {
+                if (is_device_ptr(x.ins_members)) B.mem = x.ins_members;
+                else return E->fail(ESC_ERR_INVALID_ARG, "device offsets need device members");
+            }
+            if ((s = stage(E, x.ins_timestamps, size_t(x.n_ins), E->st_ts, u_ts, size_t(E->max_ins), &B.ts)) != ESC_OK)
+                return s;
+        }
+        if (x.n_del > 0)
+            if ((s = stage(E, x.del_ids, size_t(x.n_del), E->st_del, u_del, size_t(E->max_ins), &B.del)) != ESC_OK)
+                return s;
+    }
+    ESC_CU(cudaMemcpyAsync(E->d_batches, E->h_batches, sizeof(BatchIn) * n, cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaMemcpyAsync(E->d_bins_lo, bins, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaMemcpyAsync(E->d_bdel_lo, bdel, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st), "copy");
+    ESC_CU(cudaMemsetAsync(E->d_sc, 0, sizeof(Scalars), st), "memset");
+    Call C = E->C;
+    C.n_batches = n;
+    C.n_ins = tot_ins;
+    C.n_del = tot_del;
+    const Store& S = E->S;
+    LaunchCounter lc;
+    const bool prof = E->profiling;
+    if (prof) cudaEventRecord(E->ev[0], st);
+    ESC_CU(store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc), "ingest");
+    if (prof) cudaEventRecord(E->ev[1], st);
+    ESC_CU(count_launch(S, C.sc, C.del, C.del_g, S.delb, 0, tot_del, 0, S.dcounts, E->cs, E->max_u, st, lc),
+           "count (deleted side)");
+    if (prof) cudaEventRecord(E->ev[2], st);
+    ESC_CU(store_delete(S, C, st, lc), "store delete");
+    ESC_CU(store_insert(S, C, E->sm_count, st, lc), "store insert");
+    if (prof) cudaEventRecord(E->ev[3], st);
+    ESC_CU(count_launch(S, C.sc, C.ids, C.ins_g, S.insb, 0, tot_ins, 1,
+                        S.dcounts + int64_t(S.n_graphs) * kCStride, E->cs, E->max_u, st, lc),
+           "count (inserted side)");
+    if (prof) cudaEventRecord(E->ev[4], st);
+    ESC_CU(store_finish(S, C, E->sm_count, st, lc), "finish");
+    if (prof) cudaEventRecord(E->ev[5], st);
+    ESC_CU(cudaMemcpyAsync(E->h_sc, E->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "status");
+    if (tot_ins > 0)
+        ESC_CU(cudaMemcpyAsync(E->h_ids, C.out_local, sizeof(int32_t) * tot_ins, cudaMemcpyDeviceToHost, st), "ids");
+    ESC_CU(cudaStreamSynchronize(st), "sync");
+    E->lc.total += lc.total;
+    E->lc.count += lc.count;
+    if (prof) {
+        esc_batch_stats& L = E->last;
+        cudaEventElapsedTime(&L.ms_total, E->ev[0], E->ev[5]);
+        cudaEventElapsedTime(&L.ms_ingest, E->ev[0], E->ev[1]);
+        cudaEventElapsedTime(&L.ms_count_del, E->ev[1], E->ev[2]);
+        cudaEventElapsedTime(&L.ms_store, E->ev[2], E->ev[3]);
+        cudaEventElapsedTime(&L.ms_count_ins, E->ev[3], E->ev[4]);
+    }
+    E->last.launches = lc.total;
+    E->last.count_launches = lc.count;
+    E->last.v2h_reads = int64_t(E->h_sc->stats[0]);
+    E->last.h2v_reads = int64_t(E->h_sc->stats[1]);
+    E->last.meta_reads = int64_t(E->h_sc->stats[2]);
+    E->last.triads = int64_t(E->h_sc->stats[3]);
+    if (E->h_sc->status != 0) {
+        E->err = describe(*E->h_sc);
+        return esc_status(E->h_sc->status);
+    }
+    for (int b = 0; b < n; ++b) {
+        const esc_batch& x = bs[b];
+        if (!x.out_ins_ids || x.n_ins == 0) continue;
+        const int32_t* src = E->h_ids + bins[b];
+        if (is_device_ptr(x.out_ins_ids))
+            ESC_CU(cudaMemcpy(x.out_ins_ids, src, sizeof(int32_t) * x.n_ins, cudaMemcpyHostToDevice), "ids out");
+        else
+            memcpy(x.out_ins_ids, src, sizeof(int32_t) * x.n_ins);
+    }
+    return ESC_OK;
+}
+
+static esc_status read_counts(Engine* E, int32_t g, esc_triad_type type, int64_t window, uint64_t* out,
+                              int32_t n_out) {
+    if (g < 0 || g >= E->G || !out) return E->fail(ESC_ERR_INVALID_ARG, "bad graph or output");
+    int off, len;
+    uint32_t fam;
+    switch (type) {
+        case ESC_TRIAD_HYPEREDGE: off = 0; len = kNH; fam = kFamH; break;
+        case ESC_TRIAD_VERTEX: off = kOffV; len = kNV; fam = kFamV; break;
+        case ESC_TRIAD_TEMPORAL: off = kOffT; len = kNT; fam = kFamT; break;
+        default: return E->fail(ESC_ERR_INVALID_ARG, "bad triad type");
+    }
+    if (n_out < len) return E->fail(ESC_ERR_INVALID_ARG, "output too small");
+    if (!(E->shared.families & fam)) return E->fail(ESC_ERR_UNSUPPORTED, "family not maintained");
+    if (type == ESC_TRIAD_TEMPORAL && window != E->shared.delta)
+        return E->fail(ESC_ERR_UNSUPPORTED, "temporal counts are kept for the configured delta only");
+    ESC_CU(cudaMemcpyAsync(E->h_counts, E->S.counts + int64_t(g) * kCStride, sizeof(uint64_t) * kCStride,
+                           cudaMemcpyDeviceToHost, E->st),
+           "counts");
+    ESC_CU(cudaStreamSynchronize(E->st), "sync");
+    memcpy(out, E->h_counts + off, sizeof(uint64_t) * len);
+    return ESC_OK;
+}
+
+namespace {
+
+__global__ void k_mark_sel(Store S, Scalars* sc, const int32_t* ids, int64_t n, int32_t* out_global) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t h = ids[i];
+    if (h < 0 || h >= S.ecap[0] || !bit_test(S.live, h)) {
+        set_error(sc, kErrNotFound, -1, i, h);
+        out_global[i] = 0;
+        return;
+    }
+    out_global[i] = h;
+    uint32_t old = atomicOr(&S.insb[h >> 5], 1u << (h & 31));
+    if (old & (1u << (h & 31))) set_error(sc, kErrInvalid, -1, i, h);
+}
+
+__global__ void k_unmark_sel(Store S, const int32_t* ids, int64_t n) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t h = ids[i];
+    if (h >= 0 && h < S.ecap[0]) atomicAnd(&S.insb[h >> 5], ~(1u << (h & 31)));
+}
+
+__global__ void k_latch_api(Scalars* sc) { sc->gate = sc->status; }
+
+}  // namespace
+
+static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_t* oh, uint64_t* ov, uint64_t* ot) {
+    if (n < 0 || (n > 0 && !ids)) return E->fail(ESC_ERR_INVALID_ARG, "bad id list");
+    cudaStream_t st = E->st;
+    const Store& S = E->S;
+    int32_t* d_ids = nullptr;
+    int32_t* d_glob = nullptr;
+    ESC_CU(cudaMalloc(&d_ids, sizeof(int32_t) * (n > 0 ? n : 1)), "alloc");
+    ESC_CU(cudaMalloc(&d_glob, sizeof(int32_t) * (n > 0 ? n : 1)), "alloc");
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        cudaFree(d_ids);
+        cudaFree(d_glob);
+    };
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(d_ids, ids, sizeof(int32_t) * n, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) { cleanup(); return E->cuda_fail(e, "copy ids"); }
+    }
+    cudaMemsetAsync(E->d_sc, 0, sizeof(Scalars), st);
+    uint64_t* dside = S.dcounts + int64_t(S.n_graphs) * kCStride;
+    cudaMemsetAsync(dside, 0, sizeof(uint64_t) * kCStride, st);
+    LaunchCounter lc;
+    if (n > 0) {
+        k_mark_sel<<<unsigned((n + 255) / 256), 256, 0, st>>>(S, E->d_sc, d_ids, n, d_glob);
+        k_latch_api<<<1, 1, 0, st>>>(E->d_sc);
+        for (int64_t lo = 0; lo < n; lo += E->cs.cap) {
+            int64_t hi = lo + E->cs.cap < n ? lo + E->cs.cap : n;
+            cudaError_t e = count_launch(S, E->d_sc, d_glob, nullptr, S.insb, lo, hi, 1, dside, E->cs,
+                                         E->max_u, st, lc);
+            if (e != cudaSuccess) { cleanup(); return E->cuda_fail(e, "count"); }
+        }
+        k_unmark_sel<<<unsigned((n + 255) / 256), 256, 0, st>>>(S, d_glob, n);
+    }
+    cudaMemcpyAsync(E->h_counts, dside, sizeof(uint64_t) * kCStride, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(E->h_sc, E->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+    cudaMemsetAsync(dside, 0, sizeof(uint64_t) * kCStride, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return E->cuda_fail(e, "sync");
+    E->lc.total += lc.total + (n > 0 ? 3 : 0);
+    E->lc.count += lc.count;
+    if (E->h_sc->status) {
+        E->err = describe(*E->h_sc);
+        return esc_status(E->h_sc->status);
+    }
+    if (oh && (E->shared.families & kFamH)) memcpy(oh, E->h_counts, sizeof(uint64_t) * kNH);
+    if (ov && (E->shared.families & kFamV)) memcpy(ov, E->h_counts + kOffV, sizeof(uint64_t) * kNV);
+    if (ot && (E->shared.families & kFamT)) memcpy(ot, E->h_counts + kOffT, sizeof(uint64_t) * kNT);
+    return ESC_OK;
+}
+
+}  // namespace esc
+
+using esc::Engine;
+
+struct esc_graph {
+    Engine* e;
+};
+struct esc_group {
+    Engine* e;
+};
+
+extern "C" {
+
+const char* esc_version(void) { return "escher-gb300 0.1 (sm_103a)"; }
+
+esc_status esc_group_create(const esc_config* shared, int32_t n_graphs, const esc_config* graph_cfg,
+                            void* cuda_stream, esc_group** out) {
+    if (!out) return ESC_ERR_INVALID_ARG;
+    *out = nullptr;
+    esc_status s = esc::check_cfg(shared, false);
+    if (s != ESC_OK || n_graphs <= 0 || !graph_cfg) {
+        esc::t_create_error = "invalid configuration";
+        return s != ESC_OK ? s : ESC_ERR_INVALID_ARG;
+    }
+    for (int g = 0; g < n_graphs; ++g)
+        if ((s = esc::check_cfg(&graph_cfg[g], true)) != ESC_OK) {
+            esc::t_create_error = "invalid graph configuration " + std::to_string(g);
+            return s;
+        }
+    Engine* E = new Engine();
+    s = esc::build_engine(E, *shared, n_graphs, graph_cfg, static_cast<cudaStream_t>(cuda_stream));
+    if (s != ESC_OK) {
+        esc::t_create_error = E->err;
+        delete E;
+        return s;
+    }
+    *out = new esc_group{E};
+    return ESC_OK;
+}
+
+esc_status esc_group_apply(esc_group* grp, int32_t n, const esc_batch* batches) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::run_call(grp->e, n, batches);
+}
+
+esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window, uint64_t* out,
+                            int32_t n_out) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::read_counts(grp->e, graph, type, window, out, n_out);
+}
+
+esc_status esc_group_destroy(esc_group* grp) {
+    if (!grp) return ESC_OK;
+    delete grp->e;
+    delete grp;
+    return ESC_OK;
+}
+
+const char* esc_group_last_error(const esc_group* grp) {
+    return grp ? grp->e->err.c_str() : esc::t_create_error.c_str();
+}
+
+esc_status esc_group_set_profiling(esc_group* grp, int32_t on) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    grp->e->profiling = on != 0;
+    return ESC_OK;
+}
+
+esc_status esc_group_last_stats(esc_group* grp, esc_batch_stats* out) {
+    if (!grp || !out) return ESC_ERR_INVALID_ARG;
+    *out = grp->e->last;
+    return ESC_OK;
+}
+
+int64_t esc_group_launch_count(const esc_group* grp) { return grp ? grp->e->lc.total : 0; }
+
+esc_status esc_create(const esc_config* cfg, int64_t n_he, const int64_t* offsets, const int32_t* members,
+                      const int64_t* timestamps, void* cuda_stream, esc_graph** out) {
+    if (!out) return ESC_ERR_INVALID_ARG;
+    *out = nullptr;
+    esc_status s = esc::check_cfg(cfg, false);
+    if (s != ESC_OK) {
+        esc::t_create_error = "invalid configuration";
+        return s;
+    }
+    if (n_he < 0 || (n_he > 0 && (!offsets || !members))) {
+        esc::t_create_error = "invalid initial hypergraph";
+        return ESC_ERR_INVALID_ARG;
+    }
+    if (n_he > 0 && (cfg->families & esc::kFamT) && !timestamps) {
+        esc::t_create_error = "timestamps required by the temporal family";
+        return ESC_ERR_INVALID_ARG;
+    }
+    Engine* E = new Engine();
+    s = esc::build_engine(E, *cfg, 1, cfg, static_cast<cudaStream_t>(cuda_stream));
+    if (s != ESC_OK) {
+        esc::t_create_error = E->err;
+        delete E;
+        return s;
+    }
+    esc_graph* g = new esc_graph{E};
+    if (n_he > 0) {
+        // initial hyperedges enter as insert batches, in order, so they get
+        // IDs 0..n_he-1 and their triads are counted by the same kernels
+        std::vector<int64_t> hoff(size_t(n_he) + 1);
+        if (esc::is_device_ptr(offsets)) {
+            cudaMemcpy(hoff.data(), offsets, sizeof(int64_t) * (n_he + 1), cudaMemcpyDeviceToHost);
+        } else {
+            memcpy(hoff.data(), offsets, sizeof(int64_t) * (n_he + 1));
+        }
+        if (hoff[0] != 0) {
+            esc::t_create_error = "offsets must start at 0";
+            esc_destroy(g);
+            return ESC_ERR_INVALID_ARG;
+        }
+        const bool mem_dev = esc::is_device_ptr(members);
+        const bool ts_dev = timestamps && esc::is_device_ptr(timestamps);
+        int64_t i0 = 0;
+        std::vector<int64_t> rebased;
+        while (i0 < n_he) {
+            int64_t i1 = i0;
+            while (i1 < n_he && i1 - i0 < E->max_ins && hoff[i1 + 1] - hoff[i0] <= E->max_nnz) ++i1;
+            if (i1 == i0) {
+                esc::t_create_error = "a hyperedge is larger than max_batch_incidences";
+                esc_destroy(g);
+                return ESC_ERR_OUT_OF_MEMORY;
+            }
+            rebased.resize(size_t(i1 - i0) + 1);
+            for (int64_t i = i0; i <= i1; ++i) rebased[i - i0] = hoff[i] - hoff[i0];
+            esc_batch b{};
+            b.graph = 0;
+            b.n_ins = i1 - i0;
+            b.ins_offsets = rebased.data();
+            b.ins_members = members + hoff[i0];
+            b.ins_timestamps = timestamps ? timestamps + i0 : nullptr;
+            (void)mem_dev;
+            (void)ts_dev;
+            s = esc::run_call(E, 1, &b);
+            if (s != ESC_OK) {
+                esc::t_create_error = E->err;
+                esc_destroy(g);
+                return s;
+            }
+            i0 = i1;
+        }
+    }
+    *out = g;
+    return ESC_OK;
+}
+
+esc_status esc_apply_batch(esc_graph* g, int64_t n_ins, const int64_t* ins_offsets, const int32_t* ins_members,
+                           const int64_t* ins_timestamps, int64_t n_del, const int32_t* del_ids, int32_t* out_ins_ids) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    if (n_ins == 0 && n_del == 0) return ESC_OK;
+    esc_batch b{};
+    b.graph = 0;
+    b.n_ins = n_ins;
+    b.ins_offsets = ins_offsets;
+    b.ins_members = ins_members;
+    b.ins_timestamps = ins_timestamps;
+    b.n_del = n_del;
+    b.del_ids = del_ids;
+    b.out_ins_ids = out_ins_ids;
+    return esc::run_call(g->e, 1, &b);
+}
+
+esc_status esc_triads(esc_graph* g, esc_triad_type type, int64_t window, uint64_t* out, int32_t n_out) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    return esc::read_counts(g->e, 0, type, window, out, n_out);
+}
+
+esc_status esc_local_triads(esc_graph* g, int64_t n_ids, const int32_t* ids, uint64_t* out_hyperedge,
+                            uint64_t* out_vertex, uint64_t* out_temporal) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    return esc::local_triads(g->e, n_ids, ids, out_hyperedge, out_vertex, out_temporal);
+}
+
+esc_status esc_destroy(esc_graph* g) {
+    if (!g) return ESC_OK;
+    delete g->e;
+    delete g;
+    return ESC_OK;
+}
+
+const char* esc_last_error(const esc_graph* g) { return g ? g->e->err.c_str() : esc::t_create_error.c_str(); }
+
+esc_status esc_set_profiling(esc_graph* g, int32_t on) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    g->e->profiling = on != 0;
+    return ESC_OK;
+}
+
+esc_status esc_last_stats(esc_graph* g, esc_batch_stats* out) {
+    if (!g || !out) return ESC_ERR_INVALID_ARG;
+    *out = g->e->last;
+    return ESC_OK;
+}
+
+int64_t esc_launch_count(const esc_graph* g) { return g ? g->e->lc.total : 0; }
+
+esc_status esc_export_sizes(esc_graph* g, int64_t* n_live, int64_t* n_incidences) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    Engine* E = g->e;
+    std::vector<int32_t> card(size_t(E->S.e_total));
+    std::vector<uint32_t> live(size_t(E->S.e_total / 32));
+    ESC_CU(cudaMemcpy(card.data(), E->S.h_card, card.size() * 4, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(live.data(), E->S.live, live.size() * 4, cudaMemcpyDeviceToHost), "export");
+    int64_t nl = 0, ni = 0;
+    for (size_t i = 0; i < card.size(); ++i)
+        if (live[i >> 5] >> (i & 31) & 1) {
+            ++nl;
+            ni += card[i];
+        }
+    if (n_live) *n_live = nl;
+    if (n_incidences) *n_incidences = ni;
+    return ESC_OK;
+}
+
+esc_status esc_export(esc_graph* g, int32_t* ids, int64_t* timestamps, int64_t* offsets, int32_t* members,
+                      int64_t* v_offsets, int32_t* v_members) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    Engine* E = g->e;
+    ESC_CU(cudaStreamSynchronize(E->st), "sync");
+    const esc::Store& S = E->S;
+    const size_t ne = size_t(S.e_total), nvt = size_t(S.nv_total);
+    std::vector<int32_t> card(ne), vdeg(nvt);
+    std::vector<uint32_t> live(ne / 32);
+    std::vector<int64_t> hoff(ne), hts(ne), voff(nvt);
+    int64_t htail = 0, vtail = 0;
+    ESC_CU(cudaMemcpy(card.data(), S.h_card, ne * 4, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(live.data(), S.live, live.size() * 4, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(hoff.data(), S.h_off, ne * 8, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(hts.data(), S.h_ts, ne * 8, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(vdeg.data(), S.v_deg, nvt * 4, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(voff.data(), S.v_off, nvt * 8, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(&htail, S.hp.tail, 8, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(&vtail, S.vp.tail, 8, cudaMemcpyDeviceToHost), "export");
+    std::vector<int32_t> harena(static_cast<size_t>(htail)), varena(static_cast<size_t>(vtail));
+    if (htail) ESC_CU(cudaMemcpy(harena.data(), S.hp.arena, size_t(htail) * 4, cudaMemcpyDeviceToHost), "export");
+    if (vtail) ESC_CU(cudaMemcpy(varena.data(), S.vp.arena, size_t(vtail) * 4, cudaMemcpyDeviceToHost), "export");
+    int64_t k = 0, p = 0;
+    if (offsets) offsets[0] = 0;
+    for (size_t i = 0; i < ne; ++i) {
+        if (!(live[i >> 5] >> (i & 31) & 1)) continue;
+        if (ids) ids[k] = int32_t(i);
+        if (timestamps) timestamps[k] = hts[i];
+        for (int j = 0; j < card[i]; ++j, ++p)
+            if (members) members[p] = harena[size_t(hoff[i]) + j];
+        ++k;
+        if (offsets) offsets[k] = p;
+    }
+    int64_t q = 0;
+    if (v_offsets) v_offsets[0] = 0;
+    for (size_t v = 0; v < nvt; ++v) {
+        std::vector<int32_t> l(varena.begin() + voff[v], varena.begin() + voff[v] + vdeg[v]);
+        std::sort(l.begin(), l.end());
+        if (v_members)
+            for (int32_t x : l) v_members[q++] = x;
+        else
+            q += int64_t(l.size());
+        if (v_offsets) v_offsets[v + 1] = q;
+    }
+    return ESC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+"""Bit-exact parity of the CUDA path with the CPU oracle (uint64 counts,
+identical incidence sets, identical assigned IDs), through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import OracleHypergraph
+from oracle import oracle as O
+from tests.harness import assert_counts_equal, assert_store_equal, caps_for, run_stream
+
+pytestmark = pytest.mark.gpu
+
+ALL = 7
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    from paper_2512_21009_gb300 import build as b
+    b.build()
+    from paper_2512_21009_gb300 import escher
+    escher.load()
+    torch.cuda.init()
+    return escher
+
+
+def test_tiny_config_all_families(E):
+    """2,000 vertices, 1,000 hyperedges of 2..8 members, one batch of 100
+    inserts and 100 deletes (the tiny configuration)."""
+    s = gen.tiny(0)
+    delta = int(s.initial.timestamps[-1] // 4)
+    run_stream(E, s, ALL, delta, method="brute", local_check=True)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_multi_batch_streams(E, seed):
+    s = gen.random_small(seed, 400, 300, 1, 9, n_batches=4, n_ins=40, n_del=40)
+    delta = int(s.initial.timestamps[-1] // 3)
+    run_stream(E, s, ALL, delta)
+
+
+def test_device_resident_inputs(E):
+    import torch
+    s = gen.random_small(4, 300, 200, 2, 7, n_batches=2, n_ins=30, n_del=30)
+    run_stream(E, s, ALL, 1 << 60, device=torch.device("cuda:0"))
+
+
+def test_zipf_cards_and_hub_vertices(E):
+    """Zipf(2) cardinalities up to 100 (the block sorter path) and Zipf(1.1)
+    vertex popularity (hubs)."""
+    s = gen.random_small(5, 600, 220, 2, 100, n_batches=2, n_ins=25, n_del=25,
+                         membership="zipf", card="zipf")
+    run_stream(E, s, ALL, 1 << 60)
+
+
+def test_repeated_members_ties_and_identical_sets(E):
+    rng = np.random.default_rng(6)
+    edges = [sorted(rng.choice(40, size=rng.integers(1, 6), replace=False).tolist()) for _ in range(60)]
+    edges += [list(e) for e in edges[:12]]                     # identical vertex sets
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    ts = rng.integers(0, 10, size=len(edges)).astype(np.int64)  # many equal timestamps
+    ins = [[3, 3, 7, 7, 7, 1], [5], [9, 2, 9], [11, 12, 13, 11]]  # repeats collapse
+    ioff = np.zeros(len(ins) + 1, np.int64)
+    ioff[1:] = np.cumsum([len(e) for e in ins])
+    imem = np.array([v for e in ins for v in e], np.int32)
+    its = np.array([4, 4, 5, 9], np.int64)
+    delta = 6
+    og = OracleHypergraph(40, off, mem, ts)
+    g = E.Graph(40, off, mem, ts, families=ALL, delta=delta, **caps_for(40, 200, 1000, 100, 1000))
+    assert_counts_equal(g.counts(), O.counts(og, ALL, delta, "brute"), "initial")
+    dels = np.array([0, 5, 61, 70], np.int64)
+    ids_o = og.apply_batch(ioff, imem, its, dels)
+    ids_g = g.apply_batch(ioff, imem, its, dels.astype(np.int32))
+    assert np.array_equal(ids_g, ids_o)
+    assert_counts_equal(g.counts(), O.counts(og, ALL, delta, "brute"), "after")
+    assert_store_equal(g, og)
+
+
+def test_large_neighbourhoods_use_global_tables(E):
+    """A hyperedge meeting more than the shared-memory tables hold: N(h) and
+    N(g1) go to the per-block global tables."""
+    rng = np.random.default_rng(7)
+    nv = 3000
+    big = sorted(rng.choice(nv, size=600, replace=False).tolist())
+    edges = [big] + [sorted(rng.choice(nv, size=rng.integers(2, 12), replace=False).tolist())
+                     for _ in range(1500)]
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    og = OracleHypergraph(nv, off, mem, np.arange(len(edges)))
+    g = E.Graph(nv, off, mem, np.arange(len(edges)), families=ALL, delta=1 << 40,
+                **caps_for(nv, 4000, 40000, 2000, 40000))
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), "initial")
+    # delete and re-insert the big hyperedge
+    ids_o = og.apply_batch(np.array([0, 600]), np.array(big), np.array([7]), np.array([0]))
+    ids_g = g.apply_batch(np.array([0, 600]), np.array(big, np.int32), np.array([7]), np.array([0], np.int32))
+    assert np.array_equal(ids_g, ids_o)
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), "after")
+
+
+def test_multi_pass_and_global_tables(E, monkeypatch):
+    """Small table limits force the global tables and the partitioned
+    (multi-pass) N(g1) build: an unchanged hyperedge B whose vertices gain
+    degree becomes a neighbour with more entries than one table holds."""
+    monkeypatch.setenv("ESC_COUNT_TABLE_SLOTS", "1024")
+    monkeypatch.setenv("ESC_COUNT_SMEM_SLOTS", "64")
+    rng = np.random.default_rng(13)
+    nv = 400
+    B = sorted(rng.choice(nv, size=60, replace=False).tolist())
+    edges = [B] + [sorted(rng.choice(nv, size=rng.integers(2, 6), replace=False).tolist()) for _ in range(300)]
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    ts = np.arange(len(edges), dtype=np.int64)
+    og = OracleHypergraph(nv, off, mem, ts)
+    g = E.Graph(nv, off, mem, ts, families=ALL, delta=1 << 40, **caps_for(nv, 2000, 20000, 1000, 20000))
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), "initial")
+    for step in range(3):
+        ins = [[B[(7 * j + step) % 60], int(rng.integers(0, nv))] for j in range(120)]
+        ins = [sorted(set(e)) for e in ins]
+        ioff = np.zeros(len(ins) + 1, np.int64)
+        ioff[1:] = np.cumsum([len(e) for e in ins])
+        imem = np.array([v for e in ins for v in e], np.int32)
+        its = np.full(len(ins), 1000 + step, np.int64)
+        dels = og.live_ids()[1:11]
+        ids_o = og.apply_batch(ioff, imem, its, dels)
+        ids_g = g.apply_batch(ioff, imem, its, dels.astype(np.int32))
+        assert np.array_equal(ids_g, ids_o)
+        assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), f"step {step}")
+    assert_store_equal(g, og)
+
+
+@pytest.mark.parametrize("families", [1, 2, 4, 3, 5, 6])
+def test_family_subsets(E, families):
+    s = gen.random_small(9, 300, 200, 2, 7, n_batches=1, n_ins=30, n_del=30)
+    run_stream(E, s, families, int(s.initial.timestamps[-1] // 2), check_store=False)
+
+
+def test_edge_cases_empty_and_degenerate(E):
+    # empty initial graph, insert-only, delete-only, delete everything
+    nv = 50
+    g = E.Graph(nv, None, None, None, families=ALL, delta=100, **caps_for(nv, 200, 2000, 200, 2000))
+    og = OracleHypergraph(nv)
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 100), "empty")
+    g.apply_batch(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64), np.zeros(0, np.int32))
+    rng = np.random.default_rng(10)
+    edges = [sorted(rng.choice(nv, size=rng.integers(1, 5), replace=False).tolist()) for _ in range(40)]
+    off = np.zeros(41, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    ts = np.arange(40, dtype=np.int64) * 7
+    ids_o = og.apply_batch(off, mem, ts, np.zeros(0, np.int64))
+    ids_g = g.apply_batch(off, mem, ts, None)
+    assert np.array_equal(ids_g, ids_o)
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 100), "insert-only")
+    dels = np.arange(0, 40, 3)
+    og.apply_batch(np.zeros(1, np.int64), np.zeros(0), None, dels)
+    g.apply_batch(None, None, None, dels.astype(np.int32))
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 100), "delete-only")
+    rest = og.live_ids()
+    og.apply_batch(np.zeros(1, np.int64), np.zeros(0), None, rest)
+    g.apply_batch(None, None, None, rest.astype(np.int32))
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 100), "all deleted")
+    for v in g.counts().values():
+        assert not np.any(v)
+    assert_store_equal(g, og)
+
+
+def test_invalid_batches_leave_graph_unchanged(E):
+    s = gen.random_small(11, 200, 100, 2, 6)
+    caps = caps_for(200, 150, 1000, 100, 1000)
+    g = E.Graph(200, s.initial.offsets, s.initial.members, s.initial.timestamps, families=ALL, delta=1 << 50, **caps)
+    before = g.counts()
+    ex0 = g.export()
+    bad = [
+        dict(ins_offsets=np.array([0, 2]), ins_members=np.array([1, 999], np.int32), ins_timestamps=np.array([1]),
+             del_ids=None, code=1),          # vertex out of range
+        dict(ins_offsets=np.array([0, 0]), ins_members=np.zeros(0, np.int32), ins_timestamps=np.array([1]),
+             del_ids=None, code=1),          # empty hyperedge
+        dict(ins_offsets=None, ins_members=None, ins_timestamps=None, del_ids=np.array([3, 3], np.int32), code=1),
+        dict(ins_offsets=None, ins_members=None, ins_timestamps=None, del_ids=np.array([140], np.int32), code=2),
+        dict(ins_offsets=np.array([0, 2]), ins_members=np.array([1, 2], np.int32), ins_timestamps=np.array([1]),
+             del_ids=np.array([5, 150], np.int32), code=2),   # valid insert, one bad delete
+        dict(ins_offsets=np.arange(0, 102, dtype=np.int64), ins_members=np.arange(101, dtype=np.int32) % 200,
+             ins_timestamps=np.arange(101), del_ids=None, code=3),   # more than max_batch_hyperedges
+    ]
+    for b in bad:
+        code = b.pop("code")
+        with pytest.raises(E.EscError) as ei:
+            g.apply_batch(**b)
+        assert ei.value.status == code, (ei.value, code)
+        assert_counts_equal(g.counts(), before, "after a rejected batch")
+        ex = g.export()
+        for k in ex0:
+            assert np.array_equal(ex[k], ex0[k]), k
+    # the graph still works
+    og = OracleHypergraph(200, s.initial.offsets, s.initial.members, s.initial.timestamps)
+    ids_o = og.apply_batch(np.array([0, 3]), np.array([4, 5, 6]), np.array([9]), np.array([1, 2]))
+    ids_g = g.apply_batch(np.array([0, 3]), np.array([4, 5, 6], np.int32), np.array([9]), np.array([1, 2], np.int32))
+    assert np.array_equal(ids_g, ids_o)
+    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 50), "recovered")
+
+
+def test_out_of_capacity_is_rejected_cleanly(E):
+    g = E.Graph(100, None, None, None, families=ALL, delta=10, capacity_hyperedges=32,
+                capacity_incidences=64, max_batch_hyperedges=100, max_batch_incidences=1000)
+    off = np.arange(0, 41, dtype=np.int64)
+    with pytest.raises(E.EscError) as ei:
+        g.apply_batch(off, np.arange(40, dtype=np.int32), np.arange(40), None)
+    assert ei.value.status == 3
+    for v in g.counts().values():
+        assert not np.any(v)
+
+
+def test_local_triads_match_oracle(E):
+    s = gen.random_small(12, 300, 250, 2, 8)
+    g = E.Graph(300, s.initial.offsets, s.initial.members, s.initial.timestamps, families=ALL,
+                delta=1 << 50, **caps_for(300, 300, 3000, 300, 3000))
+    og = OracleHypergraph(300, s.initial.offsets, s.initial.members, s.initial.timestamps)
+    off, mem, ts, ids = og.csr()
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(len(ids), size=17, replace=False))
+    h, t = O.count_containing(off, mem, ts, ids, 1 << 50, 5, sel)
+    got = g.local_triads(ids[sel])
+    assert np.array_equal(got["hyperedge"], h)
+    assert np.array_equal(got["temporal"], t)
+    full = g.local_triads(ids)
+    assert_counts_equal(full, g.counts(), "recount")
+
+
+def test_group_matches_single_graphs(E):
+    streams = [gen.random_small(20 + i, 150 + 30 * i, 100 + 40 * i, 2, 7, n_batches=1, n_ins=15 + i,
+                                n_del=10 + i) for i in range(5)]
+    delta = 1 << 50
+    shared = E.make_config(1, 1, 1, 4000, 40000, ALL, delta)
+    cfgs = [E.make_config(s.n_vertices, 400, 4000, 0, 0, ALL, delta) for s in streams]
+    grp = E.esc_group_create(shared, cfgs)
+    try:
+        ogs = []
+        first = [dict(graph=i, ins_offsets=s.initial.offsets, ins_members=s.initial.members,
+                      ins_timestamps=s.initial.timestamps, del_ids=None) for i, s in enumerate(streams)]
+        E.esc_group_apply(grp, first)
+        for i, s in enumerate(streams):
+            og = OracleHypergraph(s.n_vertices, s.initial.offsets, s.initial.members, s.initial.timestamps)
+            ogs.append(og)
+            want = O.counts(og, ALL, delta)
+            assert np.array_equal(E.esc_group_triads(grp, i, 0), want["hyperedge"])
+        batches, expect_ids = [], []
+        for i in (4, 1, 3):   # a subset, out of order
+            s, og = streams[i], ogs[i]
+            b = s.batches[0]
+            dels = og.resolve_ranks(b.del_ranks)
+            expect_ids.append(og.apply_batch(b.inserts.offsets, b.inserts.members, b.inserts.timestamps, dels))
+            out = np.zeros(b.inserts.n, np.int32)
+            batches.append(dict(graph=i, ins_offsets=b.inserts.offsets, ins_members=b.inserts.members,
+                                ins_timestamps=b.inserts.timestamps, del_ids=dels.astype(np.int32), out_ids=out))
+        E.esc_group_apply(grp, batches)
+        for b, want_ids in zip(batches, expect_ids):
+            assert np.array_equal(b["out_ids"], want_ids)
+        for i, og in enumerate(ogs):
+            want = O.counts(og, ALL, delta)
+            assert np.array_equal(E.esc_group_triads(grp, i, 0), want["hyperedge"]), i
+            assert np.array_equal(E.esc_group_triads(grp, i, 1), want["vertex"]), i
+            assert np.array_equal(E.esc_group_triads(grp, i, 2, delta), want["temporal"]), i
+    finally:
+        E.esc_group_destroy(grp)
+
+
+def test_temporal_stream_with_expirations(E):
+    """Time-ordered stream (scaled temporal configuration): every batch
+    inserts the next hyperedges and deletes those older than T - delta."""
+    ts_stream = gen.temporal(seed=3, scale=0.0005, batch=256, n_batches=6, kmax=12)
+    delta = int(ts_stream.delta // 7200)
+    from tests.harness import GpuLive
+    nv = ts_stream.n_vertices
+    g = E.Graph(nv, None, None, None, families=ALL, delta=delta,
+                **caps_for(nv, 4000, 60000, 2000, 20000))
+    og = OracleHypergraph(nv)
+    live = GpuLive(0)
+    for k, b in enumerate(ts_stream.batches):
+        t_cut = int(b.timestamps.max()) - delta
+        dels_o = np.array([i for i in og.live_ids() if og.ts[i] < t_cut], np.int64)
+        dels_g = live.expired(t_cut)
+        ids_o = og.apply_batch(b.offsets, b.members, b.timestamps, dels_o)
+        ids_g = g.apply_batch(b.offsets, b.members, b.timestamps, dels_g.astype(np.int32))
+        assert np.array_equal(ids_g, ids_o)
+        live.apply(dels_g, ids_g, b.timestamps)
+        assert_counts_equal(g.counts(), O.counts(og, ALL, delta), f"batch {k}")
