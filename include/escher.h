@@ -247,6 +247,37 @@ esc_status esc_group_set_profiling(esc_group* grp, int32_t on);
 esc_status esc_group_last_stats(esc_group* grp, esc_batch_stats* out);
 int64_t esc_group_launch_count(const esc_group* grp);
 
+/* Allocation-free counting.  The paper has no counterpart of this call; it
+ * exists for callers that cannot allocate device memory -- code running
+ * while a stream is captured into a CUDA graph, code confined to a memory
+ * budget handed out by its own allocator -- and so cannot use esc_create.
+ *
+ * Counts every triad of one static hypergraph: n_he hyperedges in CSR form
+ * (offsets int64[n_he+1] with offsets[0] == 0; members int32[offsets[n_he]],
+ * each hyperedge's members sorted ascending without repeats, vertex IDs in
+ * [0, n_vertices)); timestamps int64[n_he] or NULL (all zero).  families and
+ * delta as in esc_config.  out_counts receives uint64[129]: 30 hyperedge
+ * classes, then the 3 vertex types, then the 96 temporal classes (families
+ * not asked for read 0).  Hyperedge i has ID i.  Every pointer must be
+ * device memory of the current device; the call runs on cuda_stream and
+ * returns once out_counts is written.
+ *
+ * It calls no cudaMalloc or cudaFree: its temporary buffers live in one
+ * fixed array of device memory (80 MiB) that every GPU which loads the
+ * library holds until the process exits.  The first call on a device looks
+ * up that array's device address; make it before any stream capture.  All
+ * calls share the array and every call resets what it needs, so calls whose
+ * GPU work overlaps race on it: serialise them.
+ *
+ * Limits: n_he <= 524,288; offsets[n_he] <= 4,194,304; n_vertices <=
+ * 1,048,576; each hyperedge at most ESC_MAX_CARDINALITY members; for every
+ * hyperedge, the sum of its members' degrees at most 2,048.
+ * Errors: INVALID_ARG (bad arguments, host pointers, malformed hypergraph),
+ * UNSUPPORTED (a limit exceeded), CUDA. */
+esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int64_t* offsets,
+                                    const int32_t* members, const int64_t* timestamps, uint32_t families,
+                                    int64_t delta, uint64_t* out_counts, void* cuda_stream);
+
 /* Library version string. */
 const char* esc_version(void);
 

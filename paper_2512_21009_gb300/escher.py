@@ -34,7 +34,7 @@ EXPORTED = [
     "esc_export_sizes", "esc_export", "esc_set_profiling", "esc_last_stats", "esc_launch_count",
     "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
     "esc_group_last_error", "esc_group_set_profiling", "esc_group_last_stats", "esc_group_launch_count",
-    "esc_version",
+    "esc_version", "esc_count_static_noalloc",
 ]
 
 
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH):
     L.esc_group_launch_count.argtypes = [vp]
     L.esc_group_launch_count.restype = i64
     L.esc_version.restype = C.c_char_p
+    L.esc_count_static_noalloc.argtypes = [i32, i64, vp, vp, vp, u32, i64, vp, vp]
+    L.esc_count_static_noalloc.restype = st
     for name in ("esc_create", "esc_apply_batch", "esc_triads", "esc_local_triads", "esc_destroy",
                  "esc_export_sizes", "esc_export", "esc_set_profiling", "esc_last_stats",
                  "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
@@ -301,6 +303,22 @@ def esc_group_last_stats(grp: int) -> dict:
 
 def esc_group_launch_count(grp: int) -> int:
     return int(load().esc_group_launch_count(grp))
+
+
+def esc_count_static_noalloc(n_vertices: int, offsets, members, timestamps, families: int, delta: int,
+                             out_counts, stream=None) -> None:
+    """All triad counts of a static hypergraph whose arrays are CUDA tensors,
+    written to ``out_counts`` (a CUDA int64/uint64 tensor of 129 entries),
+    without any device allocation by the library."""
+    L = load()
+    po, ko = _ptr(offsets, np.int64)
+    pm, km = _ptr(members, np.int32)
+    pt, kt = _ptr(timestamps, np.int64)
+    n_he = len(offsets) - 1
+    rc = L.esc_count_static_noalloc(int(n_vertices), n_he, po, pm, pt, int(families), int(delta),
+                                    out_counts.data_ptr(), _stream_ptr(stream))
+    if rc != 0:
+        raise EscError(rc, "esc_count_static_noalloc failed")
 
 
 # ---------------------------------------------------------------------------
