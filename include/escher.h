@@ -195,6 +195,11 @@ typedef struct {
     int64_t h2v_reads;       /* hyperedge->vertex entries read by the counter  */
     int64_t meta_reads;      /* per-neighbour metadata lookups by the counter  */
     int64_t triads;          /* triads classified by the counter               */
+    int64_t alg_entries;     /* incidence entries the method reads for the
+                                changed hyperedges: for each changed h,
+                                |h| + sum of its members' degrees, plus, for
+                                each candidate neighbour g1 of h, |g1| + sum
+                                of g1's members' degrees                      */
 } esc_batch_stats;
 
 esc_status esc_set_profiling(esc_graph* g, int32_t on);
@@ -269,9 +274,9 @@ int64_t esc_group_launch_count(const esc_group* grp);
  * calls share the array and every call resets what it needs, so calls whose
  * GPU work overlaps race on it: serialise them.
  *
- * Limits: n_he <= 524,288; offsets[n_he] <= 4,194,304; n_vertices <=
- * 1,048,576; each hyperedge at most ESC_MAX_CARDINALITY members; for every
- * hyperedge, the sum of its members' degrees at most 2,048.
+ * Limits: n_he <= 262,144; offsets[n_he] <= 2,097,152; n_vertices <=
+ * 524,288; each hyperedge at most ESC_MAX_CARDINALITY members; for every
+ * hyperedge, the sum of its members' degrees at most 1,024.
  * Errors: INVALID_ARG (bad arguments, host pointers, malformed hypergraph),
  * UNSUPPORTED (a limit exceeded), CUDA. */
 esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int64_t* offsets,

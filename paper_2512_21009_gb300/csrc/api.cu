@@ -57,6 +57,7 @@ struct Engine {
     Scalars* h_sc = nullptr;           // pinned
     uint64_t* h_counts = nullptr;      // pinned [kCStride]
     int32_t* h_ids = nullptr;          // pinned [max_ins]
+    int64_t* h_word = nullptr;         // pinned word read back by the counter
     // device staging for host-pointer inputs
     int64_t* st_off = nullptr;
     int32_t* st_mem = nullptr;
@@ -90,6 +91,7 @@ struct Engine {
         if (h_sc) cudaFreeHost(h_sc);
         if (h_counts) cudaFreeHost(h_counts);
         if (h_ids) cudaFreeHost(h_ids);
+        if (h_word) cudaFreeHost(h_word);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -240,22 +242,29 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     ESC_CU(cudaMallocHost(&E->h_sc, sizeof(Scalars)), "pinned");
     ESC_CU(cudaMallocHost(&E->h_counts, sizeof(uint64_t) * kCStride), "pinned");
     ESC_CU(cudaMallocHost(&E->h_ids, sizeof(int32_t) * E->max_ins), "pinned");
-    // counter scratch: overflow tables large enough for the biggest
-    // neighbourhood the capacities allow, within [2^15, 2^18] slots per table
+    // counter scratch: neighbour lists for a run of changed hyperedges (runs
+    // are split when the lists would not fit), per-ID inversion arrays, and
+    // per-block overflow hash tables
+    CountShape sh;
+    sh.cap = E->max_ins;
+    sh.list_cap = std::max<int64_t>(int64_t(1) << 22, 128 * sh.cap);
+    sh.e_cap = Ecap;
     int64_t slots = int64_t(1) << 15;
-    int64_t want = 2 * int64_t(inc < (int64_t(1) << 20) ? inc : (int64_t(1) << 20));
-    while (slots < want && slots < (int64_t(1) << 18)) slots <<= 1;
+    while (slots < 2 * std::min<int64_t>(inc, int64_t(1) << 20) && slots < (int64_t(1) << 16)) slots <<= 1;
+    sh.gs_nh = slots;
+    sh.gs_c = slots < (int64_t(1) << 16) ? slots : (int64_t(1) << 17);
     if (const char* env = getenv("ESC_COUNT_TABLE_SLOTS")) {
         long long v = atoll(env);
-        if (v >= 1024 && (v & (v - 1)) == 0) slots = v;
+        if (v >= 1024 && (v & (v - 1)) == 0) sh.gs_nh = sh.gs_c = v;
     }
-    int n_cta = E->sm_count * 2;
-    int64_t cap = E->max_ins;
+    sh.n_cta_nh = E->sm_count * 2;
+    sh.n_cta_c = E->sm_count;
     void* csmem = nullptr;
-    ESC_CU(cudaMalloc(&csmem, count_scratch_bytes(cap, slots, n_cta)), "alloc count scratch");
+    ESC_CU(cudaMalloc(&csmem, count_scratch_bytes(sh)), "alloc count scratch");
     E->allocs.push_back(csmem);
-    ESC_CU(count_scratch_init(&E->cs, csmem, cap, slots, n_cta, st), "scratch init");
-    E->max_u = count_max_u(slots);
+    ESC_CU(cudaMallocHost(&E->h_word, sizeof(int64_t)), "pinned");
+    ESC_CU(count_scratch_init(&E->cs, csmem, sh, E->h_word, st), "scratch init");
+    E->max_u = count_max_u(sh);
     // test knob: shrink the shared-memory tables so that the global-table
     // and partitioned paths run on small inputs
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
@@ -425,6 +434,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     E->last.h2v_reads = int64_t(E->h_sc->stats[1]);
     E->last.meta_reads = int64_t(E->h_sc->stats[2]);
     E->last.triads = int64_t(E->h_sc->stats[3]);
+    E->last.alg_entries = int64_t(E->h_sc->stats[4]);
     if (E->h_sc->status != 0) {
         E->err = describe(*E->h_sc);
         return esc_status(E->h_sc->status);

@@ -3,35 +3,43 @@
 // The paper counts the triads of the affected regions before and after the
 // update.  Here the same change is computed exactly as
 //     new = old - T_old(holding >= 1 deleted) + T_new(holding >= 1 inserted),
-// since a triad of unchanged hyperedges keeps its class.  For one set of
-// changed hyperedges X, every triad holding a member of X is counted once, at
-// its member of X with the smallest ID (the "attribution" rule); the kernel
-// therefore enumerates, for each h in X, the triads {h, a, b} in which no
-// other member of X with a smaller ID appears.
+// since a triad of unchanged hyperedges keeps its class.  For one set X of
+// changed hyperedges, every triad holding a member of X is counted once, at
+// its member of X with the smallest ID (the "attribution" rule).
 //
 // For a changed h with neighbourhood N(h) (hyperedges sharing a vertex with
-// h, paper Section II: neighbouring hyperedges), the connected triples
-// holding h are exactly
-//   (i)  {h, g1, g2} with g1, g2 in N(h)        -- closed if g1 meets g2,
-//                                                   else open with centre h;
-//   (ii) {h, g1, f}  with g1 in N(h), f in N(g1) outside N(h) and f != h
-//                                                -- open with centre g1.
-// One work item is (h, a range of h's incidence positions).  Its block builds
-// N(h) in a hash table with x_hg = |h & g|, takes as candidates the g1 first
-// met inside its position range, and for each candidate builds N(g1) with
-// x = |g1 & f| and t = |h & g1 & f| in a second hash table; type (ii) triads
-// come from scanning that table, type (i) from probing it with every g2 > g1
-// of N(h).  Venn region sizes follow from |a|, |b|, |c|, the three pairwise
-// intersections and t by inclusion-exclusion; the 7-bit pattern is mapped to
-// its class by the tables of tables.cu.
+// h), the connected triples holding h are exactly
+//   (i)  {h, g1, g2}, g1 < g2 both in N(h)     -- closed if g1 meets g2,
+//                                                 else open with centre h;
+//   (ii) {h, g1, f},  g1 in N(h), f in N(g1) outside N(h), f != h
+//                                              -- open with centre g1.
+// Both are enumerated from the pair (h, g1).  The work is organised by g1
+// (centre-major): one block builds N(g1) once, in shared memory, with
+// x = |g1 & f| and the size, timestamp and changed flag of every f, and
+// then serves every changed h that has g1 as a candidate neighbour:
+//   1. k_nh_build   per changed h: N(h) with x_hg and the smallest shared
+//                   vertex, written as a list; the incident-vertex types 1
+//                   and 2; candidate pairs (g1, h) counted per g1;
+//   2. scans and k_scatter invert the pairs into lists L(g1);
+//   3. k_center     per (g1, part of L(g1)): N(g1) in shared memory; for each
+//                   h of the part, (i) by probing N(g1) with every g2 in N(h)
+//                   (which also marks N(h) inside N(g1)), then (ii) by one
+//                   pass over the unmarked entries of N(g1).
+// t = |h & g1 & g2| for a closed triple comes from the smallest shared
+// vertices: if |h & g1| = 1 it is [that vertex is in g2], and symmetrically;
+// otherwise the members of h are tested against g1 and g2.
 //
-// The incident-vertex types (Section II) come from the same quantities:
+// Venn region sizes follow from |a|, |b|, |c|, the three pairwise
+// intersections and t by inclusion-exclusion; the 7-bit pattern is mapped to
+// its class by the tables of tables.cu.  The incident-vertex types (Sec. II):
 //   type 1 = sum over h of C(|h|, 3)
 //   type 2 = sum over hyperedge pairs {h, g} of C(x_hg, 2) (|h| + |g| - 4)
 //   type 3 = sum over closed triples {a, b, c} of
 //            x_ab x_bc x_ac - t (x_ab + x_bc + x_ac) + 2 t
-// (choose a vertex in each pairwise intersection, all three distinct).
+// (a vertex in each pairwise intersection, all three distinct).
+#include <algorithm>
 #include <climits>
+#include <vector>
 
 #include "escher_internal.cuh"
 #include "store_api.cuh"
@@ -40,61 +48,25 @@ namespace esc {
 
 namespace {
 
-constexpr int NT = 256;
-constexpr int NW = NT / 32;
-constexpr int NH_S = 2048;   // shared-memory N(h) table slots
-constexpr int T1_S = 4096;   // shared-memory N(g1) table slots
-constexpr int HM_S = 1024;   // members of h kept in shared memory
-constexpr int SEG = NT;      // members per segment
-constexpr int CHUNK = 256;   // incidence positions of h per work item
 constexpr int32_t EMPTY = -1;
-constexpr int kHistT = kNH;  // temporal bins start here in the shared histograms
+constexpr int kHistT = kNH;          // temporal bins start here in the shared histograms
 constexpr int kHistN = kNH + kNT;
+constexpr uint32_t kFlag = 0x80000000u;  // "also in N(h)" mark in N(g1) values
+constexpr uint32_t kXMask = 0xffffu;
+
+// neighbourhood build
+constexpr int NT_NH = 256;
+constexpr int NH_S = 4096;           // shared-memory N(h) table slots
+// centre kernel
+constexpr int NT_C = 512;
+constexpr int NW_C = NT_C / 32;
+constexpr int T1_S = 8192;           // shared-memory N(g1) table slots
+constexpr int LCH = 32;              // changed hyperedges per centre work item
+constexpr int kWin = 64;             // |h & g1| values served from the histogram window
+constexpr int kBigNH = 512;          // N(h) with more entries also gets a hash table in the lists
+constexpr int kHistSmem = 1024;      // |h| up to which the open-at-h histograms live in shared memory
 
 __constant__ ClassTables c_tables;
-
-struct CountArgs {
-    Store S;
-    Scalars* sc;
-    const int32_t* changed;
-    const int32_t* changed_g;
-    const uint32_t* chg;
-    int64_t lo, hi;
-    const int64_t* item_start;  // [hi-lo+1]
-    int side;
-    uint64_t* dc;               // [G][kCStride]
-    int32_t* g_keys;
-    uint32_t* g_vals;
-    int32_t* g_aux;
-    int32_t* g_list;
-    int64_t g_slots;
-    uint32_t nh_smem_cap, t1_smem_cap;  // shared-memory table limits (<= NH_S, T1_S)
-};
-
-struct __align__(16) Smem {
-    unsigned long long acc[128];
-    uint32_t hist[NW][128];
-    int32_t nh_keys[NH_S];
-    uint32_t nh_x[NH_S];
-    int32_t nh_fp[NH_S];
-    int32_t nh_list[NH_S / 2];
-    int32_t t1_keys[T1_S];
-    uint32_t t1_vals[T1_S];
-    int32_t t1_list[T1_S / 2];
-    int32_t hm[HM_S];
-    int64_t seg_off[SEG];
-    int32_t seg_pre[SEG + 1];
-    uint8_t seg_inh[SEG];
-    int32_t cand_g[CHUNK];
-    uint32_t cand_x[CHUNK];
-    int8_t cls30[128];
-    int8_t cls96[128];
-    uint8_t perm[6][128];
-    int warp_tmp[32];
-    long long red[NW];
-    long long item;
-    int n_nh, n_t1, n_cand;
-};
 
 // MurmurHash3's 32-bit finaliser (Appleby, public domain), used as the slot hash.
 __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
@@ -160,6 +132,7 @@ __device__ __forceinline__ int tab_find(const Tab& T, int32_t k) {
     return -1;
 }
 
+template <int NT>
 __device__ __forceinline__ void tab_clear(const Tab& T, int n) {
     for (int i = threadIdx.x; i < n; i += NT) {
         int s = T.list[i];
@@ -185,44 +158,45 @@ __device__ __forceinline__ bool contains_sorted(const int32_t* a, int n, int32_t
     return lo < n && a[lo] == v;
 }
 
-__device__ __forceinline__ long long block_sum(long long v, Smem& s) {
+template <int NT>
+__device__ __forceinline__ long long block_sum(long long v, long long* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane_id() == 0) s.red[warp_id()] = v;
+    if (lane_id() == 0) red[warp_id()] = v;
     __syncthreads();
     long long t = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) t += s.red[w];
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
     __syncthreads();
     return t;
 }
 
-// Load members mem[0..n) (n <= SEG) into the segment arrays: v2h offset,
-// optionally "also in h", and the exclusive prefix of their degrees.
-// Returns the number of incidence entries of the segment.
-__device__ __forceinline__ int load_segment(const Store& S, const int32_t* mem, int n, bool want_inh,
-                                            const int32_t* hmem, int kh, Smem& s) {
+// Members mem[0..n) (n <= NT) of one segment: v2h offset, vertex, and the
+// exclusive prefix of their degrees.  Returns the segment's entry count.
+template <int NT>
+__device__ __forceinline__ int load_segment(const Store& S, const int32_t* mem, int n, int64_t* seg_off,
+                                            int32_t* seg_v, int32_t* seg_pre, int* warp_tmp) {
     int d = 0;
     if (int(threadIdx.x) < n) {
         int32_t v = mem[threadIdx.x];
         d = S.v_deg[v];
-        s.seg_off[threadIdx.x] = S.v_off[v];
-        if (want_inh) s.seg_inh[threadIdx.x] = contains_sorted(hmem, kh, v) ? 1 : 0;
+        seg_off[threadIdx.x] = S.v_off[v];
+        if (seg_v) seg_v[threadIdx.x] = v;
     }
     int tot;
-    int pre = block_exclusive_scan<NT>(d, &tot, s.warp_tmp);
-    if (int(threadIdx.x) < n) s.seg_pre[threadIdx.x] = pre;
-    if (threadIdx.x == 0) s.seg_pre[n] = tot;
+    int pre = block_exclusive_scan<NT>(d, &tot, warp_tmp);
+    if (int(threadIdx.x) < n) seg_pre[threadIdx.x] = pre;
+    if (threadIdx.x == 0) seg_pre[n] = tot;
     __syncthreads();
     return tot;
 }
 
-// member index of incidence entry e of the loaded segment
-__device__ __forceinline__ int seg_member(const Smem& s, int n, int e) {
-    int lo = 0, hi = n;  // largest m with seg_pre[m] <= e
+// member of incidence entry e of a loaded segment: largest m with pre[m] <= e
+__device__ __forceinline__ int seg_member(const int32_t* pre, int n, int e) {
+    int lo = 0, hi = n;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (s.seg_pre[mid] <= e) lo = mid;
+        if (pre[mid] <= e) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -230,26 +204,39 @@ __device__ __forceinline__ int seg_member(const Smem& s, int n, int e) {
 
 struct Accum {
     unsigned long long v1, v2, v3;
-    unsigned long long n_v2h, n_h2v, n_meta, n_tri;
+    unsigned long long n_v2h, n_h2v, n_meta, n_tri, n_alg;
 };
 
+struct Tables {
+    int8_t cls30[128];
+    int8_t cls96[128];
+    uint8_t perm[6][128];
+};
+
+__device__ __forceinline__ void load_tables(Tables& t, int nt) {
+    for (int i = threadIdx.x; i < 128; i += nt) {
+        t.cls30[i] = c_tables.cls30[i];
+        t.cls96[i] = c_tables.cls96[i];
+        for (int q = 0; q < 6; ++q) t.perm[q][i] = c_tables.perm[q][i];
+    }
+}
+
 // Classify the triad (a, b, c) with sizes ka, kb, kc, pairwise intersections
-// xab, xbc, xac and triple intersection t.
-__device__ __forceinline__ void classify(Smem& s, uint32_t fam, int64_t delta, int32_t ia, int32_t ib,
-                                         int32_t ic, int ka, int kb, int kc, int xab, int xbc, int xac, int t,
-                                         int64_t ta, int64_t tb, int64_t tc, Accum& acc) {
+// xab, xbc, xac and triple intersection t into the warp's histogram.
+__device__ __forceinline__ void classify(const Tables& tb, uint32_t* hist, uint32_t fam, int64_t delta, int32_t ia,
+                                         int32_t ib, int32_t ic, int ka, int kb, int kc, int xab, int xbc, int xac,
+                                         int t, int64_t ta, int64_t tbb, int64_t tc, Accum& acc) {
     int ra = ka - xab - xac + t, rb = kb - xab - xbc + t, rc = kc - xbc - xac + t;
     int m = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xab - t > 0) << 3) | ((xbc - t > 0) << 4) |
             ((xac - t > 0) << 5) | ((t > 0) << 6);
-    uint32_t* hist = s.hist[warp_id()];
     ++acc.n_tri;
     if (fam & kFamH) {
-        int c = s.cls30[m];
+        int c = tb.cls30[m];
         if (c >= 0) atomicAdd(&hist[c], 1u);
     }
     if (fam & kFamT) {
         // order the labels 0 (a), 1 (b), 2 (c) by (timestamp, ID)
-        int64_t T[3] = {ta, tb, tc};
+        int64_t T[3] = {ta, tbb, tc};
         int32_t I[3] = {ia, ib, ic};
         int o0 = 0, o1 = 1, o2 = 2, tmp;
 #define ESC_BEFORE(x, y) (T[x] < T[y] || (T[x] == T[y] && I[x] < I[y]))
@@ -258,22 +245,42 @@ __device__ __forceinline__ void classify(Smem& s, uint32_t fam, int64_t delta, i
         if (ESC_BEFORE(o1, o0)) { tmp = o0; o0 = o1; o1 = tmp; }
 #undef ESC_BEFORE
         if (T[o2] - T[o0] <= delta) {
-            int c = s.cls96[s.perm[perm_index(o0, o1)][m]];
+            int c = tb.cls96[tb.perm[perm_index(o0, o1)][m]];
             if (c >= 0) atomicAdd(&hist[kHistT + c], 1u);
         }
     }
 }
 
-__device__ void flush(const CountArgs& A, Smem& s, int g, Accum& acc) {
+struct CountArgs {
+    Store S;
+    Scalars* sc;
+    const int32_t* changed;
+    const int32_t* changed_g;
+    const uint32_t* chg;
+    int64_t lo, n;
+    int side;
+    uint64_t* dc;               // [G][kCStride]
+    CountScratch cs;
+    uint32_t nh_smem_cap, c_smem_cap;
+};
+
+template <int NT>
+__device__ void flush(const CountArgs& A, unsigned long long* acc_bins, uint32_t (*hist)[128], int nw, int g,
+                      Accum& acc, long long* red) {
     uint64_t* out = A.dc + int64_t(g) * kCStride;
     for (int b = threadIdx.x; b < kHistN; b += NT) {
-        unsigned long long v = s.acc[b];
+        unsigned long long v = acc_bins ? acc_bins[b] : 0;
+        if (hist)
+            for (int w = 0; w < nw; ++w) {
+                v += hist[w][b];
+                hist[w][b] = 0;
+            }
         if (v) atomicAdd(reinterpret_cast<unsigned long long*>(b < kNH ? &out[b] : &out[kOffT + (b - kHistT)]), v);
-        s.acc[b] = 0;
+        if (acc_bins) acc_bins[b] = 0;
     }
-    long long v1 = block_sum((long long)acc.v1, s);
-    long long v2 = block_sum((long long)acc.v2, s);
-    long long v3 = block_sum((long long)acc.v3, s);
+    long long v1 = block_sum<NT>((long long)acc.v1, red);
+    long long v2 = block_sum<NT>((long long)acc.v2, red);
+    long long v3 = block_sum<NT>((long long)acc.v3, red);
     if (threadIdx.x == 0) {
         if (v1) atomicAdd(reinterpret_cast<unsigned long long*>(&out[kOffV + 0]), (unsigned long long)v1);
         if (v2) atomicAdd(reinterpret_cast<unsigned long long*>(&out[kOffV + 1]), (unsigned long long)v2);
@@ -283,275 +290,33 @@ __device__ void flush(const CountArgs& A, Smem& s, int g, Accum& acc) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT, 2) k_count(CountArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& s = *reinterpret_cast<Smem*>(smem_raw);
-    const Store& S = A.S;
-    if (A.sc->gate) return;
-    const int tid = threadIdx.x;
-    const uint32_t fam = S.fam;
-    const int64_t delta = S.delta;
-    const bool want_open = (fam & (kFamH | kFamT)) != 0;
-    const int32_t* v2h = S.vp.arena;
-    const int32_t* h2v = S.hp.arena;
-
-    for (int i = tid; i < 128; i += NT) {
-        s.cls30[i] = c_tables.cls30[i];
-        s.cls96[i] = c_tables.cls96[i];
-        s.acc[i] = 0;
-        for (int q = 0; q < 6; ++q) s.perm[q][i] = c_tables.perm[q][i];
-        for (int w = 0; w < NW; ++w) s.hist[w][i] = 0;
-    }
-    for (int i = tid; i < NH_S; i += NT) {
-        s.nh_keys[i] = EMPTY;
-        s.nh_x[i] = 0;
-        s.nh_fp[i] = INT_MAX;
-    }
-    for (int i = tid; i < T1_S; i += NT) {
-        s.t1_keys[i] = EMPTY;
-        s.t1_vals[i] = 0;
-    }
-    if (tid == 0) s.n_nh = s.n_t1 = s.n_cand = 0;
-    __syncthreads();
-
-    const int64_t gs = A.g_slots;
-    const int64_t r_nh = int64_t(blockIdx.x) * 2, r_t1 = r_nh + 1;
-    Tab gNH{A.g_keys + r_nh * gs, A.g_vals + r_nh * gs, A.g_aux + r_nh * gs, A.g_list + r_nh * (gs / 2),
-            &s.n_nh, uint32_t(gs - 1), int(gs / 2)};
-    Tab gT1{A.g_keys + r_t1 * gs, A.g_vals + r_t1 * gs, nullptr, A.g_list + r_t1 * (gs / 2), &s.n_t1,
-            uint32_t(gs - 1), int(gs / 2)};
-
-    Accum acc = {0, 0, 0, 0, 0, 0, 0};
-    const int64_t n_items = A.sc->items[A.side];
-    const int64_t n_changed = A.hi - A.lo;
-    int cur_g = -1;
-
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s.item = (long long)atomicAdd(&A.sc->queue[A.side], 1ull);
-        __syncthreads();
-        const int64_t item = s.item;
-        if (item >= n_items) break;
-        const int64_t i = upper_bound_dev(A.item_start, n_changed + 1, item) - 1;
-        const int64_t chunk = item - A.item_start[i];
-        const int32_t h = A.changed[A.lo + i];
-        const int g = A.changed_g ? A.changed_g[A.lo + i] : 0;
-        if (g != cur_g) {
-            if (cur_g >= 0) flush(A, s, cur_g, acc);
-            cur_g = g;
-        }
-        const int kh = S.h_card[h];
-        const int32_t* hmem = h2v + S.h_off[h];
-        const int64_t tsh = S.h_ts[h];
-        const bool hm_smem = kh <= HM_S;
-        long long uh = 0;
-        for (int t = tid; t < kh; t += NT) {
-            int32_t v = hmem[t];
-            if (hm_smem) s.hm[t] = v;
-            uh += S.v_deg[v];
-        }
-        acc.n_h2v += (tid < kh) ? (kh - tid + NT - 1) / NT : 0;
-        uh = block_sum(uh, s);  // also orders the hm writes before use
-        const int32_t* hm = hm_smem ? s.hm : hmem;
-
-        // ---- N(h) with x_hg and the first incidence position of every g
-        Tab NH;
-        const uint32_t nh_cap = pow2_at_least(2 * uh);
-        if (nh_cap <= A.nh_smem_cap) {
-            NH = Tab{s.nh_keys, s.nh_x, s.nh_fp, s.nh_list, &s.n_nh, nh_cap - 1, NH_S / 2};
-        } else if ((int64_t)nh_cap <= gs) {
-            NH = gNH;
-            NH.mask = nh_cap - 1;
-        } else {
-            if (tid == 0) set_error(A.sc, kErrUnsupported, -8, h, uh);
-            continue;
-        }
-        const bool single_h = kh <= SEG;
-        int seg_n = 0, seg_tot = 0;
-        {
-            long long pos_base = 0;
-            for (int m0 = 0; m0 < kh; m0 += SEG) {
-                seg_n = min(SEG, kh - m0);
-                seg_tot = load_segment(S, hmem + m0, seg_n, false, nullptr, 0, s);
-                for (int e = tid; e < seg_tot; e += NT) {
-                    int m = seg_member(s, seg_n, e);
-                    int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
-                    if (f != h) tab_insert(NH, f, 1u, int32_t(pos_base + e), A.sc);
-                }
-                acc.n_v2h += (tid < seg_tot) ? (seg_tot - tid + NT - 1) / NT : 0;
-                pos_base += seg_tot;
-                __syncthreads();
-            }
-        }
-        const int n_nh = min(s.n_nh, NH.list_cap);
-
-        // ---- candidates g1: first met at a position of this chunk, and not
-        //      a changed hyperedge of smaller ID
-        const long long p_lo = chunk * CHUNK, p_hi = min(p_lo + CHUNK, (long long)uh);
-        {
-            long long pos_base = 0;
-            for (int m0 = 0; m0 < kh && pos_base < p_hi; m0 += SEG) {
-                int n = min(SEG, kh - m0);
-                int tot = single_h ? seg_tot : load_segment(S, hmem + m0, n, false, nullptr, 0, s);
-                long long lo = max(p_lo - pos_base, 0LL), hi = min(p_hi - pos_base, (long long)tot);
-                for (long long e = lo + tid; e < hi; e += NT) {
-                    int m = seg_member(s, n, int(e));
-                    int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
-                    if (f == h) continue;
-                    int sl = tab_find(NH, f);
-                    if (sl < 0 || NH.aux[sl] != int32_t(pos_base + e)) continue;
-                    if (f < h && bit_test(A.chg, f)) continue;
-                    int c = atomicAdd(&s.n_cand, 1);
-                    s.cand_g[c] = f;
-                    s.cand_x[c] = NH.vals[sl];
-                }
-                pos_base += tot;
-                __syncthreads();
-            }
-        }
-        const int n_cand = s.n_cand;
-
-        // ---- every candidate g1
-        for (int c = 0; c < n_cand; ++c) {
-            const int32_t g1 = s.cand_g[c];
-            const int xh1 = int(s.cand_x[c]);
-            const int k1 = S.h_card[g1];
-            const int32_t* g1mem = h2v + S.h_off[g1];
-            const int64_t ts1 = S.h_ts[g1];
-            const bool single = k1 <= SEG;
-            long long u1;
-            int n1seg = 0;
-            if (single) {
-                n1seg = k1;
-                u1 = load_segment(S, g1mem, k1, true, hm, kh, s);
-            } else {
-                long long u = 0;
-                for (int t = tid; t < k1; t += NT) u += S.v_deg[g1mem[t]];
-                u1 = block_sum(u, s);
-            }
-            acc.n_h2v += (tid < k1) ? (k1 - tid + NT - 1) / NT : 0;
-            Tab T1;
-            int P = 1;
-            const uint32_t t1_cap = pow2_at_least(2 * u1);
-            if (t1_cap <= A.t1_smem_cap) {
-                T1 = Tab{s.t1_keys, s.t1_vals, nullptr, s.t1_list, &s.n_t1, t1_cap - 1, T1_S / 2};
-            } else {
-                T1 = gT1;
-                if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
-                else P = int((4 * u1 + gs - 1) / gs);
-            }
-            for (int p = 0; p < P; ++p) {
-                // build N(g1): x in the low 16 bits, t (also in h) in the high 16
-                for (int m0 = 0; m0 < k1; m0 += SEG) {
-                    int n = single ? n1seg : min(SEG, k1 - m0);
-                    int tot = single ? int(u1) : load_segment(S, g1mem + m0, n, true, hm, kh, s);
-                    for (int e = tid; e < tot; e += NT) {
-                        int m = seg_member(s, n, e);
-                        int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
-                        if (f == g1) continue;
-                        if (P > 1 && part_of(f, P) != p) continue;
-                        tab_insert(T1, f, 1u | (uint32_t(s.seg_inh[m]) << 16), 0, A.sc);
-                    }
-                    acc.n_v2h += (tid < tot) ? (tot - tid + NT - 1) / NT : 0;
-                    if (!single) __syncthreads();
-                }
-                __syncthreads();
-                const int n_t1 = min(s.n_t1, T1.list_cap);
-                // (ii) open at g1: f in N(g1), not in N(h), not h
-                if (want_open) {
-                    for (int q = tid; q < n_t1; q += NT) {
-                        const int sl = T1.list[q];
-                        const int32_t f = T1.keys[sl];
-                        if (f == h) continue;
-                        if (tab_find(NH, f) >= 0) continue;
-                        ++acc.n_meta;
-                        if (f < h && bit_test(A.chg, f)) continue;
-                        const int kf = S.h_card[f];
-                        const int64_t tf = (fam & kFamT) ? S.h_ts[f] : 0;
-                        classify(s, fam, delta, h, g1, f, kh, k1, kf, xh1, int(T1.vals[sl] & 0xffffu), 0, 0, tsh,
-                                 ts1, tf, acc);
-                    }
-                }
-                // (i) g2 in N(h) with g2 > g1: closed if g2 is in N(g1), else open at h
-                for (int q = tid; q < n_nh; q += NT) {
-                    const int sl2 = NH.list[q];
-                    const int32_t g2 = NH.keys[sl2];
-                    if (g2 <= g1) continue;
-                    if (P > 1 && part_of(g2, P) != p) continue;
-                    if (g2 < h && bit_test(A.chg, g2)) continue;
-                    const int s1 = tab_find(T1, g2);
-                    const uint32_t val = s1 >= 0 ? T1.vals[s1] : 0u;
-                    const int x12 = int(val & 0xffffu), t = int(val >> 16);
-                    if (x12 == 0 && !want_open) continue;
-                    ++acc.n_meta;
-                    const int xh2 = int(NH.vals[sl2]);
-                    const int k2 = S.h_card[g2];
-                    const int64_t t2 = (fam & kFamT) ? S.h_ts[g2] : 0;
-                    if (want_open) classify(s, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, tsh, ts1, t2, acc);
-                    if ((fam & kFamV) && x12 > 0)
-                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
-                                  2ull * t;
-                }
-                __syncthreads();
-                tab_clear(T1, n_t1);
-                __syncthreads();
-                if (tid == 0) s.n_t1 = 0;
-                __syncthreads();
-            }
-        }
-
-        // ---- pairs {h, g} (type 2) and h itself (type 1), once per h
-        if (chunk == 0 && (fam & kFamV)) {
-            for (int q = tid; q < n_nh; q += NT) {
-                const int sl = NH.list[q];
-                const int32_t g2 = NH.keys[sl];
-                if (g2 < h && bit_test(A.chg, g2)) continue;
-                const unsigned long long x = NH.vals[sl];
-                if (x >= 2) acc.v2 += (x * (x - 1) / 2) * (unsigned long long)(kh + S.h_card[g2] - 4);
-            }
-            if (tid == 0 && kh >= 3) acc.v1 += (unsigned long long)kh * (kh - 1) * (kh - 2) / 6;
-        }
-
-        // ---- fold the warp histograms, clear N(h)
-        __syncthreads();
-        for (int b = tid; b < kHistN; b += NT) {
-            unsigned long long v = 0;
-            for (int w = 0; w < NW; ++w) {
-                v += s.hist[w][b];
-                s.hist[w][b] = 0;
-            }
-            s.acc[b] += v;
-        }
-        tab_clear(NH, n_nh);
-        __syncthreads();
-        if (tid == 0) {
-            s.n_nh = 0;
-            s.n_cand = 0;
-        }
-    }
-    __syncthreads();
-    if (cur_g >= 0) flush(A, s, cur_g, acc);
-    long long r0 = block_sum((long long)acc.n_v2h, s);
-    long long r1 = block_sum((long long)acc.n_h2v, s);
-    long long r2 = block_sum((long long)acc.n_meta, s);
-    long long r3 = block_sum((long long)acc.n_tri, s);
-    if (tid == 0) {
+template <int NT>
+__device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
+    long long r0 = block_sum<NT>((long long)acc.n_v2h, red);
+    long long r1 = block_sum<NT>((long long)acc.n_h2v, red);
+    long long r2 = block_sum<NT>((long long)acc.n_meta, red);
+    long long r3 = block_sum<NT>((long long)acc.n_tri, red);
+    long long r4 = block_sum<NT>((long long)acc.n_alg, red);
+    if (threadIdx.x == 0) {
         atomicAdd(&A.sc->stats[0], (unsigned long long)r0);
         atomicAdd(&A.sc->stats[1], (unsigned long long)r1);
         atomicAdd(&A.sc->stats[2], (unsigned long long)r2);
         atomicAdd(&A.sc->stats[3], (unsigned long long)r3);
+        atomicAdd(&A.sc->stats[4], (unsigned long long)r4);
     }
 }
 
-// ---- work list: chunks of every changed hyperedge, then their prefix sum
+// ---------------------------------------------------------------------------
+// 1. sizes and N(h)
+// ---------------------------------------------------------------------------
 
-__global__ void k_chunks(Store S, Scalars* sc, const int32_t* changed, int64_t lo, int64_t n, int32_t* chunks,
-                         int64_t max_u) {
+__global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t lo, int64_t n, int32_t* sizes,
+                          int64_t max_u) {
     int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     int lane = lane_id();
     if (i >= n) return;
     if (sc->gate) {  // the call failed earlier: the changed list may hold invalid IDs
-        if (lane == 0) chunks[i] = 1;
+        if (lane == 0) sizes[i] = 0;
         return;
     }
     int32_t h = changed[lo + i];
@@ -562,17 +327,673 @@ __global__ void k_chunks(Store S, Scalars* sc, const int32_t* changed, int64_t l
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
     if (lane == 0) {
-        if (u > max_u) set_error(sc, kErrUnsupported, -4, h, u);
-        long long c = (u + CHUNK - 1) / CHUNK;
-        chunks[i] = int32_t(c < 1 ? 1 : c);
+        if (u > max_u) {
+            set_error(sc, kErrUnsupported, -4, h, u);
+            u = 0;
+        }
+        // list of up to u entries, plus a hash table for a large N(h)
+        sizes[i] = int32_t(u > kBigNH ? u + pow2_at_least(2 * u) : u);
     }
 }
 
+struct SmemNH {
+    int32_t keys[NH_S];
+    uint32_t vals[NH_S];
+    int32_t aux[NH_S];
+    int32_t list[NH_S / 2];
+    int64_t seg_off[NT_NH];
+    int32_t seg_v[NT_NH];
+    int32_t seg_pre[NT_NH + 1];
+    int warp_tmp[32];
+    long long red[NT_NH / 32];
+    long long item;
+    int n_list;
+    unsigned long long acc[128];      // open-at-h class counts of this block
+    uint32_t hx[2][kHistSmem + 1];    // x histograms of N'(h), split by [g inside h]
+    unsigned long long q3[3];
+};
+
+// Class of an open triad {h, g1, g2} centred at h (g1, g2 in N(h), g1 and
+// g2 disjoint): regions h-only |h| - x1 - x2, g1-only |g1| - x1, g2-only
+// |g2| - x2, h&g1 and h&g2 non-empty, the rest empty.
+__device__ __forceinline__ int open_at_h_mask(int kh, int x1, int x2, int k1, int k2) {
+    return (kh != x1 + x2 ? 1 : 0) | (k1 != x1 ? 2 : 0) | (k2 != x2 ? 4 : 0) | (1 << 3) | (1 << 5);
+}
+
+__global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemNH& s = *reinterpret_cast<SmemNH*>(smem_raw);
+    const Store& S = A.S;
+    if (A.sc->gate) return;
+    const int tid = threadIdx.x;
+    const uint32_t fam = S.fam;
+    const CountScratch& cs = A.cs;
+    for (int i = tid; i < NH_S; i += NT_NH) {
+        s.keys[i] = EMPTY;
+        s.vals[i] = 0;
+        s.aux[i] = INT_MAX;
+    }
+    for (int i = tid; i < 128; i += NT_NH) s.acc[i] = 0;
+    for (int i = tid; i < 2 * (kHistSmem + 1); i += NT_NH) s.hx[i / (kHistSmem + 1)][i % (kHistSmem + 1)] = 0;
+    if (tid == 0) s.n_list = 0;
+    // open-at-h triads are counted in aggregate unless the temporal family is kept
+    const bool agg = (fam & kFamH) && !(fam & kFamT);
+    uint32_t* ghx = cs.onh_hist + int64_t(blockIdx.x) * 2 * (kMaxCard + 1);
+    __syncthreads();
+    const int64_t gs = cs.gs_nh;
+    Tab gNH{cs.onh_keys + blockIdx.x * gs, cs.onh_vals + blockIdx.x * gs, cs.onh_aux + blockIdx.x * gs,
+            cs.onh_list + blockIdx.x * (gs / 2), &s.n_list, uint32_t(gs - 1), int(gs / 2)};
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cur_g = -1;
+    const int32_t* v2h = S.vp.arena;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s.item = (long long)atomicAdd(&A.sc->qnh[A.side], 1ull);
+        __syncthreads();
+        const int64_t i = s.item;
+        if (i >= A.n) break;
+        const int32_t h = A.changed[A.lo + i];
+        const int g = A.changed_g ? A.changed_g[A.lo + i] : 0;
+        if (g != cur_g) {
+            if (cur_g >= 0) flush<NT_NH>(A, s.acc, nullptr, 0, cur_g, acc, s.red);
+            cur_g = g;
+        }
+        const int kh = S.h_card[h];
+        const int32_t* hmem = S.hp.arena + S.h_off[h];
+        long long uh = 0;
+        for (int t = tid; t < kh; t += NT_NH) uh += S.v_deg[hmem[t]];
+        uh = block_sum<NT_NH>(uh, s.red);
+        Tab NH;
+        const uint32_t cap = pow2_at_least(2 * uh);
+        if (cap <= A.nh_smem_cap) {
+            NH = Tab{s.keys, s.vals, s.aux, s.list, &s.n_list, cap - 1, NH_S / 2};
+        } else if ((int64_t)cap <= gs) {
+            NH = gNH;
+            NH.mask = cap - 1;
+        } else {
+            if (tid == 0) {
+                set_error(A.sc, kErrUnsupported, -8, h, uh);
+                cs.nh_n[i] = 0;
+                cs.nh_tcap[i] = 0;
+            }
+            continue;
+        }
+        acc.n_h2v += (tid < kh) ? (kh - tid + NT_NH - 1) / NT_NH : 0;
+        if (tid == 0) acc.n_alg += (unsigned long long)(uh + kh);
+        for (int m0 = 0; m0 < kh; m0 += NT_NH) {
+            const int n = min(NT_NH, kh - m0);
+            const int tot = load_segment<NT_NH>(S, hmem + m0, n, s.seg_off, s.seg_v, s.seg_pre, s.warp_tmp);
+            for (int e = tid; e < tot; e += NT_NH) {
+                const int m = seg_member(s.seg_pre, n, e);
+                const int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
+                if (f != h) tab_insert(NH, f, 1u, s.seg_v[m], A.sc);
+            }
+            acc.n_v2h += (tid < tot) ? (tot - tid + NT_NH - 1) / NT_NH : 0;
+            __syncthreads();
+        }
+        // distinct neighbours never outnumber the region reserved for them
+        // (sum of member degrees); the clamp only matters after an error
+        const int nn = int(min((long long)min(s.n_list, NH.list_cap), uh));
+        const int64_t base = cs.nh_off[i];
+        for (int q = tid; q < nn; q += NT_NH) {
+            const int sl = NH.list[q];
+            const int32_t gg = NH.keys[sl];
+            const uint32_t x = NH.vals[sl];
+            cs.nh_g[base + q] = gg;
+            cs.nh_xv[base + q] = uint64_t(x) | (uint64_t(uint32_t(NH.aux[sl])) << 32);
+            if (gg < h && bit_test(A.chg, gg)) continue;  // pair attributed elsewhere
+            if (atomicAdd(&cs.lcnt[gg], 1) == 0) cs.d_list[atomicAdd(&A.sc->n_d[A.side], 1)] = gg;
+            if ((fam & kFamV) && x >= 2)
+                acc.v2 += (unsigned long long)(x * (x - 1) / 2) * (unsigned long long)(kh + S.h_card[gg] - 4);
+        }
+        // a large N(h) also goes out as its hash table, probed by k_center
+        const bool big = uh > kBigNH;
+        if (big) {
+            const int64_t toff = base + uh;
+            for (uint32_t t = tid; t <= NH.mask; t += NT_NH) {
+                const int32_t key = NH.keys[t];
+                cs.nh_g[toff + t] = key;
+                if (key != EMPTY)
+                    cs.nh_xv[toff + t] = uint64_t(NH.vals[t]) | (uint64_t(uint32_t(NH.aux[t])) << 32);
+            }
+        }
+        if (tid == 0) {
+            cs.nh_n[i] = nn;
+            cs.nh_toff[i] = big ? base + uh : 0;
+            cs.nh_tcap[i] = big ? int32_t(NH.mask + 1) : 0;
+            if ((fam & kFamV) && kh >= 3) acc.v1 += (unsigned long long)kh * (kh - 1) * (kh - 2) / 6;
+        }
+        if (agg) {
+            // open triads centred at h, in aggregate over the pairs of N'(h)
+            // (N(h) without the neighbours attributed elsewhere): the class is
+            // set by E = [x1 + x2 = |h|] and by which of g1, g2 lie inside h.
+            // Closed pairs are counted here too and taken back by k_center.
+            uint32_t* H = kh <= kHistSmem ? &s.hx[0][0] : ghx;
+            const int hstride = kh <= kHistSmem ? kHistSmem + 1 : kMaxCard + 1;
+            unsigned long long n1w = 0, n0w = 0;
+            for (int q = tid; q < nn; q += NT_NH) {
+                const int sl = NH.list[q];
+                const int32_t gg = NH.keys[sl];
+                if (gg < h && bit_test(A.chg, gg)) continue;
+                const int x = int(NH.vals[sl]);
+                const int in = S.h_card[gg] == x ? 1 : 0;
+                atomicAdd(&H[in * hstride + x], 1u);
+                if (in) ++n1w; else ++n0w;
+            }
+            const long long n1 = block_sum<NT_NH>((long long)n1w, s.red);
+            const long long n0 = block_sum<NT_NH>((long long)n0w, s.red);
+            unsigned long long q00 = 0, q11 = 0, q01 = 0;
+            for (int x = 1 + tid; x < kh; x += NT_NH) {
+                const unsigned long long a0 = H[x], a1 = H[hstride + x];
+                const unsigned long long b0 = H[kh - x], b1 = H[hstride + kh - x];
+                q00 += a0 * b0;
+                q11 += a1 * b1;
+                q01 += a0 * b1;
+            }
+            q00 = (unsigned long long)block_sum<NT_NH>((long long)q00, s.red);
+            q11 = (unsigned long long)block_sum<NT_NH>((long long)q11, s.red);
+            q01 = (unsigned long long)block_sum<NT_NH>((long long)q01, s.red);
+            if (tid == 0) {
+                if ((kh & 1) == 0) {  // ordered pairs (g, g) with x = |h|/2
+                    q00 -= H[kh / 2];
+                    q11 -= H[hstride + kh / 2];
+                }
+                q00 /= 2;
+                q11 /= 2;
+                const unsigned long long p00 = (unsigned long long)n0 * (n0 - 1) / 2;
+                const unsigned long long p11 = (unsigned long long)n1 * (n1 - 1) / 2;
+                const unsigned long long p01 = (unsigned long long)n0 * n1;
+                // mask with E, s1 = [g1 inside h], s2 = [g2 inside h]
+                auto add = [&](int E, int s1, int s2, unsigned long long c) {
+                    if (!c) return;
+                    const int m = (E ? 0 : 1) | (s1 ? 0 : 2) | (s2 ? 0 : 4) | (1 << 3) | (1 << 5);
+                    s.acc[c_tables.cls30[m]] += c;
+                    acc.n_tri += c;
+                };
+                add(1, 0, 0, q00);
+                add(0, 0, 0, p00 - q00);
+                add(1, 1, 1, q11);
+                add(0, 1, 1, p11 - q11);
+                add(1, 0, 1, q01);
+                add(0, 0, 1, p01 - q01);
+            }
+            __syncthreads();
+            for (int q = tid; q < nn; q += NT_NH) {
+                const int sl = NH.list[q];
+                const int x = int(NH.vals[sl]);
+                H[x] = 0;
+                H[hstride + x] = 0;
+            }
+        }
+        __syncthreads();
+        tab_clear<NT_NH>(NH, nn);
+        __syncthreads();
+        if (tid == 0) s.n_list = 0;
+    }
+    __syncthreads();
+    if (cur_g >= 0) flush<NT_NH>(A, s.acc, nullptr, 0, cur_g, acc, s.red);
+    flush_stats<NT_NH>(A, acc, s.red);
+}
+
+// ---------------------------------------------------------------------------
+// 2. invert candidate pairs into L(g1)
+// ---------------------------------------------------------------------------
+
+__global__ void k_d_prep(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    const int nd = A.sc->n_d[A.side];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
+        const int c = cs.lcnt[cs.d_list[j]];
+        cs.d_cnt[j] = c;
+        cs.d_items[j] = (c + LCH - 1) / LCH;
+    }
+}
+
+__global__ void k_set_loffg(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    const int nd = A.sc->n_d[A.side];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x)
+        cs.loffg[cs.d_list[j]] = cs.d_loff[j];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.sc->items[A.side] = A.sc->gate ? 0 : cs.d_item_start[nd];
+        A.sc->queue[A.side] = 0;
+    }
+}
+
+__global__ void k_scatter(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = lane_id();
+    if (i >= A.n || A.sc->gate) return;
+    const int32_t h = A.changed[A.lo + i];
+    const int64_t base = cs.nh_off[i];
+    const int nn = cs.nh_n[i];
+    for (int q = lane; q < nn; q += 32) {
+        const int32_t gg = cs.nh_g[base + q];
+        if (gg < h && bit_test(A.chg, gg)) continue;
+        const int64_t pos = cs.loffg[gg] + atomicAdd(&cs.lfill[gg], 1);
+        cs.l_i[pos] = int32_t(i);
+        cs.l_xv[pos] = cs.nh_xv[base + q];
+    }
+}
+
+__global__ void k_d_clean(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    const int nd = A.sc->n_d[A.side];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
+        const int32_t g = cs.d_list[j];
+        cs.lcnt[g] = 0;
+        cs.lfill[g] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. centre kernel
+// ---------------------------------------------------------------------------
+
+struct SmemC {
+    Tables tb;
+    uint32_t hist[NW_C][128];
+    uint32_t hneg[NW_C][32];   // open-at-h classes taken back for closed pairs
+    unsigned long long acc[128];
+    int32_t keys[T1_S];
+    uint32_t vals[T1_S];
+    int32_t list[T1_S / 2];
+    int32_t lk[T1_S / 2];      // size of f, bit 31: f is changed
+    int64_t lts[T1_S / 2];     // timestamp of f
+    int64_t seg_off[NT_C];
+    int32_t seg_pre[NT_C + 1];
+    int warp_tmp[32];
+    long long red[NW_C];
+    long long item;
+    int n_list;
+    // aggregated open-at-centre counts (no temporal family): over the f of
+    // N(g1), totals by C = [f not inside g1] and a window of x = |g1 & f|
+    // values near |g1|; per h the subtracted buckets
+    uint32_t tot[2];
+    uint32_t win[kWin][2];
+    uint32_t sub[4];
+    uint32_t xcnt[2];
+    int n_cl;                  // changed f of N(g1) (slot, size) in the lts array
+};
+
+// t = |h & g1 & g2| from the smallest shared vertices (see the file comment).
+__device__ __forceinline__ int triple_size(int xh1, int32_t vf1, int xh2, int32_t vf2, const int32_t* g1mem,
+                                           int k1, const int32_t* g2mem, int k2, const int32_t* hmem, int kh) {
+    if (xh1 == 1 && xh2 == 1) return vf1 == vf2;
+    if (xh1 == 1) return contains_sorted(g2mem, k2, vf1);
+    if (xh2 == 1) return contains_sorted(g1mem, k1, vf2);
+    int t = 0;
+    const int32_t lo = vf1 > vf2 ? vf1 : vf2;
+    for (int q = 0; q < kh; ++q) {
+        const int32_t u = hmem[q];
+        if (u < lo) continue;
+        if (contains_sorted(g1mem, k1, u) && contains_sorted(g2mem, k2, u)) ++t;
+    }
+    return t;
+}
+
+__global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemC& s = *reinterpret_cast<SmemC*>(smem_raw);
+    const Store& S = A.S;
+    if (A.sc->gate) return;
+    const int tid = threadIdx.x;
+    const uint32_t fam = S.fam;
+    const int64_t delta = S.delta;
+    const bool want_open = (fam & (kFamH | kFamT)) != 0;
+    const bool want_t = (fam & kFamT) != 0;
+    // without the temporal family, the open triads {h, g1, f} centred at g1
+    // are counted in aggregate (see the (ii) comment below)
+    const bool agg = want_open && !want_t;
+    const CountScratch& cs = A.cs;
+    const int32_t* v2h = S.vp.arena;
+    const int32_t* h2v = S.hp.arena;
+    load_tables(s.tb, NT_C);
+    if (tid < 2) s.tot[tid] = s.xcnt[tid] = 0;
+    if (tid < 4) s.sub[tid] = 0;
+    for (int i = tid; i < kWin * 2; i += NT_C) s.win[i >> 1][i & 1] = 0;
+    if (tid == 0) s.n_cl = 0;
+    for (int i = tid; i < 128; i += NT_C) {
+        s.acc[i] = 0;
+        for (int w = 0; w < NW_C; ++w) s.hist[w][i] = 0;
+    }
+    for (int i = tid; i < NW_C * 32; i += NT_C) s.hneg[i / 32][i % 32] = 0;
+    for (int i = tid; i < T1_S; i += NT_C) {
+        s.keys[i] = EMPTY;
+        s.vals[i] = 0;
+    }
+    if (tid == 0) s.n_list = 0;
+    __syncthreads();
+    const int64_t gs = cs.gs_c;
+    int32_t* g_keys = cs.oc_keys + blockIdx.x * gs;
+    uint32_t* g_vals = cs.oc_vals + blockIdx.x * gs;
+    int32_t* g_list = cs.oc_list + blockIdx.x * (gs / 2);
+    int32_t* g_lk = cs.oc_lk + blockIdx.x * (gs / 2);
+    int64_t* g_lts = cs.oc_lts + blockIdx.x * (gs / 2);
+    uint32_t* hist = s.hist[warp_id()];
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t n_items = A.sc->items[A.side];
+    const int nd = A.sc->n_d[A.side];
+    int cur_g = -1;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s.item = (long long)atomicAdd(&A.sc->queue[A.side], 1ull);
+        __syncthreads();
+        const int64_t item = s.item;
+        if (item >= n_items) break;
+        const int64_t j = upper_bound_dev(cs.d_item_start, int64_t(nd) + 1, item) - 1;
+        const int64_t chunk = item - cs.d_item_start[j];
+        const int32_t g1 = cs.d_list[j];
+        const int64_t lbeg = cs.d_loff[j] + chunk * LCH;
+        const int64_t lend = min(lbeg + LCH, cs.d_loff[j + 1]);
+        const int g = A.changed_g ? A.changed_g[A.lo + cs.l_i[lbeg]] : 0;
+        if (g != cur_g) {
+            if (cur_g >= 0) flush<NT_C>(A, s.acc, s.hist, NW_C, cur_g, acc, s.red);
+            cur_g = g;
+        }
+        const int k1 = S.h_card[g1];
+        const int32_t* g1mem = h2v + S.h_off[g1];
+        const int64_t ts1 = S.h_ts[g1];
+        // size of N(g1) with repeats, to choose the table
+        long long u1 = 0;
+        for (int t = tid; t < k1; t += NT_C) u1 += S.v_deg[g1mem[t]];
+        u1 = block_sum<NT_C>(u1, s.red);
+        acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
+        // the method reads N(g1) (sum of member degrees) once per pair (h, g1)
+        if (tid == 0) acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)(lend - lbeg);
+        Tab T1;
+        int32_t* lk;
+        int64_t* lts;
+        int P = 1;
+        const uint32_t t1_cap = pow2_at_least(2 * u1);
+        if (t1_cap <= A.c_smem_cap) {
+            T1 = Tab{s.keys, s.vals, nullptr, s.list, &s.n_list, t1_cap - 1, T1_S / 2};
+            lk = s.lk;
+            lts = s.lts;
+        } else {
+            T1 = Tab{g_keys, g_vals, nullptr, g_list, &s.n_list, uint32_t(gs - 1), int(gs / 2)};
+            lk = g_lk;
+            lts = g_lts;
+            if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
+            else P = int((4 * u1 + gs - 1) / gs);
+        }
+        for (int p = 0; p < P; ++p) {
+            // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p)
+            for (int m0 = 0; m0 < k1; m0 += NT_C) {
+                const int n = min(NT_C, k1 - m0);
+                const int tot = load_segment<NT_C>(S, g1mem + m0, n, s.seg_off, nullptr, s.seg_pre, s.warp_tmp);
+                for (int e = tid; e < tot; e += NT_C) {
+                    const int m = seg_member(s.seg_pre, n, e);
+                    const int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
+                    if (f == g1) continue;
+                    if (P > 1 && part_of(f, P) != p) continue;
+                    tab_insert(T1, f, 1u, 0, A.sc);
+                }
+                acc.n_v2h += (tid < tot) ? (tot - tid + NT_C - 1) / NT_C : 0;
+                __syncthreads();
+            }
+            const int n1 = min(s.n_list, T1.list_cap);
+            // ---- what the per-h passes need of every f: size, changed flag,
+            //      time; in aggregate mode the totals, the x window and the
+            //      list of changed f
+            const int wlo = k1 - kWin;
+            for (int q0 = 0; q0 < n1; q0 += NT_C) {
+                const int q = q0 + tid;
+                int wkey = -1, C = 0;
+                bool changed_f = false;
+                if (q < n1) {
+                    const int sl = T1.list[q];
+                    const int32_t f = T1.keys[sl];
+                    const int kf = S.h_card[f];
+                    changed_f = bit_test(A.chg, f);
+                    lk[q] = kf | (changed_f ? int32_t(0x80000000u) : 0);
+                    if (want_t) lts[q] = S.h_ts[f];
+                    if (agg) {
+                        const int x = int(T1.vals[sl] & kXMask);
+                        C = kf > x ? 1 : 0;
+                        if (x >= wlo && x < k1) wkey = (x - wlo) * 2 + C;
+                        if (changed_f) {
+                            const int c = atomicAdd(&s.n_cl, 1);
+                            lts[c] = int64_t(uint32_t(sl)) | (int64_t(kf) << 32);
+                        }
+                    }
+                }
+                if (agg) {
+                    const unsigned in = __ballot_sync(0xffffffffu, q < n1);
+                    const unsigned c1 = __ballot_sync(0xffffffffu, q < n1 && C == 1);
+                    if (lane_id() == 0) {
+                        if (__popc(in & ~c1)) atomicAdd(&s.tot[0], __popc(in & ~c1));
+                        if (__popc(c1)) atomicAdd(&s.tot[1], __popc(c1));
+                    }
+                    const unsigned same = __match_any_sync(0xffffffffu, wkey);
+                    if (wkey >= 0 && lane_id() == __ffs(same) - 1)
+                        atomicAdd(&s.win[wkey >> 1][wkey & 1], __popc(same));
+                }
+            }
+            acc.n_meta += (tid < n1) ? (n1 - tid + NT_C - 1) / NT_C : 0;
+            __syncthreads();
+            const int n_cl = s.n_cl;
+            // ---- every changed h of this item
+            for (int64_t e = lbeg; e < lend; ++e) {
+                const int32_t li = cs.l_i[e];
+                const uint64_t xv1 = cs.l_xv[e];
+                const int xh1 = int(xv1 & kXMask);
+                const int32_t vf1 = int32_t(uint32_t(xv1 >> 32));
+                const int32_t h = A.changed[A.lo + li];
+                const int kh = S.h_card[h];
+                const int64_t tsh = S.h_ts[h];
+                const int32_t* hmem = h2v + S.h_off[h];
+                const int64_t nb0 = cs.nh_off[li];
+                const int nnh = cs.nh_n[li];
+                // bucket of an f of N(g1) for this h: B = [|g1 & f| != |g1| - |h & g1|],
+                // C = [f not inside g1]; 16-bit fields of a per-thread word
+                const int xstar = k1 - xh1;
+                unsigned long long subw = 0;
+                // (i) the pairs {g1, g2}, g2 in N(h).  Each g2 in N(g1) too (a
+                // closed pair) is marked in N(g1).  Counted at g1 < g2 unless
+                // g2 is a changed hyperedge of smaller ID than h.  In aggregate
+                // mode the open pairs were counted by k_nh_build, so only the
+                // closed ones are visited: from the smaller of N(h) and N(g1),
+                // probing the other's hash table.
+                const int32_t* g1m = g1mem;
+                const uint32_t* bits = A.chg;
+                auto closed_pair = [&](int32_t g2, int x12, int xh2, int32_t vf2, int k2, bool chg2) {
+                    if (agg) subw += 1ull << (16 * ((x12 != xstar ? 2 : 0) | (k2 > x12 ? 1 : 0)));
+                    if (g2 <= g1) return;
+                    if (g2 < h && chg2) return;
+                    ++acc.n_meta;
+                    const int t = triple_size(xh1, vf1, xh2, vf2, g1m, k1, h2v + S.h_off[g2], k2, hmem, kh);
+                    if (want_open) {
+                        const int64_t t2 = want_t ? S.h_ts[g2] : 0;
+                        classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, tsh, ts1, t2, acc);
+                    }
+                    if (agg) atomicAdd(&s.hneg[warp_id()][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
+                    if (fam & kFamV)
+                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 -
+                                  (unsigned long long)t * (xh1 + x12 + xh2) + 2ull * t;
+                };
+                const int tcap = cs.nh_tcap[li];
+                const bool from_g1 = agg && tcap > 0 && nnh > n1;
+                if (from_g1) {
+                    const int64_t toff = cs.nh_toff[li];
+                    const uint32_t tmask = uint32_t(tcap - 1);
+                    for (int q = tid; q < n1; q += NT_C) {
+                        const int sl = T1.list[q];
+                        const int32_t f = T1.keys[sl];
+                        uint32_t ps = fmix32(uint32_t(f)) & tmask;
+                        int found = -1;
+                        for (uint32_t probe = 0; probe <= tmask; ++probe) {
+                            const int32_t key = cs.nh_g[toff + ps];
+                            if (key == f) { found = int(ps); break; }
+                            if (key == EMPTY) break;
+                            ps = (ps + 1) & tmask;
+                        }
+                        if (found < 0) continue;
+                        atomicOr(&T1.vals[sl], kFlag);
+                        const uint64_t xv2 = cs.nh_xv[toff + found];
+                        const int32_t meta = lk[q];
+                        closed_pair(f, int(T1.vals[sl] & kXMask), int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)),
+                                    meta & 0x7fffffff, meta < 0);
+                    }
+                } else {
+                    for (int q = tid; q < nnh; q += NT_C) {
+                        const int32_t g2 = cs.nh_g[nb0 + q];
+                        if (P > 1 && part_of(g2, P) != p) continue;
+                        const int sl = tab_find(T1, g2);
+                        const uint64_t xv2 = cs.nh_xv[nb0 + q];
+                        const int xh2 = int(xv2 & kXMask);
+                        const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
+                        if (sl >= 0) {
+                            if (want_open) atomicOr(&T1.vals[sl], kFlag);
+                            closed_pair(g2, int(T1.vals[sl] & kXMask), xh2, vf2, S.h_card[g2], bit_test(bits, g2));
+                            continue;
+                        }
+                        if (agg || !want_open) continue;
+                        // open pair centred at h, enumerated (temporal family kept)
+                        if (g2 <= g1) continue;
+                        if (g2 < h && bit_test(bits, g2)) continue;
+                        ++acc.n_meta;
+                        const int k2 = S.h_card[g2];
+                        const int64_t t2 = want_t ? S.h_ts[g2] : 0;
+                        classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, 0, xh2, 0, tsh, ts1, t2, acc);
+                    }
+                }
+                if (!want_open) continue;
+                __syncthreads();
+                if (agg) {
+                    // (ii) in aggregate.  An open triad {h, g1, f} (f in N(g1),
+                    // f outside N(h), f != h) has regions h-only |h| - |h&g1|,
+                    // g1-only |g1| - |h&g1| - |g1&f|, f-only |f| - |g1&f|,
+                    // h&g1 and g1&f non-empty, the rest empty: its class is set
+                    // by A = [h not inside g1] and the bucket (B, C) of f.  The
+                    // buckets over all of N(g1) come from the totals and the
+                    // x window; subtracted are the f inside N(h) (marked in (i)),
+                    // f = h, and the changed f < h (attributed to f).
+                    for (int c = tid; c < n_cl; c += NT_C) {
+                        const int64_t v = lts[c];
+                        const int sl = int(uint32_t(v));
+                        const int32_t f = T1.keys[sl];
+                        if (f >= h) continue;
+                        const uint32_t val = T1.vals[sl];
+                        if (val & kFlag) continue;
+                        const int x = int(val & kXMask);
+                        subw += 1ull << (16 * ((x != xstar ? 2 : 0) | (int(v >> 32) > x ? 1 : 0)));
+                    }
+                    if (tid == 0 && (P == 1 || part_of(h, P) == p))
+                        subw += 1ull << (16 * ((xh1 != xstar ? 2 : 0) | (kh > xh1 ? 1 : 0)));
+                    unsigned long long xw = 0;
+                    if (xh1 > kWin) {  // outside the window: count x = xstar directly
+                        for (int q = tid; q < n1; q += NT_C) {
+                            const int sl = T1.list[q];
+                            if (int(T1.vals[sl] & kXMask) == xstar)
+                                xw += 1ull << (16 * ((lk[q] & 0x7fffffff) > xstar ? 1 : 0));
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        subw += __shfl_xor_sync(0xffffffffu, subw, o);
+                        xw += __shfl_xor_sync(0xffffffffu, xw, o);
+                    }
+                    if (lane_id() == 0) {
+                        for (int b = 0; b < 4; ++b)
+                            if ((subw >> (16 * b)) & 0xffff) atomicAdd(&s.sub[b], uint32_t((subw >> (16 * b)) & 0xffff));
+                        for (int c = 0; c < 2; ++c)
+                            if ((xw >> (16 * c)) & 0xffff) atomicAdd(&s.xcnt[c], uint32_t((xw >> (16 * c)) & 0xffff));
+                    }
+                    __syncthreads();
+                    if (tid == 0) {
+                        const int A_bit = kh > xh1 ? 1 : 0;
+                        for (int b = 0; b < 4; ++b) {
+                            const int B = b >> 1, C = b & 1;
+                            const uint32_t h0 = xh1 <= kWin ? s.win[kWin - xh1][C] : s.xcnt[C];
+                            const uint32_t total = B == 0 ? h0 : s.tot[C] - h0;
+                            const uint32_t n = total - s.sub[b];
+                            if (n) {
+                                const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
+                                s.acc[s.tb.cls30[m]] += n;
+                                acc.n_tri += n;
+                            }
+                            s.sub[b] = 0;
+                        }
+                        s.xcnt[0] = s.xcnt[1] = 0;
+                    }
+                    // unmark N(h)
+                    if (from_g1) {
+                        for (int q = tid; q < n1; q += NT_C) T1.vals[T1.list[q]] &= ~kFlag;
+                    } else {
+                        for (int q = tid; q < nnh; q += NT_C) {
+                            const int32_t g2 = cs.nh_g[nb0 + q];
+                            if (P > 1 && part_of(g2, P) != p) continue;
+                            const int sl = tab_find(T1, g2);
+                            if (sl >= 0) T1.vals[sl] &= ~kFlag;
+                        }
+                    }
+                    __syncthreads();
+                    continue;
+                }
+                // (ii) f in N(g1), not marked (not in N(h)), f != h: open at g1
+                for (int q = tid; q < n1; q += NT_C) {
+                    const int sl = T1.list[q];
+                    const uint32_t val = T1.vals[sl];
+                    if (val & kFlag) {
+                        T1.vals[sl] = val & ~kFlag;
+                        continue;
+                    }
+                    const int32_t f = T1.keys[sl];
+                    if (f == h) continue;
+                    const int32_t meta = lk[q];
+                    if (meta < 0 && f < h) continue;  // changed, smaller ID: attributed to f
+                    classify(s.tb, hist, fam, delta, h, g1, f, kh, k1, meta & 0x7fffffff, xh1, int(val & kXMask), 0, 0,
+                             tsh, ts1, want_t ? lts[q] : 0, acc);
+                }
+                __syncthreads();
+            }
+            __syncthreads();
+            tab_clear<NT_C>(T1, n1);
+            if (agg) {
+                if (tid < 2) s.tot[tid] = 0;
+                for (int i = tid; i < kWin * 2; i += NT_C) s.win[i >> 1][i & 1] = 0;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s.n_list = 0;
+                s.n_cl = 0;
+            }
+        }
+        // fold the warp histograms of this item
+        __syncthreads();
+        for (int b = tid; b < kHistN; b += NT_C) {
+            unsigned long long v = 0;
+            for (int w = 0; w < NW_C; ++w) {
+                v += s.hist[w][b];
+                s.hist[w][b] = 0;
+                if (b < 32) {
+                    v -= s.hneg[w][b];
+                    s.hneg[w][b] = 0;
+                }
+            }
+            s.acc[b] += v;
+        }
+    }
+    __syncthreads();
+    if (cur_g >= 0) flush<NT_C>(A, s.acc, s.hist, NW_C, cur_g, acc, s.red);
+    flush_stats<NT_C>(A, acc, s.red);
+}
+
+// ---------------------------------------------------------------------------
+// scans: host-known length, and device-known length (read from a counter)
+// ---------------------------------------------------------------------------
+
 constexpr int kScanNT = 1024, kScanPer = 4, kScanBlock = kScanNT * kScanPer;
 
-__global__ void k_scan_sums(const int32_t* in, int64_t n, int64_t* sums) {
+template <typename In>
+__global__ void k_scan_sums(const In* in, int64_t n_host, const int32_t* n_dev, int64_t* sums) {
     __shared__ int64_t red[kScanNT / 32];
-    int64_t base = int64_t(blockIdx.x) * kScanBlock;
+    const int64_t n = n_dev ? *n_dev : n_host;
+    const int64_t base = int64_t(blockIdx.x) * kScanBlock;
+    if (base >= n && blockIdx.x > 0) return;
     int64_t v = 0;
     for (int k = 0; k < kScanPer; ++k) {
         int64_t i = base + int64_t(threadIdx.x) * kScanPer + k;
@@ -589,20 +1010,31 @@ __global__ void k_scan_sums(const int32_t* in, int64_t n, int64_t* sums) {
     }
 }
 
-__global__ void k_scan_top(int64_t* sums, int64_t nb, int64_t* total_out) {
+__global__ void k_scan_top(int64_t* sums, int64_t nb_host, const int32_t* n_dev) {
     if (threadIdx.x != 0) return;
+    int64_t nb = nb_host;
+    if (n_dev) {
+        nb = (int64_t(*n_dev) + kScanBlock - 1) / kScanBlock;
+        if (nb < 1) nb = 1;
+    }
     int64_t run = 0;
     for (int64_t b = 0; b < nb; ++b) {
         int64_t v = sums[b];
         sums[b] = run;
         run += v;
     }
-    *total_out = run;
 }
 
-__global__ void k_scan_apply(const int32_t* in, int64_t n, const int64_t* sums, int64_t* out) {
+template <typename In>
+__global__ void k_scan_apply(const In* in, int64_t n_host, const int32_t* n_dev, const int64_t* sums, int64_t* out) {
     __shared__ int64_t wsum[kScanNT / 32];
-    int64_t base = int64_t(blockIdx.x) * kScanBlock;
+    const int64_t n = n_dev ? *n_dev : n_host;
+    const int64_t base = int64_t(blockIdx.x) * kScanBlock;
+    if (n == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+        return;
+    }
+    if (base >= n) return;
     int64_t loc[kScanPer];
     int64_t v = 0;
     for (int k = 0; k < kScanPer; ++k) {
@@ -636,50 +1068,98 @@ __global__ void k_scan_apply(const int32_t* in, int64_t n, const int64_t* sums, 
     }
 }
 
-__global__ void k_items_from_total(Scalars* sc, int side, const int64_t* item_start, int64_t n) {
-    sc->items[side] = sc->gate ? 0 : item_start[n];
+__global__ void k_run_begin(Scalars* sc, int side) {
+    sc->qnh[side] = 0;
     sc->queue[side] = 0;
+    sc->n_d[side] = 0;
+    sc->items[side] = 0;
 }
+
+inline unsigned blocks_for(int64_t n, int per) {
+    int64_t b = (n + per - 1) / per;
+    return unsigned(b < 1 ? 1 : b);
+}
+
+inline unsigned capped(unsigned b) { return b < 4096u ? b : 4096u; }
 
 }  // namespace
 
-size_t count_scratch_bytes(int64_t cap, int64_t g_slots, int n_cta) {
-    int64_t regions = int64_t(n_cta) * 2;
+size_t count_scratch_bytes(const CountShape& sh) {
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t b = 0;
-    b += (cap + 1) * sizeof(int32_t);
-    b += (cap + 2) * sizeof(int64_t);
-    b += ((cap + kScanBlock - 1) / kScanBlock + 2) * sizeof(int64_t);
-    b += regions * g_slots * (sizeof(int32_t) + sizeof(uint32_t) + sizeof(int32_t));
-    b += regions * (g_slots / 2) * sizeof(int32_t);
-    return b + 1024;
+    const int64_t nbs = (std::max(sh.cap, sh.e_cap) + kScanBlock - 1) / kScanBlock + 2;
+    b += al(sizeof(int32_t) * sh.cap) + al(sizeof(int64_t) * (sh.cap + 1)) + al(sizeof(int32_t) * sh.cap);
+    b += al(sizeof(int64_t) * sh.cap) + al(sizeof(int32_t) * sh.cap);
+    b += al(sizeof(uint32_t) * sh.n_cta_nh * 2 * (kMaxCard + 1));
+    b += 2 * (al(sizeof(int32_t) * sh.list_cap) + al(sizeof(uint64_t) * sh.list_cap));
+    b += 2 * al(sizeof(int32_t) * sh.e_cap) + al(sizeof(int64_t) * sh.e_cap);
+    b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
+    b += al(sizeof(int64_t) * nbs);
+    const int64_t rn = sh.n_cta_nh, rc = sh.n_cta_c;
+    b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
+    b += 2 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
+         al(sizeof(int64_t) * rc * (sh.gs_c / 2));
+    return b + 4096;
 }
 
-cudaError_t count_scratch_init(CountScratch* cs, void* mem, int64_t cap, int64_t g_slots, int n_cta,
+cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh, int64_t* pinned_word,
                                cudaStream_t st) {
-    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     char* p = static_cast<char*>(mem);
     size_t o = 0;
-    int64_t regions = int64_t(n_cta) * 2;
-    cs->cap = cap;
-    cs->g_slots = g_slots;
-    cs->n_cta = n_cta;
-    cs->chunks = reinterpret_cast<int32_t*>(p + o);
-    o = align(o + (cap + 1) * sizeof(int32_t));
-    cs->item_start = reinterpret_cast<int64_t*>(p + o);
-    o = align(o + (cap + 2) * sizeof(int64_t));
-    cs->block_sums = reinterpret_cast<int64_t*>(p + o);
-    o = align(o + ((cap + kScanBlock - 1) / kScanBlock + 2) * sizeof(int64_t));
-    cs->g_keys = reinterpret_cast<int32_t*>(p + o);
-    o = align(o + regions * g_slots * sizeof(int32_t));
-    cs->g_vals = reinterpret_cast<uint32_t*>(p + o);
-    o = align(o + regions * g_slots * sizeof(uint32_t));
-    cs->g_aux = reinterpret_cast<int32_t*>(p + o);
-    o = align(o + regions * g_slots * sizeof(int32_t));
-    cs->g_list = reinterpret_cast<int32_t*>(p + o);
+    auto take = [&](size_t bytes) {
+        void* r = p + o;
+        o += al(bytes);
+        return r;
+    };
+    const int64_t nbs = (std::max(sh.cap, sh.e_cap) + kScanBlock - 1) / kScanBlock + 2;
+    cs->cap = sh.cap;
+    cs->list_cap = sh.list_cap;
+    cs->e_cap = sh.e_cap;
+    cs->gs_nh = sh.gs_nh;
+    cs->gs_c = sh.gs_c;
+    cs->n_cta_nh = sh.n_cta_nh;
+    cs->n_cta_c = sh.n_cta_c;
+    cs->sizes = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
+    cs->nh_off = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.cap + 1)));
+    cs->nh_n = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
+    cs->nh_toff = static_cast<int64_t*>(take(sizeof(int64_t) * sh.cap));
+    cs->nh_tcap = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
+    cs->onh_hist = static_cast<uint32_t*>(take(sizeof(uint32_t) * sh.n_cta_nh * 2 * (kMaxCard + 1)));
+    cs->nh_g = static_cast<int32_t*>(take(sizeof(int32_t) * sh.list_cap));
+    cs->nh_xv = static_cast<uint64_t*>(take(sizeof(uint64_t) * sh.list_cap));
+    cs->l_i = static_cast<int32_t*>(take(sizeof(int32_t) * sh.list_cap));
+    cs->l_xv = static_cast<uint64_t*>(take(sizeof(uint64_t) * sh.list_cap));
+    cs->lcnt = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
+    cs->lfill = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
+    cs->loffg = static_cast<int64_t*>(take(sizeof(int64_t) * sh.e_cap));
+    cs->d_list = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
+    cs->d_cnt = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
+    cs->d_items = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
+    cs->d_loff = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.e_cap + 1)));
+    cs->d_item_start = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.e_cap + 1)));
+    cs->block_sums = static_cast<int64_t*>(take(sizeof(int64_t) * nbs));
+    cs->n_block_sums = nbs;
+    const int64_t rn = sh.n_cta_nh, rc = sh.n_cta_c;
+    cs->onh_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
+    cs->onh_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rn * sh.gs_nh));
+    cs->onh_aux = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
+    cs->onh_list = static_cast<int32_t*>(take(sizeof(int32_t) * rn * (sh.gs_nh / 2)));
+    cs->oc_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rc * sh.gs_c));
+    cs->oc_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rc * sh.gs_c));
+    cs->oc_list = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
+    cs->oc_lk = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
+    cs->oc_lts = static_cast<int64_t*>(take(sizeof(int64_t) * rc * (sh.gs_c / 2)));
+    cs->h_total = pinned_word;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(cs->g_keys, 0xff, regions * g_slots * sizeof(int32_t), st))) return e;
-    if ((e = cudaMemsetAsync(cs->g_vals, 0, regions * g_slots * sizeof(uint32_t), st))) return e;
-    if ((e = cudaMemsetAsync(cs->g_aux, 0x7f, regions * g_slots * sizeof(int32_t), st))) return e;
+    if ((e = cudaMemsetAsync(cs->lcnt, 0, sizeof(int32_t) * sh.e_cap, st))) return e;
+    if ((e = cudaMemsetAsync(cs->lfill, 0, sizeof(int32_t) * sh.e_cap, st))) return e;
+    if ((e = cudaMemsetAsync(cs->onh_hist, 0, sizeof(uint32_t) * sh.n_cta_nh * 2 * (kMaxCard + 1), st))) return e;
+    if ((e = cudaMemsetAsync(cs->onh_keys, 0xff, sizeof(int32_t) * rn * sh.gs_nh, st))) return e;
+    if ((e = cudaMemsetAsync(cs->onh_vals, 0, sizeof(uint32_t) * rn * sh.gs_nh, st))) return e;
+    if ((e = cudaMemsetAsync(cs->onh_aux, 0x7f, sizeof(int32_t) * rn * sh.gs_nh, st))) return e;
+    if ((e = cudaMemsetAsync(cs->oc_keys, 0xff, sizeof(int32_t) * rc * sh.gs_c, st))) return e;
+    if ((e = cudaMemsetAsync(cs->oc_vals, 0, sizeof(uint32_t) * rc * sh.gs_c, st))) return e;
     return cudaSuccess;
 }
 
@@ -693,32 +1173,73 @@ cudaError_t upload_tables(cudaStream_t st) {
     return cudaMemcpyToSymbolAsync(c_tables, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
 }
 
+static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
+                             const uint32_t* chg_bits, int64_t lo, int64_t n, int side, uint64_t* dcounts_side,
+                             const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
+    CountArgs A{S, sc, changed, changed_g, chg_bits, lo, n, side, dcounts_side, cs,
+                uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
+                uint32_t(cs.smem_slots < T1_S ? cs.smem_slots : T1_S)};
+    const unsigned gd = blocks_for(cs.e_cap, kScanBlock);
+    const unsigned ge = capped(blocks_for(cs.e_cap, 256));
+    k_run_begin<<<1, 1, 0, st>>>(sc, side);
+    k_nh_build<<<cs.n_cta_nh, NT_NH, sizeof(SmemNH), st>>>(A);
+    k_d_prep<<<ge, 256, 0, st>>>(A);
+    k_scan_sums<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_cnt, 0, &sc->n_d[side], cs.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, 0, &sc->n_d[side]);
+    k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_cnt, 0, &sc->n_d[side], cs.block_sums, cs.d_loff);
+    k_scan_sums<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, 0, &sc->n_d[side]);
+    k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
+    k_set_loffg<<<ge, 256, 0, st>>>(A);
+    k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
+    k_center<<<cs.n_cta_c, NT_C, sizeof(SmemC), st>>>(A);
+    k_d_clean<<<ge, 256, 0, st>>>(A);
+    lc.total += 13;
+    lc.count += 2;
+    return cudaGetLastError();
+}
+
 cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                          const uint32_t* chg_bits, int64_t lo, int64_t hi, int side, uint64_t* dcounts_side,
                          const CountScratch& cs, int64_t max_u, cudaStream_t st, LaunchCounter& lc) {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_count, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(Smem)));
+        cudaFuncSetAttribute(k_nh_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemNH)));
+        cudaFuncSetAttribute(k_center, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemC)));
         attr_done = true;
     }
-    int64_t n = hi - lo;
-    if (n <= 0) return cudaSuccess;
-    if (n > cs.cap) return cudaErrorInvalidValue;
-    unsigned gb = unsigned((n * 32 + 255) / 256);
-    k_chunks<<<gb, 256, 0, st>>>(S, sc, changed, lo, n, cs.chunks, max_u);
-    int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_sums<<<unsigned(nb), kScanNT, 0, st>>>(cs.chunks, n, cs.block_sums);
-    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, nb, cs.block_sums + nb);
-    k_scan_apply<<<unsigned(nb), kScanNT, 0, st>>>(cs.chunks, n, cs.block_sums, cs.item_start);
-    k_items_from_total<<<1, 1, 0, st>>>(sc, side, cs.item_start, n);
-    CountArgs A{S, sc, changed, changed_g, chg_bits, lo, hi, cs.item_start, side, dcounts_side,
-                cs.g_keys, cs.g_vals, cs.g_aux, cs.g_list, cs.g_slots,
-                uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
-                uint32_t(cs.smem_slots < T1_S ? cs.smem_slots : T1_S)};
-    k_count<<<cs.n_cta, NT, sizeof(Smem), st>>>(A);
-    lc.total += 6;
-    lc.count += 1;
-    return cudaGetLastError();
+    for (int64_t a = lo; a < hi; a += cs.cap) {
+        const int64_t b = a + cs.cap < hi ? a + cs.cap : hi;
+        const int64_t n = b - a;
+        // sizes of N(h) and the prefix that places every list
+        k_nh_size<<<blocks_for(n * 32, 256), 256, 0, st>>>(S, sc, changed, a, n, cs.sizes, max_u);
+        const unsigned gb = blocks_for(n, kScanBlock);
+        k_scan_sums<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, n, nullptr, cs.block_sums);
+        k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gb, nullptr);
+        k_scan_apply<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, n, nullptr, cs.block_sums, cs.nh_off);
+        lc.total += 4;
+        cudaError_t e = cudaMemcpyAsync(cs.h_total, cs.nh_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (*cs.h_total <= cs.list_cap) {
+            if ((e = count_run(S, sc, changed, changed_g, chg_bits, a, n, side, dcounts_side, cs, st, lc))) return e;
+            continue;
+        }
+        // the lists do not fit: split [a, b) by the prefix of the sizes
+        std::vector<int64_t> pre(size_t(n) + 1);
+        if ((e = cudaMemcpy(pre.data(), cs.nh_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost))) return e;
+        int64_t s0 = 0;
+        while (s0 < n) {
+            int64_t s1 = s0;
+            while (s1 < n && pre[s1 + 1] - pre[s0] <= cs.list_cap) ++s1;
+            if (s1 == s0) return cudaErrorInvalidValue;  // one list alone exceeds the capacity
+            if ((e = count_launch(S, sc, changed, changed_g, chg_bits, a + s0, a + s1, side, dcounts_side, cs,
+                                  max_u, st, lc)))
+                return e;
+            s0 = s1;
+        }
+    }
+    return cudaSuccess;
 }
 
 }  // namespace esc

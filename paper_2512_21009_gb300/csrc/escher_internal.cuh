@@ -68,8 +68,10 @@ struct Scalars {
     int32_t need_h[kNumClasses];
     int32_t freed_h[kNumClasses];
     int32_t need_v[kNumClasses];
-    unsigned long long queue[2];  // count work queues (deleted side, inserted side)
-    int64_t items[2];     // count work items
+    unsigned long long queue[2];  // centre work queues (deleted side, inserted side)
+    unsigned long long qnh[2];    // neighbourhood-build queues
+    int64_t items[2];     // centre work items
+    int32_t n_d[2];       // distinct candidate neighbours g1 of one count run
     unsigned long long stats[8];  // v2h reads, h2v reads, meta reads, triads
 };
 

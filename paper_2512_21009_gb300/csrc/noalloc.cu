@@ -26,12 +26,25 @@ namespace esc {
 
 namespace {
 
-constexpr int64_t kNAMaxHyperedges = int64_t(1) << 19;
-constexpr int64_t kNAMaxIncidences = int64_t(1) << 22;
-constexpr int64_t kNAMaxVertices = int64_t(1) << 20;
-constexpr int kNABlocks = 152;          // counter blocks
-constexpr int64_t kNATableSlots = 4096; // per counter overflow table
+constexpr int64_t kNAMaxHyperedges = int64_t(1) << 18;
+constexpr int64_t kNAMaxIncidences = int64_t(1) << 21;
+constexpr int64_t kNAMaxVertices = int64_t(1) << 19;
+constexpr int kNABlocks = 152;          // blocks of each counting kernel
+constexpr int64_t kNATableSlots = 2048; // per counter overflow table
+constexpr int64_t kNAListEntries = int64_t(1) << 19;  // neighbour-list entries per counting run
 constexpr size_t kNoAllocBytes = size_t(80) << 20;
+
+CountShape na_shape() {
+    CountShape sh;
+    sh.cap = kNAMaxHyperedges;
+    sh.list_cap = kNAListEntries;
+    sh.e_cap = kNAMaxHyperedges;
+    sh.gs_nh = sh.gs_c = kNATableSlots;
+    sh.n_cta_nh = sh.n_cta_c = kNABlocks;
+    return sh;
+}
+
+thread_local int64_t t_word;  // host word the counter reads back (pageable: no allocation)
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -58,7 +71,7 @@ Layout layout() {
     L.vdeg = o;    o = align256(o + sizeof(int32_t) * kNAMaxVertices);
     L.vfill = o;   o = align256(o + sizeof(int32_t) * kNAMaxVertices);
     L.v2h = o;     o = align256(o + sizeof(int32_t) * kNAMaxIncidences);
-    L.count = o;   o = align256(o + count_scratch_bytes(kNAMaxHyperedges, kNATableSlots, kNABlocks));
+    L.count = o;   o = align256(o + count_scratch_bytes(na_shape()));
     L.total = o;
     return L;
 }
@@ -154,8 +167,8 @@ extern "C" esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he,
     if (!on_device(offsets) || !on_device(out_counts) || (n_he > 0 && !on_device(members)) ||
         (timestamps && !on_device(timestamps)))
         return na_fail(ESC_ERR_INVALID_ARG, "inputs and output must be device memory");
-    if (n_he > kNAMaxHyperedges) return na_fail(ESC_ERR_UNSUPPORTED, "more than 524,288 hyperedges");
-    if (n_vertices > kNAMaxVertices) return na_fail(ESC_ERR_UNSUPPORTED, "more than 1,048,576 vertices");
+    if (n_he > kNAMaxHyperedges) return na_fail(ESC_ERR_UNSUPPORTED, "more than 262,144 hyperedges");
+    if (n_vertices > kNAMaxVertices) return na_fail(ESC_ERR_UNSUPPORTED, "more than 524,288 vertices");
     static_assert(sizeof(Scalars) < 4096, "layout");
     const Layout L = layout();
     if (L.total > kNoAllocBytes) return na_fail(ESC_ERR_UNSUPPORTED, "internal layout exceeds the scratch array");
@@ -188,7 +201,7 @@ extern "C" esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he,
             cudaStreamSynchronize(st) != cudaSuccess)
             return na_fail(ESC_ERR_CUDA, "reading offsets failed");
         if (first != 0 || nnz < 0) return na_fail(ESC_ERR_INVALID_ARG, "offsets must start at 0");
-        if (nnz > kNAMaxIncidences) return na_fail(ESC_ERR_UNSUPPORTED, "more than 4,194,304 incidences");
+        if (nnz > kNAMaxIncidences) return na_fail(ESC_ERR_UNSUPPORTED, "more than 2,097,152 incidences");
     }
     Scalars* sc = reinterpret_cast<Scalars*>(base + L.sc);
     uint64_t* dc = reinterpret_cast<uint64_t*>(base + L.dc);
@@ -209,7 +222,7 @@ extern "C" esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he,
     ok(cudaMemsetAsync(chg, 0xff, size_t((n_he + 31) / 32) * 4, st));
     if (!timestamps) ok(cudaMemsetAsync(tsz, 0, sizeof(int64_t) * (n_he > 0 ? n_he : 1), st));
     CountScratch cs;
-    ok(count_scratch_init(&cs, base + L.count, kNAMaxHyperedges, kNATableSlots, kNABlocks, st));
+    ok(count_scratch_init(&cs, base + L.count, na_shape(), &t_word, st));
     ok(upload_tables(st));
     if (e != cudaSuccess) return na_fail(ESC_ERR_CUDA, cudaGetErrorString(e));
     LaunchCounter lc;
@@ -232,7 +245,7 @@ extern "C" esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he,
         S.v_deg = vdeg;
         S.hp.arena = const_cast<int32_t*>(members);
         S.vp.arena = v2h;
-        ok(count_launch(S, sc, changed, nullptr, chg, 0, n_he, 1, dc, cs, count_max_u(kNATableSlots), st, lc));
+        ok(count_launch(S, sc, changed, nullptr, chg, 0, n_he, 1, dc, cs, count_max_u(na_shape()), st, lc));
     }
     k_na_out<<<1, 160, 0, st>>>(dc, out_counts, sc);
     ok(cudaGetLastError());

@@ -20,34 +20,77 @@ cudaError_t store_finish(const Store& S, const Call& C, int sm_count, cudaStream
 
 // count.cu
 struct CountScratch {
-    int32_t* chunks = nullptr;       // [cap]
-    int64_t* item_start = nullptr;   // [cap+1]
+    // per changed hyperedge of one run
+    int64_t cap = 0;                 // changed hyperedges per run
+    int32_t* sizes = nullptr;        // [cap] sum of member degrees (entries of N(h) with repeats)
+    int64_t* nh_off = nullptr;       // [cap+1] start of each N(h) list
+    int32_t* nh_n = nullptr;         // [cap] length of each N(h) list
+    int64_t* nh_toff = nullptr;      // [cap] start of the hash table of a large N(h)
+    int32_t* nh_tcap = nullptr;      // [cap] its slots (0: no table)
+    // neighbour lists N(h) and the inverted candidate lists L(g1)
+    int64_t list_cap = 0;            // entries
+    int32_t* nh_g = nullptr;         // [list_cap] neighbour g
+    uint64_t* nh_xv = nullptr;       // [list_cap] |h & g| (low 16 bits), smallest shared vertex (high 32)
+    int32_t* l_i = nullptr;          // [list_cap] index of h in the run
+    uint64_t* l_xv = nullptr;        // [list_cap] as nh_xv
+    // per hyperedge ID
+    int64_t e_cap = 0;
+    int32_t* lcnt = nullptr;         // [e_cap] candidate pairs (g1, .) per g1; zero between runs
+    int32_t* lfill = nullptr;        // [e_cap]
+    int64_t* loffg = nullptr;        // [e_cap] start of L(g1)
+    int32_t* d_list = nullptr;       // [e_cap] distinct g1 of the run
+    int32_t* d_cnt = nullptr;        // [e_cap] |L(d_list[j])|
+    int32_t* d_items = nullptr;      // [e_cap] work items of d_list[j]
+    int64_t* d_loff = nullptr;       // [e_cap+1]
+    int64_t* d_item_start = nullptr; // [e_cap+1]
     int64_t* block_sums = nullptr;   // scan scratch
-    int64_t cap = 0;                 // changed hyperedges per count launch
-    int32_t* g_keys = nullptr;       // per-CTA overflow hash tables (2 per CTA)
-    uint32_t* g_vals = nullptr;
-    int32_t* g_aux = nullptr;
-    int32_t* g_list = nullptr;
-    int64_t g_slots = 0;             // slots of one overflow table
-    int n_cta = 0;                   // persistent grid of the counter
+    int64_t n_block_sums = 0;
+    // per-block overflow hash tables
+    int n_cta_nh = 0, n_cta_c = 0;   // persistent grids of the two counting kernels
+    int64_t gs_nh = 0, gs_c = 0;     // slots of one overflow table
+    int32_t* onh_keys = nullptr;
+    uint32_t* onh_vals = nullptr;
+    int32_t* onh_aux = nullptr;
+    int32_t* onh_list = nullptr;
+    uint32_t* onh_hist = nullptr;    // per block: x histograms for |h| above the shared-memory limit
+    int32_t* oc_keys = nullptr;
+    uint32_t* oc_vals = nullptr;
+    int32_t* oc_list = nullptr;
+    int32_t* oc_lk = nullptr;
+    int64_t* oc_lts = nullptr;
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
+    int64_t* h_total = nullptr;      // pinned host word for the list total
+};
+
+struct CountShape {
+    int64_t cap;        // changed hyperedges per run
+    int64_t list_cap;   // N(h) entries per run
+    int64_t e_cap;      // hyperedge IDs of the store
+    int64_t gs_nh, gs_c;
+    int n_cta_nh, n_cta_c;
 };
 
 // Largest neighbour-entry count sum(deg) of a changed hyperedge the counter
-// accepts with the given overflow table size.
-inline int64_t count_max_u(int64_t g_slots) { return g_slots / 2; }
+// accepts with the given shape.
+inline int64_t count_max_u(const CountShape& sh) {
+    int64_t a = sh.gs_nh / 2;
+    return a < sh.list_cap / 8 ? a : sh.list_cap / 8;
+}
 
-size_t count_scratch_bytes(int64_t cap, int64_t g_slots, int n_cta);
-cudaError_t count_scratch_init(CountScratch* cs, void* mem, int64_t cap, int64_t g_slots, int n_cta,
+size_t count_scratch_bytes(const CountShape& sh);
+cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh, int64_t* pinned_word,
                                cudaStream_t st);
 cudaError_t upload_tables(cudaStream_t st);
 
 // Count, for every family of the store, the triads of the current graph that
 // hold at least one of the changed hyperedges, attributing each triad to its
 // changed member of smallest ID, into dcounts_side[g][...] of each graph g.
-// changed[i] / changed_g[i]: global ID and graph of changed hyperedge i;
-// chg_bits marks every changed ID (also those outside [lo, hi)).  Only
-// changed[lo, hi) are enumerated by this launch.  side selects the work queue.
+// changed[i] / changed_g[i]: global ID and graph of changed hyperedge i
+// (changed_g may be null: graph 0); chg_bits marks every changed ID (also
+// those outside [lo, hi)).  Only changed[lo, hi) are enumerated by this call.
+// side selects the work queues.  The call reads one word back from the
+// device (the size of the neighbour lists) and splits [lo, hi) when the lists
+// would not fit.
 cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                          const uint32_t* chg_bits, int64_t lo, int64_t hi, int side, uint64_t* dcounts_side,
                          const CountScratch& cs, int64_t max_u, cudaStream_t st, LaunchCounter& lc);

@@ -55,7 +55,7 @@ class esc_batch_stats(C.Structure):
     _fields_ = [("ms_total", C.c_float), ("ms_ingest", C.c_float), ("ms_count_del", C.c_float),
                 ("ms_store", C.c_float), ("ms_count_ins", C.c_float), ("launches", C.c_int64),
                 ("count_launches", C.c_int64), ("v2h_reads", C.c_int64), ("h2v_reads", C.c_int64),
-                ("meta_reads", C.c_int64), ("triads", C.c_int64)]
+                ("meta_reads", C.c_int64), ("triads", C.c_int64), ("alg_entries", C.c_int64)]
 
 
 class esc_batch(C.Structure):

@@ -47,12 +47,13 @@ def test_device_resident_inputs(E):
     run_stream(E, s, ALL, 1 << 60, device=torch.device("cuda:0"))
 
 
-def test_zipf_cards_and_hub_vertices(E):
+@pytest.mark.parametrize("families", [ALL, 3])
+def test_zipf_cards_and_hub_vertices(E, families):
     """Zipf(2) cardinalities up to 100 (the block sorter path) and Zipf(1.1)
     vertex popularity (hubs)."""
     s = gen.random_small(5, 600, 220, 2, 100, n_batches=2, n_ins=25, n_del=25,
                          membership="zipf", card="zipf")
-    run_stream(E, s, ALL, 1 << 60)
+    run_stream(E, s, families, 1 << 60)
 
 
 def test_repeated_members_ties_and_identical_sets(E):
@@ -80,7 +81,8 @@ def test_repeated_members_ties_and_identical_sets(E):
     assert_store_equal(g, og)
 
 
-def test_large_neighbourhoods_use_global_tables(E):
+@pytest.mark.parametrize("families", [ALL, 3])
+def test_large_neighbourhoods_use_global_tables(E, families):
     """A hyperedge meeting more than the shared-memory tables hold: N(h) and
     N(g1) go to the per-block global tables."""
     rng = np.random.default_rng(7)
@@ -92,17 +94,18 @@ def test_large_neighbourhoods_use_global_tables(E):
     off[1:] = np.cumsum([len(e) for e in edges])
     mem = np.array([v for e in edges for v in e], np.int32)
     og = OracleHypergraph(nv, off, mem, np.arange(len(edges)))
-    g = E.Graph(nv, off, mem, np.arange(len(edges)), families=ALL, delta=1 << 40,
+    g = E.Graph(nv, off, mem, np.arange(len(edges)), families=families, delta=1 << 40,
                 **caps_for(nv, 4000, 40000, 2000, 40000))
-    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), "initial")
+    assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "initial")
     # delete and re-insert the big hyperedge
     ids_o = og.apply_batch(np.array([0, 600]), np.array(big), np.array([7]), np.array([0]))
     ids_g = g.apply_batch(np.array([0, 600]), np.array(big, np.int32), np.array([7]), np.array([0], np.int32))
     assert np.array_equal(ids_g, ids_o)
-    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), "after")
+    assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "after")
 
 
-def test_multi_pass_and_global_tables(E, monkeypatch):
+@pytest.mark.parametrize("families", [ALL, 3])
+def test_multi_pass_and_global_tables(E, monkeypatch, families):
     """Small table limits force the global tables and the partitioned
     (multi-pass) N(g1) build: an unchanged hyperedge B whose vertices gain
     degree becomes a neighbour with more entries than one table holds."""
@@ -117,8 +120,8 @@ def test_multi_pass_and_global_tables(E, monkeypatch):
     mem = np.array([v for e in edges for v in e], np.int32)
     ts = np.arange(len(edges), dtype=np.int64)
     og = OracleHypergraph(nv, off, mem, ts)
-    g = E.Graph(nv, off, mem, ts, families=ALL, delta=1 << 40, **caps_for(nv, 2000, 20000, 1000, 20000))
-    assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), "initial")
+    g = E.Graph(nv, off, mem, ts, families=families, delta=1 << 40, **caps_for(nv, 2000, 20000, 1000, 20000))
+    assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "initial")
     for step in range(3):
         ins = [[B[(7 * j + step) % 60], int(rng.integers(0, nv))] for j in range(120)]
         ins = [sorted(set(e)) for e in ins]
@@ -130,7 +133,7 @@ def test_multi_pass_and_global_tables(E, monkeypatch):
         ids_o = og.apply_batch(ioff, imem, its, dels)
         ids_g = g.apply_batch(ioff, imem, its, dels.astype(np.int32))
         assert np.array_equal(ids_g, ids_o)
-        assert_counts_equal(g.counts(), O.counts(og, ALL, 1 << 40), f"step {step}")
+        assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), f"step {step}")
     assert_store_equal(g, og)
 
 
@@ -290,3 +293,35 @@ def test_temporal_stream_with_expirations(E):
         assert np.array_equal(ids_g, ids_o)
         live.apply(dels_g, ids_g, b.timestamps)
         assert_counts_equal(g.counts(), O.counts(og, ALL, delta), f"batch {k}")
+
+
+@pytest.mark.parametrize("families", [ALL, 3])
+def test_large_overlaps(E, families):
+    """Pairs of hyperedges sharing more than 64 vertices (outside the
+    aggregated counter's histogram window) and nested hyperedges."""
+    rng = np.random.default_rng(14)
+    nv = 500
+    edges = []
+    for _ in range(12):
+        core = sorted(rng.choice(nv, size=150, replace=False).tolist())
+        edges.append(core)
+        edges.append(sorted(set(core[:100]) | set(rng.choice(nv, size=20).tolist())))
+        edges.append(core[10:90])
+    edges += [sorted(rng.choice(nv, size=rng.integers(2, 8), replace=False).tolist()) for _ in range(150)]
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    ts = np.arange(len(edges), dtype=np.int64)
+    og = OracleHypergraph(nv, off, mem, ts)
+    g = E.Graph(nv, off, mem, ts, families=families, delta=1 << 40, **caps_for(nv, 600, 20000, 400, 20000))
+    assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "initial")
+    dels = np.array([0, 4, 8, 40, 41, 100], np.int64)
+    ins = [list(range(0, 120)), list(range(50, 130)), [1, 2, 3]]
+    ioff = np.zeros(len(ins) + 1, np.int64)
+    ioff[1:] = np.cumsum([len(e) for e in ins])
+    imem = np.array([v for e in ins for v in e], np.int32)
+    its = np.array([500, 501, 502], np.int64)
+    ids_o = og.apply_batch(ioff, imem, its, dels)
+    ids_g = g.apply_batch(ioff, imem, its, dels.astype(np.int32))
+    assert np.array_equal(ids_g, ids_o)
+    assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "after")

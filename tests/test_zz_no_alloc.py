@@ -60,7 +60,7 @@ def test_noalloc_matches_allocating_entry_point_twice(E):
 def test_noalloc_rejects_sizes_beyond_its_limit(E):
     import torch
     dev = torch.device("cuda:0")
-    n = (1 << 19) + 1
+    n = (1 << 18) + 1
     off = torch.arange(n + 1, dtype=torch.int64, device=dev)
     mem = torch.zeros(n, dtype=torch.int32, device=dev)
     out = torch.zeros(129, dtype=torch.int64, device=dev)
