@@ -216,6 +216,7 @@ def run_ours(args):
     clocks.start()
     launches0 = g.launch_count()
     lat, cnt_ms, store_ms, alg_bytes, triads = [], [], [], 0, 0
+    work = [0] * 6
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -229,6 +230,7 @@ def run_ours(args):
         store_ms.append(sts["ms_ingest"] + sts["ms_store"])
         alg_bytes += 4 * sts["alg_entries"]
         triads += sts["triads"]
+        work = [a + b for a, b in zip(work, sts["work"])]
     e1.record(st)
     torch.cuda.synchronize(dev)
     launches = g.launch_count() - launches0
@@ -288,6 +290,9 @@ def run_ours(args):
         "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
         "stage_ms_per_step": {"count": sum(cnt_ms) / len(cnt_ms), "store_and_ingest": sum(store_ms) / len(store_ms)},
         "triads_per_step": triads / args.steps,
+        "counter_work_per_step": {k: v / args.steps for k, v in zip(
+            ["centre_items", "n_g1_build_entries", "pair_pass_visits", "closed_pairs", "slow_t_steps",
+             "aggregate_visits"], work)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": kind,
                      "kernel": "triad count (k_nh_build + k_center and their work lists), per batch",

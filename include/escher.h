@@ -200,6 +200,9 @@ typedef struct {
                                 |h| + sum of its members' degrees, plus, for
                                 each candidate neighbour g1 of h, |g1| + sum
                                 of g1's members' degrees                      */
+    int64_t work[6];         /* counter work: centre items, N(g1) build entries,
+                                pair-pass visits, closed pairs, slow-path
+                                triple-intersection steps, aggregate-pass visits */
 } esc_batch_stats;
 
 esc_status esc_set_profiling(esc_graph* g, int32_t on);

@@ -435,6 +435,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     E->last.meta_reads = int64_t(E->h_sc->stats[2]);
     E->last.triads = int64_t(E->h_sc->stats[3]);
     E->last.alg_entries = int64_t(E->h_sc->stats[4]);
+    for (int k = 0; k < 6; ++k) E->last.work[k] = int64_t(E->h_sc->stats[5 + k]);
     if (E->h_sc->status != 0) {
         E->err = describe(*E->h_sc);
         return esc_status(E->h_sc->status);

@@ -51,7 +51,6 @@ namespace {
 constexpr int32_t EMPTY = -1;
 constexpr int kHistT = kNH;          // temporal bins start here in the shared histograms
 constexpr int kHistN = kNH + kNT;
-constexpr uint32_t kFlag = 0x80000000u;  // "also in N(h)" mark in N(g1) values
 constexpr uint32_t kXMask = 0xffffu;
 
 // neighbourhood build
@@ -64,6 +63,7 @@ constexpr int T1_S = 8192;           // shared-memory N(g1) table slots
 constexpr int LCH = 32;              // changed hyperedges per centre work item
 constexpr int kWin = 64;             // |h & g1| values served from the histogram window
 constexpr int kBigNH = 512;          // N(h) with more entries also gets a hash table in the lists
+constexpr int kIC = 32;              // |h & g1| up to which h & g1 is listed for the triple sizes
 constexpr int kHistSmem = 1024;      // |h| up to which the open-at-h histograms live in shared memory
 
 __constant__ ClassTables c_tables;
@@ -205,6 +205,7 @@ __device__ __forceinline__ int seg_member(const int32_t* pre, int n, int e) {
 struct Accum {
     unsigned long long v1, v2, v3;
     unsigned long long n_v2h, n_h2v, n_meta, n_tri, n_alg;
+    unsigned long long w[6];  // items, build entries, pair visits, closed pairs, slow t steps, agg visits
 };
 
 struct Tables {
@@ -297,7 +298,11 @@ __device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
     long long r2 = block_sum<NT>((long long)acc.n_meta, red);
     long long r3 = block_sum<NT>((long long)acc.n_tri, red);
     long long r4 = block_sum<NT>((long long)acc.n_alg, red);
+    long long wk[6];
+    for (int k = 0; k < 6; ++k) wk[k] = block_sum<NT>((long long)acc.w[k], red);
     if (threadIdx.x == 0) {
+        for (int k = 0; k < 6; ++k)
+            if (wk[k]) atomicAdd(&A.sc->stats[5 + k], (unsigned long long)wk[k]);
         atomicAdd(&A.sc->stats[0], (unsigned long long)r0);
         atomicAdd(&A.sc->stats[1], (unsigned long long)r1);
         atomicAdd(&A.sc->stats[2], (unsigned long long)r2);
@@ -383,7 +388,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
     const int64_t gs = cs.gs_nh;
     Tab gNH{cs.onh_keys + blockIdx.x * gs, cs.onh_vals + blockIdx.x * gs, cs.onh_aux + blockIdx.x * gs,
             cs.onh_list + blockIdx.x * (gs / 2), &s.n_list, uint32_t(gs - 1), int(gs / 2)};
-    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0};
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
     int cur_g = -1;
     const int32_t* v2h = S.vp.arena;
     for (;;) {
@@ -598,9 +603,10 @@ struct SmemC {
     unsigned long long acc[128];
     int32_t keys[T1_S];
     uint32_t vals[T1_S];
+    uint32_t mark[T1_S];       // bit l: the entry is in N(h) of the item's l-th h
     int32_t list[T1_S / 2];
     int32_t lk[T1_S / 2];      // size of f, bit 31: f is changed
-    int64_t lts[T1_S / 2];     // timestamp of f
+    int64_t lts[T1_S / 2];     // timestamp of f; in aggregate mode the changed f as (slot, size)
     int64_t seg_off[NT_C];
     int32_t seg_pre[NT_C + 1];
     int warp_tmp[32];
@@ -609,21 +615,38 @@ struct SmemC {
     int n_list;
     // aggregated open-at-centre counts (no temporal family): over the f of
     // N(g1), totals by C = [f not inside g1] and a window of x = |g1 & f|
-    // values near |g1|; per h the subtracted buckets
+    // values near |g1|
     uint32_t tot[2];
     uint32_t win[kWin][2];
-    uint32_t sub[4];
-    uint32_t xcnt[2];
-    int n_cl;                  // changed f of N(g1) (slot, size) in the lts array
+    int n_cl;
+    // the changed hyperedges h of the item
+    int32_t hh[LCH], hk[LCH], hx[LCH], hvf[LCH], hli[LCH], hnn[LCH], htcap[LCH];
+    int64_t hts[LCH], hnb[LCH], htoff[LCH];
+    const int32_t* hmem[LCH];
+    int32_t hfrom[LCH];        // 1: visit N(g1) probing N(h)'s table, 0: visit N(h)
+    int32_t hpre[LCH + 1];     // prefix of the per-h work of pass (i)
+    uint32_t sub[LCH][4];
+    uint32_t xc[LCH][2];
+    int32_t hI[LCH][kIC];      // h & g1 when 2 <= |h & g1| <= kIC
+    int hIn[LCH];
 };
 
-// t = |h & g1 & g2| from the smallest shared vertices (see the file comment).
+// t = |h & g1 & g2| from the smallest shared vertices (see the file comment);
+// when both |h & g1| and |h & g2| exceed 1, the listed h & g1 (hI, nI
+// entries) is tested against g2, else every member of h.
 __device__ __forceinline__ int triple_size(int xh1, int32_t vf1, int xh2, int32_t vf2, const int32_t* g1mem,
-                                           int k1, const int32_t* g2mem, int k2, const int32_t* hmem, int kh) {
+                                           int k1, const int32_t* g2mem, int k2, const int32_t* hmem, int kh,
+                                           const int32_t* hI, int nI, unsigned long long& slow) {
     if (xh1 == 1 && xh2 == 1) return vf1 == vf2;
     if (xh1 == 1) return contains_sorted(g2mem, k2, vf1);
     if (xh2 == 1) return contains_sorted(g1mem, k1, vf2);
     int t = 0;
+    if (nI == xh1) {
+        slow += nI;
+        for (int q = 0; q < nI; ++q) t += contains_sorted(g2mem, k2, hI[q]) ? 1 : 0;
+        return t;
+    }
+    slow += kh;
     const int32_t lo = vf1 > vf2 ? vf1 : vf2;
     for (int q = 0; q < kh; ++q) {
         const int32_t u = hmem[q];
@@ -633,27 +656,43 @@ __device__ __forceinline__ int triple_size(int xh1, int32_t vf1, int xh2, int32_
     return t;
 }
 
+// slot of key k in a table stored in the neighbour lists (a large N(h)), or -1
+__device__ __forceinline__ int probe_list_table(const int32_t* keys, uint32_t mask, int32_t k) {
+    uint32_t ps = fmix32(uint32_t(k)) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t key = keys[ps];
+        if (key == k) return int(ps);
+        if (key == EMPTY) return -1;
+        ps = (ps + 1) & mask;
+    }
+    return -1;
+}
+
+// add 1 to counter[key] for every lane holding key >= 0, one atomic per distinct key
+__device__ __forceinline__ void warp_count(uint32_t* counter, int key) {
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    if (key >= 0 && lane_id() == __ffs(same) - 1) atomicAdd(&counter[key], __popc(same));
+}
+
 __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemC& s = *reinterpret_cast<SmemC*>(smem_raw);
     const Store& S = A.S;
     if (A.sc->gate) return;
     const int tid = threadIdx.x;
+    const int lane = lane_id();
+    const int wid = warp_id();
     const uint32_t fam = S.fam;
     const int64_t delta = S.delta;
     const bool want_open = (fam & (kFamH | kFamT)) != 0;
     const bool want_t = (fam & kFamT) != 0;
-    // without the temporal family, the open triads {h, g1, f} centred at g1
-    // are counted in aggregate (see the (ii) comment below)
+    // without the temporal family, open triads are counted in aggregate: those
+    // centred at h by k_nh_build, those centred at g1 here from totals
     const bool agg = want_open && !want_t;
     const CountScratch& cs = A.cs;
     const int32_t* v2h = S.vp.arena;
     const int32_t* h2v = S.hp.arena;
     load_tables(s.tb, NT_C);
-    if (tid < 2) s.tot[tid] = s.xcnt[tid] = 0;
-    if (tid < 4) s.sub[tid] = 0;
-    for (int i = tid; i < kWin * 2; i += NT_C) s.win[i >> 1][i & 1] = 0;
-    if (tid == 0) s.n_cl = 0;
     for (int i = tid; i < 128; i += NT_C) {
         s.acc[i] = 0;
         for (int w = 0; w < NW_C; ++w) s.hist[w][i] = 0;
@@ -662,17 +701,26 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
     for (int i = tid; i < T1_S; i += NT_C) {
         s.keys[i] = EMPTY;
         s.vals[i] = 0;
+        s.mark[i] = 0;
     }
-    if (tid == 0) s.n_list = 0;
+    for (int i = tid; i < LCH * 4; i += NT_C) s.sub[i >> 2][i & 3] = 0;
+    for (int i = tid; i < LCH * 2; i += NT_C) s.xc[i >> 1][i & 1] = 0;
+    if (tid < 2) s.tot[tid] = 0;
+    for (int i = tid; i < kWin * 2; i += NT_C) s.win[i >> 1][i & 1] = 0;
+    if (tid == 0) {
+        s.n_list = 0;
+        s.n_cl = 0;
+    }
     __syncthreads();
     const int64_t gs = cs.gs_c;
     int32_t* g_keys = cs.oc_keys + blockIdx.x * gs;
     uint32_t* g_vals = cs.oc_vals + blockIdx.x * gs;
+    uint32_t* g_mark = cs.oc_mark + blockIdx.x * gs;
     int32_t* g_list = cs.oc_list + blockIdx.x * (gs / 2);
     int32_t* g_lk = cs.oc_lk + blockIdx.x * (gs / 2);
     int64_t* g_lts = cs.oc_lts + blockIdx.x * (gs / 2);
-    uint32_t* hist = s.hist[warp_id()];
-    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t* hist = s.hist[wid];
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
     const int64_t n_items = A.sc->items[A.side];
     const int nd = A.sc->n_d[A.side];
     int cur_g = -1;
@@ -687,7 +735,7 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
         const int64_t chunk = item - cs.d_item_start[j];
         const int32_t g1 = cs.d_list[j];
         const int64_t lbeg = cs.d_loff[j] + chunk * LCH;
-        const int64_t lend = min(lbeg + LCH, cs.d_loff[j + 1]);
+        const int nh = int(min(lbeg + LCH, cs.d_loff[j + 1]) - lbeg);
         const int g = A.changed_g ? A.changed_g[A.lo + cs.l_i[lbeg]] : 0;
         if (g != cur_g) {
             if (cur_g >= 0) flush<NT_C>(A, s.acc, s.hist, NW_C, cur_g, acc, s.red);
@@ -702,22 +750,67 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
         u1 = block_sum<NT_C>(u1, s.red);
         acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
         // the method reads N(g1) (sum of member degrees) once per pair (h, g1)
-        if (tid == 0) acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)(lend - lbeg);
+        if (tid == 0) {
+            acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)nh;
+            ++acc.w[0];
+            acc.w[1] += (unsigned long long)u1;
+        }
         Tab T1;
+        uint32_t* mark;
         int32_t* lk;
         int64_t* lts;
         int P = 1;
         const uint32_t t1_cap = pow2_at_least(2 * u1);
         if (t1_cap <= A.c_smem_cap) {
             T1 = Tab{s.keys, s.vals, nullptr, s.list, &s.n_list, t1_cap - 1, T1_S / 2};
+            mark = s.mark;
             lk = s.lk;
             lts = s.lts;
         } else {
             T1 = Tab{g_keys, g_vals, nullptr, g_list, &s.n_list, uint32_t(gs - 1), int(gs / 2)};
+            mark = g_mark;
             lk = g_lk;
             lts = g_lts;
             if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
             else P = int((4 * u1 + gs - 1) / gs);
+        }
+        // the item's changed hyperedges
+        if (tid < nh) {
+            const int64_t e = lbeg + tid;
+            const int32_t li = cs.l_i[e];
+            const uint64_t xv1 = cs.l_xv[e];
+            const int32_t h = A.changed[A.lo + li];
+            s.hh[tid] = h;
+            s.hk[tid] = S.h_card[h];
+            s.hx[tid] = int(xv1 & kXMask);
+            s.hvf[tid] = int32_t(uint32_t(xv1 >> 32));
+            s.hli[tid] = li;
+            s.hts[tid] = S.h_ts[h];
+            s.hmem[tid] = h2v + S.h_off[h];
+            s.hnb[tid] = cs.nh_off[li];
+            s.hnn[tid] = cs.nh_n[li];
+            s.htcap[tid] = cs.nh_tcap[li];
+            s.htoff[tid] = cs.nh_toff[li];
+            s.hIn[tid] = 0;
+        }
+        __syncthreads();
+        // h & g1 for the h sharing 2..kIC vertices with g1: the smaller list is
+        // searched in the larger
+        for (int l = 0; l < nh; ++l) {
+            const int xh1 = s.hx[l];
+            if (xh1 < 2 || xh1 > kIC) continue;
+            const int kh = s.hk[l];
+            const bool from_h = kh <= k1;
+            const int32_t* a = from_h ? s.hmem[l] : g1mem;
+            const int32_t* b = from_h ? g1mem : s.hmem[l];
+            const int na = from_h ? kh : k1, nb = from_h ? k1 : kh;
+            for (int i = tid; i < na; i += NT_C) {
+                const int32_t u = a[i];
+                if (contains_sorted(b, nb, u)) {
+                    const int c = atomicAdd(&s.hIn[l], 1);
+                    if (c < kIC) s.hI[l][c] = u;
+                }
+            }
         }
         for (int p = 0; p < P; ++p) {
             // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p)
@@ -742,16 +835,15 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
             for (int q0 = 0; q0 < n1; q0 += NT_C) {
                 const int q = q0 + tid;
                 int wkey = -1, C = 0;
-                bool changed_f = false;
                 if (q < n1) {
                     const int sl = T1.list[q];
                     const int32_t f = T1.keys[sl];
                     const int kf = S.h_card[f];
-                    changed_f = bit_test(A.chg, f);
+                    const bool changed_f = bit_test(A.chg, f);
                     lk[q] = kf | (changed_f ? int32_t(0x80000000u) : 0);
                     if (want_t) lts[q] = S.h_ts[f];
                     if (agg) {
-                        const int x = int(T1.vals[sl] & kXMask);
+                        const int x = int(T1.vals[sl]);
                         C = kf > x ? 1 : 0;
                         if (x >= wlo && x < k1) wkey = (x - wlo) * 2 + C;
                         if (changed_f) {
@@ -763,194 +855,179 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
                 if (agg) {
                     const unsigned in = __ballot_sync(0xffffffffu, q < n1);
                     const unsigned c1 = __ballot_sync(0xffffffffu, q < n1 && C == 1);
-                    if (lane_id() == 0) {
+                    if (lane == 0) {
                         if (__popc(in & ~c1)) atomicAdd(&s.tot[0], __popc(in & ~c1));
                         if (__popc(c1)) atomicAdd(&s.tot[1], __popc(c1));
                     }
-                    const unsigned same = __match_any_sync(0xffffffffu, wkey);
-                    if (wkey >= 0 && lane_id() == __ffs(same) - 1)
-                        atomicAdd(&s.win[wkey >> 1][wkey & 1], __popc(same));
+                    warp_count(&s.win[0][0], wkey);
                 }
             }
             acc.n_meta += (tid < n1) ? (n1 - tid + NT_C - 1) / NT_C : 0;
+            if (tid == 0) {
+                // work of pass (i) per h: the smaller of N(h) and N(g1) when N(h)
+                // has a table to probe (aggregate mode), else all of N(h)
+                int run = 0;
+                for (int l = 0; l < nh; ++l) {
+                    s.hpre[l] = run;
+                    const bool from = agg && s.htcap[l] > 0 && s.hnn[l] > n1;
+                    s.hfrom[l] = from ? 1 : 0;
+                    run += from ? n1 : s.hnn[l];
+                }
+                s.hpre[nh] = run;
+            }
             __syncthreads();
             const int n_cl = s.n_cl;
-            // ---- every changed h of this item
-            for (int64_t e = lbeg; e < lend; ++e) {
-                const int32_t li = cs.l_i[e];
-                const uint64_t xv1 = cs.l_xv[e];
-                const int xh1 = int(xv1 & kXMask);
-                const int32_t vf1 = int32_t(uint32_t(xv1 >> 32));
-                const int32_t h = A.changed[A.lo + li];
-                const int kh = S.h_card[h];
-                const int64_t tsh = S.h_ts[h];
-                const int32_t* hmem = h2v + S.h_off[h];
-                const int64_t nb0 = cs.nh_off[li];
-                const int nnh = cs.nh_n[li];
-                // bucket of an f of N(g1) for this h: B = [|g1 & f| != |g1| - |h & g1|],
-                // C = [f not inside g1]; 16-bit fields of a per-thread word
-                const int xstar = k1 - xh1;
-                unsigned long long subw = 0;
-                // (i) the pairs {g1, g2}, g2 in N(h).  Each g2 in N(g1) too (a
-                // closed pair) is marked in N(g1).  Counted at g1 < g2 unless
-                // g2 is a changed hyperedge of smaller ID than h.  In aggregate
-                // mode the open pairs were counted by k_nh_build, so only the
-                // closed ones are visited: from the smaller of N(h) and N(g1),
-                // probing the other's hash table.
-                const int32_t* g1m = g1mem;
-                const uint32_t* bits = A.chg;
-                auto closed_pair = [&](int32_t g2, int x12, int xh2, int32_t vf2, int k2, bool chg2) {
-                    if (agg) subw += 1ull << (16 * ((x12 != xstar ? 2 : 0) | (k2 > x12 ? 1 : 0)));
-                    if (g2 <= g1) return;
-                    if (g2 < h && chg2) return;
-                    ++acc.n_meta;
-                    const int t = triple_size(xh1, vf1, xh2, vf2, g1m, k1, h2v + S.h_off[g2], k2, hmem, kh);
-                    if (want_open) {
-                        const int64_t t2 = want_t ? S.h_ts[g2] : 0;
-                        classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, tsh, ts1, t2, acc);
-                    }
-                    if (agg) atomicAdd(&s.hneg[warp_id()][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
-                    if (fam & kFamV)
-                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 -
-                                  (unsigned long long)t * (xh1 + x12 + xh2) + 2ull * t;
-                };
-                const int tcap = cs.nh_tcap[li];
-                const bool from_g1 = agg && tcap > 0 && nnh > n1;
-                if (from_g1) {
-                    const int64_t toff = cs.nh_toff[li];
-                    const uint32_t tmask = uint32_t(tcap - 1);
-                    for (int q = tid; q < n1; q += NT_C) {
-                        const int sl = T1.list[q];
-                        const int32_t f = T1.keys[sl];
-                        uint32_t ps = fmix32(uint32_t(f)) & tmask;
-                        int found = -1;
-                        for (uint32_t probe = 0; probe <= tmask; ++probe) {
-                            const int32_t key = cs.nh_g[toff + ps];
-                            if (key == f) { found = int(ps); break; }
-                            if (key == EMPTY) break;
-                            ps = (ps + 1) & tmask;
+
+            // ---- (i) the pairs {g1, g2}, g2 in N(h), for every h of the item.
+            // Every g2 also in N(g1) (a closed pair) is marked for that h and
+            // counted at g1 < g2 unless g2 is a changed hyperedge of smaller
+            // ID than h.  In aggregate mode the open pairs were counted by
+            // k_nh_build and only the closed ones are visited: from the
+            // smaller of N(h) and N(g1), probing the other's hash table.
+            const int wtot = s.hpre[nh];
+            if (tid == 0) acc.w[2] += (unsigned long long)wtot;
+            for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
+                const int idx = idx0 + tid;
+                int skey = -1;
+                if (idx < wtot) {
+                    int l = 0;  // the h of this work index
+                    while (l + 1 < nh && s.hpre[l + 1] <= idx) ++l;
+                    const int q = idx - s.hpre[l];
+                    const int32_t h = s.hh[l];
+                    int32_t g2;
+                    int sl = -1, x12 = 0, xh2, k2 = 0;
+                    int32_t vf2;
+                    bool chg2;
+                    if (s.hfrom[l]) {
+                        sl = T1.list[q];
+                        g2 = T1.keys[sl];
+                        const int ps =
+                            probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), g2);
+                        if (ps < 0) {
+                            sl = -1;
+                        } else {
+                            const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
+                            xh2 = int(xv2 & kXMask);
+                            vf2 = int32_t(uint32_t(xv2 >> 32));
+                            const int32_t meta = lk[q];
+                            k2 = meta & 0x7fffffff;
+                            chg2 = meta < 0;
                         }
-                        if (found < 0) continue;
-                        atomicOr(&T1.vals[sl], kFlag);
-                        const uint64_t xv2 = cs.nh_xv[toff + found];
-                        const int32_t meta = lk[q];
-                        closed_pair(f, int(T1.vals[sl] & kXMask), int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)),
-                                    meta & 0x7fffffff, meta < 0);
-                    }
-                } else {
-                    for (int q = tid; q < nnh; q += NT_C) {
-                        const int32_t g2 = cs.nh_g[nb0 + q];
-                        if (P > 1 && part_of(g2, P) != p) continue;
-                        const int sl = tab_find(T1, g2);
-                        const uint64_t xv2 = cs.nh_xv[nb0 + q];
-                        const int xh2 = int(xv2 & kXMask);
-                        const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
-                        if (sl >= 0) {
-                            if (want_open) atomicOr(&T1.vals[sl], kFlag);
-                            closed_pair(g2, int(T1.vals[sl] & kXMask), xh2, vf2, S.h_card[g2], bit_test(bits, g2));
-                            continue;
+                    } else {
+                        g2 = cs.nh_g[s.hnb[l] + q];
+                        if (P == 1 || part_of(g2, P) == p) {
+                            sl = tab_find(T1, g2);
+                            const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
+                            xh2 = int(xv2 & kXMask);
+                            vf2 = int32_t(uint32_t(xv2 >> 32));
+                            if (sl >= 0) {
+                                k2 = S.h_card[g2];
+                                chg2 = bit_test(A.chg, g2);
+                            } else if (!agg && want_open && g2 > g1 && !(g2 < h && bit_test(A.chg, g2))) {
+                                // open pair centred at h, enumerated (temporal family kept)
+                                ++acc.n_meta;
+                                classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, S.h_card[g2], s.hx[l], 0,
+                                         xh2, 0, s.hts[l], ts1, want_t ? S.h_ts[g2] : 0, acc);
+                            }
                         }
-                        if (agg || !want_open) continue;
-                        // open pair centred at h, enumerated (temporal family kept)
-                        if (g2 <= g1) continue;
-                        if (g2 < h && bit_test(bits, g2)) continue;
-                        ++acc.n_meta;
-                        const int k2 = S.h_card[g2];
-                        const int64_t t2 = want_t ? S.h_ts[g2] : 0;
-                        classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, 0, xh2, 0, tsh, ts1, t2, acc);
+                    }
+                    if (sl >= 0) {
+                        const int kh = s.hk[l], xh1 = s.hx[l];
+                        x12 = int(T1.vals[sl]);
+                        if (want_open) atomicOr(&mark[sl], 1u << l);
+                        if (agg) skey = l * 4 + ((x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 1 : 0));
+                        if (g2 > g1 && !(g2 < h && chg2)) {
+                            ++acc.n_meta;
+                            ++acc.w[3];
+                            const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2,
+                                                      s.hmem[l], kh, s.hI[l], s.hIn[l], acc.w[4]);
+                            if (want_open)
+                                classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l],
+                                         ts1, want_t ? S.h_ts[g2] : 0, acc);
+                            if (agg) atomicAdd(&s.hneg[wid][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
+                            if (fam & kFamV)
+                                acc.v3 += (unsigned long long)xh1 * x12 * xh2 -
+                                          (unsigned long long)t * (xh1 + x12 + xh2) + 2ull * t;
+                        }
                     }
                 }
-                if (!want_open) continue;
-                __syncthreads();
-                if (agg) {
-                    // (ii) in aggregate.  An open triad {h, g1, f} (f in N(g1),
-                    // f outside N(h), f != h) has regions h-only |h| - |h&g1|,
-                    // g1-only |g1| - |h&g1| - |g1&f|, f-only |f| - |g1&f|,
-                    // h&g1 and g1&f non-empty, the rest empty: its class is set
-                    // by A = [h not inside g1] and the bucket (B, C) of f.  The
-                    // buckets over all of N(g1) come from the totals and the
-                    // x window; subtracted are the f inside N(h) (marked in (i)),
-                    // f = h, and the changed f < h (attributed to f).
-                    for (int c = tid; c < n_cl; c += NT_C) {
+                if (agg) warp_count(&s.sub[0][0], skey);
+            }
+            __syncthreads();
+            if (agg) {
+                // (ii) in aggregate.  An open triad {h, g1, f} (f in N(g1),
+                // f outside N(h), f != h) has regions h-only |h| - |h&g1|,
+                // g1-only |g1| - |h&g1| - |g1&f|, f-only |f| - |g1&f|, h&g1
+                // and g1&f non-empty, the rest empty: its class is set by
+                // A = [h not inside g1] and the bucket b = 2B + C of f, with
+                // B = [|g1&f| != |g1| - |h&g1|], C = [f not inside g1].  The
+                // buckets over all of N(g1) come from the totals and the x
+                // window; subtracted are the f in N(h) (marked in (i)), f = h,
+                // and the changed f < h (attributed to f).
+                const int wc = nh * n_cl;
+                if (tid == 0) acc.w[5] += (unsigned long long)wc;
+                for (int idx0 = 0; idx0 < wc; idx0 += NT_C) {
+                    const int idx = idx0 + tid;
+                    int skey = -1;
+                    if (idx < wc) {
+                        const int l = idx / n_cl, c = idx - l * n_cl;
                         const int64_t v = lts[c];
                         const int sl = int(uint32_t(v));
                         const int32_t f = T1.keys[sl];
-                        if (f >= h) continue;
-                        const uint32_t val = T1.vals[sl];
-                        if (val & kFlag) continue;
-                        const int x = int(val & kXMask);
-                        subw += 1ull << (16 * ((x != xstar ? 2 : 0) | (int(v >> 32) > x ? 1 : 0)));
-                    }
-                    if (tid == 0 && (P == 1 || part_of(h, P) == p))
-                        subw += 1ull << (16 * ((xh1 != xstar ? 2 : 0) | (kh > xh1 ? 1 : 0)));
-                    unsigned long long xw = 0;
-                    if (xh1 > kWin) {  // outside the window: count x = xstar directly
-                        for (int q = tid; q < n1; q += NT_C) {
-                            const int sl = T1.list[q];
-                            if (int(T1.vals[sl] & kXMask) == xstar)
-                                xw += 1ull << (16 * ((lk[q] & 0x7fffffff) > xstar ? 1 : 0));
+                        if (f < s.hh[l] && !((mark[sl] >> l) & 1u)) {
+                            const int x = int(T1.vals[sl]);
+                            skey = l * 4 + ((x != k1 - s.hx[l] ? 2 : 0) | (int(v >> 32) > x ? 1 : 0));
                         }
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        subw += __shfl_xor_sync(0xffffffffu, subw, o);
-                        xw += __shfl_xor_sync(0xffffffffu, xw, o);
-                    }
-                    if (lane_id() == 0) {
-                        for (int b = 0; b < 4; ++b)
-                            if ((subw >> (16 * b)) & 0xffff) atomicAdd(&s.sub[b], uint32_t((subw >> (16 * b)) & 0xffff));
-                        for (int c = 0; c < 2; ++c)
-                            if ((xw >> (16 * c)) & 0xffff) atomicAdd(&s.xcnt[c], uint32_t((xw >> (16 * c)) & 0xffff));
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        const int A_bit = kh > xh1 ? 1 : 0;
-                        for (int b = 0; b < 4; ++b) {
-                            const int B = b >> 1, C = b & 1;
-                            const uint32_t h0 = xh1 <= kWin ? s.win[kWin - xh1][C] : s.xcnt[C];
-                            const uint32_t total = B == 0 ? h0 : s.tot[C] - h0;
-                            const uint32_t n = total - s.sub[b];
-                            if (n) {
-                                const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
-                                s.acc[s.tb.cls30[m]] += n;
-                                acc.n_tri += n;
-                            }
-                            s.sub[b] = 0;
-                        }
-                        s.xcnt[0] = s.xcnt[1] = 0;
-                    }
-                    // unmark N(h)
-                    if (from_g1) {
-                        for (int q = tid; q < n1; q += NT_C) T1.vals[T1.list[q]] &= ~kFlag;
-                    } else {
-                        for (int q = tid; q < nnh; q += NT_C) {
-                            const int32_t g2 = cs.nh_g[nb0 + q];
-                            if (P > 1 && part_of(g2, P) != p) continue;
-                            const int sl = tab_find(T1, g2);
-                            if (sl >= 0) T1.vals[sl] &= ~kFlag;
-                        }
-                    }
-                    __syncthreads();
-                    continue;
+                    warp_count(&s.sub[0][0], skey);
                 }
-                // (ii) f in N(g1), not marked (not in N(h)), f != h: open at g1
-                for (int q = tid; q < n1; q += NT_C) {
-                    const int sl = T1.list[q];
-                    const uint32_t val = T1.vals[sl];
-                    if (val & kFlag) {
-                        T1.vals[sl] = val & ~kFlag;
-                        continue;
+                if (tid < nh && (P == 1 || part_of(s.hh[tid], P) == p)) {
+                    const int xh1 = s.hx[tid];
+                    atomicAdd(&s.sub[tid][(xh1 != k1 - xh1 ? 2 : 0) | (s.hk[tid] > xh1 ? 1 : 0)], 1u);
+                }
+                for (int l = 0; l < nh; ++l) {  // x = |g1| - |h&g1| outside the window
+                    if (s.hx[l] <= kWin) continue;
+                    const int xstar = k1 - s.hx[l];
+                    for (int q = tid; q < n1; q += NT_C)
+                        if (int(T1.vals[T1.list[q]]) == xstar)
+                            atomicAdd(&s.xc[l][(lk[q] & 0x7fffffff) > xstar ? 1 : 0], 1u);
+                }
+                __syncthreads();
+                if (tid < nh) {
+                    const int xh1 = s.hx[tid], kh = s.hk[tid];
+                    const int A_bit = kh > xh1 ? 1 : 0;
+                    for (int b = 0; b < 4; ++b) {
+                        const int B = b >> 1, C = b & 1;
+                        const uint32_t h0 = xh1 <= kWin ? s.win[kWin - xh1][C] : s.xc[tid][C];
+                        const uint32_t total = B == 0 ? h0 : s.tot[C] - h0;
+                        const uint32_t n = total - s.sub[tid][b];
+                        if (n) {
+                            const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
+                            atomicAdd(&hist[s.tb.cls30[m]], n);
+                            acc.n_tri += n;
+                        }
+                        s.sub[tid][b] = 0;
                     }
+                    s.xc[tid][0] = s.xc[tid][1] = 0;
+                }
+            } else if (want_open) {
+                // (ii) f in N(g1), not in N(h), f != h: open at g1
+                const int wc = nh * n1;
+                for (int idx = tid; idx < wc; idx += NT_C) {
+                    const int l = idx / n1, q = idx - l * n1;
+                    const int sl = T1.list[q];
                     const int32_t f = T1.keys[sl];
+                    const int32_t h = s.hh[l];
                     if (f == h) continue;
                     const int32_t meta = lk[q];
                     if (meta < 0 && f < h) continue;  // changed, smaller ID: attributed to f
-                    classify(s.tb, hist, fam, delta, h, g1, f, kh, k1, meta & 0x7fffffff, xh1, int(val & kXMask), 0, 0,
-                             tsh, ts1, want_t ? lts[q] : 0, acc);
+                    if ((mark[sl] >> l) & 1u) continue;
+                    classify(s.tb, hist, fam, delta, h, g1, f, s.hk[l], k1, meta & 0x7fffffff, s.hx[l],
+                             int(T1.vals[sl]), 0, 0, s.hts[l], ts1, want_t ? lts[q] : 0, acc);
                 }
-                __syncthreads();
             }
             __syncthreads();
+            for (int i = tid; i < n1; i += NT_C) mark[T1.list[i]] = 0;
             tab_clear<NT_C>(T1, n1);
             if (agg) {
                 if (tid < 2) s.tot[tid] = 0;
@@ -1097,7 +1174,7 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += al(sizeof(int64_t) * nbs);
     const int64_t rn = sh.n_cta_nh, rc = sh.n_cta_c;
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
-    b += 2 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
+    b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
     return b + 4096;
 }
@@ -1147,6 +1224,7 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->onh_list = static_cast<int32_t*>(take(sizeof(int32_t) * rn * (sh.gs_nh / 2)));
     cs->oc_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rc * sh.gs_c));
     cs->oc_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rc * sh.gs_c));
+    cs->oc_mark = static_cast<uint32_t*>(take(sizeof(uint32_t) * rc * sh.gs_c));
     cs->oc_list = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_lk = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_lts = static_cast<int64_t*>(take(sizeof(int64_t) * rc * (sh.gs_c / 2)));
@@ -1160,6 +1238,7 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     if ((e = cudaMemsetAsync(cs->onh_aux, 0x7f, sizeof(int32_t) * rn * sh.gs_nh, st))) return e;
     if ((e = cudaMemsetAsync(cs->oc_keys, 0xff, sizeof(int32_t) * rc * sh.gs_c, st))) return e;
     if ((e = cudaMemsetAsync(cs->oc_vals, 0, sizeof(uint32_t) * rc * sh.gs_c, st))) return e;
+    if ((e = cudaMemsetAsync(cs->oc_mark, 0, sizeof(uint32_t) * rc * sh.gs_c, st))) return e;
     return cudaSuccess;
 }
 

@@ -72,7 +72,7 @@ struct Scalars {
     unsigned long long qnh[2];    // neighbourhood-build queues
     int64_t items[2];     // centre work items
     int32_t n_d[2];       // distinct candidate neighbours g1 of one count run
-    unsigned long long stats[8];  // v2h reads, h2v reads, meta reads, triads
+    unsigned long long stats[16]; // v2h, h2v, meta reads, triads, algorithmic entries, then counter work
 };
 
 struct Store {

@@ -55,6 +55,7 @@ struct CountScratch {
     uint32_t* onh_hist = nullptr;    // per block: x histograms for |h| above the shared-memory limit
     int32_t* oc_keys = nullptr;
     uint32_t* oc_vals = nullptr;
+    uint32_t* oc_mark = nullptr;
     int32_t* oc_list = nullptr;
     int32_t* oc_lk = nullptr;
     int64_t* oc_lts = nullptr;

@@ -55,7 +55,8 @@ class esc_batch_stats(C.Structure):
     _fields_ = [("ms_total", C.c_float), ("ms_ingest", C.c_float), ("ms_count_del", C.c_float),
                 ("ms_store", C.c_float), ("ms_count_ins", C.c_float), ("launches", C.c_int64),
                 ("count_launches", C.c_int64), ("v2h_reads", C.c_int64), ("h2v_reads", C.c_int64),
-                ("meta_reads", C.c_int64), ("triads", C.c_int64), ("alg_entries", C.c_int64)]
+                ("meta_reads", C.c_int64), ("triads", C.c_int64), ("alg_entries", C.c_int64),
+                ("work", C.c_int64 * 6)]
 
 
 class esc_batch(C.Structure):
@@ -224,7 +225,7 @@ def esc_last_stats(g: int) -> dict:
     L = load()
     s = esc_batch_stats()
     _check(L.esc_last_stats(g, C.byref(s)), L.esc_last_error, g)
-    return {k: getattr(s, k) for k, _ in esc_batch_stats._fields_}
+    return {k: (list(getattr(s, k)) if k == "work" else getattr(s, k)) for k, _ in esc_batch_stats._fields_}
 
 
 def esc_set_profiling(g: int, on: bool) -> None:
@@ -298,7 +299,7 @@ def esc_group_last_stats(grp: int) -> dict:
     L = load()
     s = esc_batch_stats()
     _check(L.esc_group_last_stats(grp, C.byref(s)), L.esc_group_last_error, grp)
-    return {k: getattr(s, k) for k, _ in esc_batch_stats._fields_}
+    return {k: (list(getattr(s, k)) if k == "work" else getattr(s, k)) for k, _ in esc_batch_stats._fields_}
 
 
 def esc_group_launch_count(grp: int) -> int:
