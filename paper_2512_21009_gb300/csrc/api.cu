@@ -267,6 +267,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     E->max_u = count_max_u(sh);
     // test knob: shrink the shared-memory tables so that the global-table
     // and partitioned paths run on small inputs
+    if (const char* env = getenv("ESC_CENTER_SMALL")) E->cs.center_small = atoi(env) != 0;
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
         long long v = atoll(env);
         if (v >= 64 && (v & (v - 1)) == 0) E->cs.smem_slots = v;

@@ -56,10 +56,9 @@ constexpr uint32_t kXMask = 0xffffu;
 // neighbourhood build
 constexpr int NT_NH = 256;
 constexpr int NH_S = 4096;           // shared-memory N(h) table slots
-// centre kernel
-constexpr int NT_C = 512;
-constexpr int NW_C = NT_C / 32;
-constexpr int T1_S = 8192;           // shared-memory N(g1) table slots
+// centre kernel: threads NT and shared N(g1) table slots TS are template
+// parameters (CenterBig: one 512-thread block per SM; CenterSmall: two
+// 256-thread blocks per SM with half the table)
 constexpr int LCH = 32;              // changed hyperedges per centre work item
 constexpr int kWin = 64;             // |h & g1| values served from the histogram window
 constexpr int kBigNH = 512;          // N(h) with more entries also gets a hash table in the lists
@@ -596,7 +595,9 @@ __global__ void k_d_clean(CountArgs A) {
 // 3. centre kernel
 // ---------------------------------------------------------------------------
 
+template <int NT_C, int T1_S>
 struct SmemC {
+    static constexpr int NW_C = NT_C / 32;
     Tables tb;
     uint32_t hist[NW_C][128];
     uint32_t hneg[NW_C][32];   // open-at-h classes taken back for closed pairs
@@ -674,9 +675,11 @@ __device__ __forceinline__ void warp_count(uint32_t* counter, int key) {
     if (key >= 0 && lane_id() == __ffs(same) - 1) atomicAdd(&counter[key], __popc(same));
 }
 
-__global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
+template <int NT_C, int T1_S, int MINB>
+__global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
+    constexpr int NW_C = NT_C / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemC& s = *reinterpret_cast<SmemC*>(smem_raw);
+    SmemC<NT_C, T1_S>& s = *reinterpret_cast<SmemC<NT_C, T1_S>*>(smem_raw);
     const Store& S = A.S;
     if (A.sc->gate) return;
     const int tid = threadIdx.x;
@@ -890,8 +893,12 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
                 const int idx = idx0 + tid;
                 int skey = -1;
                 if (idx < wtot) {
-                    int l = 0;  // the h of this work index
-                    while (l + 1 < nh && s.hpre[l + 1] <= idx) ++l;
+                    int l = 0, hi_l = nh - 1;  // the h of this work index: last l with hpre[l] <= idx
+                    while (l < hi_l) {
+                        const int mid = (l + hi_l + 1) >> 1;
+                        if (s.hpre[mid] <= idx) l = mid;
+                        else hi_l = mid - 1;
+                    }
                     const int q = idx - s.hpre[l];
                     const int32_t h = s.hh[l];
                     int32_t g2;
@@ -917,9 +924,11 @@ __global__ void __launch_bounds__(NT_C, 1) k_center(CountArgs A) {
                         g2 = cs.nh_g[s.hnb[l] + q];
                         if (P == 1 || part_of(g2, P) == p) {
                             sl = tab_find(T1, g2);
-                            const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
-                            xh2 = int(xv2 & kXMask);
-                            vf2 = int32_t(uint32_t(xv2 >> 32));
+                            if (sl >= 0 || (!agg && want_open)) {
+                                const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
+                                xh2 = int(xv2 & kXMask);
+                                vf2 = int32_t(uint32_t(xv2 >> 32));
+                            }
                             if (sl >= 0) {
                                 k2 = S.h_card[g2];
                                 chg2 = bit_test(A.chg, g2);
@@ -1172,7 +1181,7 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 2 * al(sizeof(int32_t) * sh.e_cap) + al(sizeof(int64_t) * sh.e_cap);
     b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
     b += al(sizeof(int64_t) * nbs);
-    const int64_t rn = sh.n_cta_nh, rc = sh.n_cta_c;
+    const int64_t rn = sh.n_cta_nh, rc = 2 * int64_t(sh.n_cta_c);  // centre grid is up to 2 blocks per SM
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
     b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
@@ -1217,7 +1226,7 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->d_item_start = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.e_cap + 1)));
     cs->block_sums = static_cast<int64_t*>(take(sizeof(int64_t) * nbs));
     cs->n_block_sums = nbs;
-    const int64_t rn = sh.n_cta_nh, rc = sh.n_cta_c;
+    const int64_t rn = sh.n_cta_nh, rc = 2 * int64_t(sh.n_cta_c);  // centre grid is up to 2 blocks per SM
     cs->onh_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
     cs->onh_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rn * sh.gs_nh));
     cs->onh_aux = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
@@ -1257,7 +1266,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
                              const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
     CountArgs A{S, sc, changed, changed_g, chg_bits, lo, n, side, dcounts_side, cs,
                 uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
-                uint32_t(cs.smem_slots < T1_S ? cs.smem_slots : T1_S)};
+                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small ? 4096 : 8192))};
     const unsigned gd = blocks_for(cs.e_cap, kScanBlock);
     const unsigned ge = capped(blocks_for(cs.e_cap, 256));
     k_run_begin<<<1, 1, 0, st>>>(sc, side);
@@ -1271,7 +1280,10 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
     k_set_loffg<<<ge, 256, 0, st>>>(A);
     k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
-    k_center<<<cs.n_cta_c, NT_C, sizeof(SmemC), st>>>(A);
+    if (cs.center_small)
+        k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A);
+    else
+        k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A);
     k_d_clean<<<ge, 256, 0, st>>>(A);
     lc.total += 13;
     lc.count += 2;
@@ -1284,7 +1296,10 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(k_nh_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemNH)));
-        cudaFuncSetAttribute(k_center, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemC)));
+        cudaFuncSetAttribute(k_center<512, 8192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(SmemC<512, 8192>)));
+        cudaFuncSetAttribute(k_center<256, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(SmemC<256, 4096>)));
         attr_done = true;
     }
     for (int64_t a = lo; a < hi; a += cs.cap) {

@@ -29,7 +29,7 @@ namespace {
 constexpr int64_t kNAMaxHyperedges = int64_t(1) << 18;
 constexpr int64_t kNAMaxIncidences = int64_t(1) << 21;
 constexpr int64_t kNAMaxVertices = int64_t(1) << 19;
-constexpr int kNABlocks = 152;          // blocks of each counting kernel
+constexpr int kNABlocks = 64;           // blocks of each counting kernel
 constexpr int64_t kNATableSlots = 2048; // per counter overflow table
 constexpr int64_t kNAListEntries = int64_t(1) << 19;  // neighbour-list entries per counting run
 constexpr size_t kNoAllocBytes = size_t(80) << 20;

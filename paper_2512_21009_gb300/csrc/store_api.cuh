@@ -60,6 +60,7 @@ struct CountScratch {
     int32_t* oc_lk = nullptr;
     int64_t* oc_lts = nullptr;
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
+    int center_small = 1;            // 1: two 256-thread centre blocks per SM, 0: one 512-thread block
     int64_t* h_total = nullptr;      // pinned host word for the list total
 };
 
