@@ -101,12 +101,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_init():
+def dist_init(backend=None):
+    """Rank, world size, local rank and the process group module (None when
+    run alone).  One process per GPU under torchrun: NCCL; gloo on CPU."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, 0, None
+    import torch
     import torch.distributed as dist
-    backend = "nccl"
+    if backend is None:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
     dist.init_process_group(backend=backend)
     return dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0")), dist
 
@@ -136,6 +140,17 @@ def allreduce_sum(dist, x: float, device) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def combine(dist, device, elapsed_s: float, units: float):
+    """Whole-job figures: the slowest rank's time and every rank's units
+    (weak scaling: each rank works on its own replica or its own graphs)."""
+    return allreduce_max(dist, elapsed_s, device), allreduce_sum(dist, units, device)
+
+
+def shard(n: int, rank: int, ws: int):
+    """Indices of the independent units (graphs) that rank handles."""
+    return list(range(rank, n, ws))
 
 
 def make_stream(args, rank):
@@ -262,10 +277,8 @@ def run_ours(args):
         if not np.array_equal(np.sort(out), np.sort(d)):
             raise SystemExit("bench: the live-ID assumption failed (inserts did not reuse the deleted IDs)")
     upd_timed = sum(n_upd[args.warmup:args.warmup + args.steps])
-    t_max = allreduce_max(dist, elapsed, dev)
-    te_max = allreduce_max(dist, te, dev)
-    tot_upd = allreduce_sum(dist, upd_timed, dev)
-    tot_upd_e2e = allreduce_sum(dist, sum(n_upd[args.warmup + args.steps:nb]), dev)
+    t_max, tot_upd = combine(dist, dev, elapsed, upd_timed)
+    te_max, tot_upd_e2e = combine(dist, dev, te, sum(n_upd[args.warmup + args.steps:nb]))
     if rank != 0:
         return
     hbm, kind = peaks()
@@ -387,13 +400,394 @@ def run_reference(args):
     }))
 
 
+# ---------------------------------------------------------------------------
+# batched form: many hypergraphs, one call vs one call per graph
+# ---------------------------------------------------------------------------
+
+def _group_cfgs(E, streams, delta, fam, max_bh, max_bi):
+    shared = E.make_config(1, 1, 1, max_bh, max_bi, fam, delta)
+    cfgs = []
+    for st in streams:
+        b = st.batches[0]
+        cfgs.append(E.make_config(st.n_vertices, st.initial.n + b.inserts.n + 64,
+                                  int(st.initial.nnz * 1.5) + 2 * b.inserts.nnz + 1024, 0, 0, fam, delta))
+    return shared, cfgs
+
+
+def _load_group(E, grp, streams, max_bh, max_bi):
+    """Initial hyperedges of every graph, in calls that fit the staging limits."""
+    todo = list(range(len(streams)))
+    while todo:
+        call, nh, ni = [], 0, 0
+        while todo:
+            st = streams[todo[0]]
+            if call and (nh + st.initial.n > max_bh or ni + st.initial.nnz > max_bi):
+                break
+            i = todo.pop(0)
+            nh += st.initial.n
+            ni += st.initial.nnz
+            call.append(dict(graph=i, ins_offsets=st.initial.offsets, ins_members=st.initial.members,
+                             ins_timestamps=st.initial.timestamps, del_ids=None))
+        E.esc_group_apply(grp, call)
+
+
+def run_batched(args):
+    """One update batch for each of many independent hypergraphs (initial sizes
+    log-uniform, one mixed batch each, all three families).  The same batches
+    are applied to two identical groups: one esc_group_apply call per graph
+    (plain, one batch per launch sequence) and one call for all graphs
+    (batched).  Every graph's counts must agree between the two."""
+    import torch
+    from paper_2512_21009_gb300 import escher as E
+    rank, ws, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ms = gen.batched(seed=4, n_graphs=args.graphs or 256, e_hi=1e6 * args.scale, b_hi=1e5 * args.scale)
+    streams = [ms.graphs[i] for i in shard(len(ms.graphs), rank, ws)]   # graphs are independent
+    fam, delta = 7, ms.delta
+    tot_upd = sum(st.batches[0].inserts.n + len(st.batches[0].del_ranks) for st in streams)
+    max_bh = max(1 << 20, tot_upd + 1024)
+    max_bi = max(1 << 24, sum(st.batches[0].inserts.nnz for st in streams) + 1024)
+    shared, cfgs = _group_cfgs(E, streams, delta, fam, max_bh, max_bi)
+    groups = []
+    t0 = time.time()
+    for _ in range(2):
+        grp = E.esc_group_create(shared, cfgs)
+        _load_group(E, grp, streams, max_bh, max_bi)
+        groups.append(grp)
+    torch.cuda.synchronize()
+    t_create = time.time() - t0
+    batches = []
+    for i, st in enumerate(streams):
+        b = st.batches[0]
+        # initial IDs are 0..E0-1 and no insert happened yet: ranks are IDs
+        dels = np.sort(b.del_ranks).astype(np.int32)
+        batches.append(dict(graph=i, ins_offsets=b.inserts.offsets, ins_members=b.inserts.members,
+                            ins_timestamps=b.inserts.timestamps, del_ids=dels))
+    # plain: one call per graph
+    lat = []
+    barrier(dist, dev)
+    t0 = time.perf_counter()
+    for bt in batches:
+        t1 = time.perf_counter()
+        E.esc_group_apply(groups[0], [bt])
+        lat.append((time.perf_counter() - t1) * 1e3)
+    t_plain = time.perf_counter() - t0
+    # batched: one call for every graph
+    l0 = E.esc_group_launch_count(groups[1])
+    barrier(dist, dev)
+    t0 = time.perf_counter()
+    E.esc_group_apply(groups[1], batches)
+    t_batched = time.perf_counter() - t0
+    launches_batched = E.esc_group_launch_count(groups[1]) - l0
+    same = True
+    for i in range(len(streams)):
+        for tt in (0, 1, 2):
+            a = E.esc_group_triads(groups[0], i, tt, delta)
+            b = E.esc_group_triads(groups[1], i, tt, delta)
+            same &= bool(np.array_equal(a, b))
+    for grp in groups:
+        E.esc_group_destroy(grp)
+    t_plain, upd_all = combine(dist, dev, t_plain, tot_upd)
+    t_batched, _ = combine(dist, dev, t_batched, tot_upd)
+    n_diff = allreduce_sum(dist, 0.0 if same else 1.0, dev)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": upd_all / t_batched, "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+        "ms_per_step": t_batched * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32 ids / uint64 counts", "data": "synthetic",
+        "config": {"workload": (f"batched: {len(ms.graphs)} hypergraphs, initial sizes log-uniform "
+                                f"[1e3, {1e6 * args.scale:.0e}], vertices = hyperedges/2, cardinality Zipf(2.0) in "
+                                f"[2,256], one mixed batch each of log-uniform size [1e2, {1e5 * args.scale:.0e}], "
+                                "all three families"), "updates": int(upd_all), "create_s": round(t_create, 2),
+                   "parallelism": f"graphs sharded over {ws} rank(s)"},
+        "plain": {"value": upd_all / t_plain, "unit": UNIT, "seconds": t_plain, "calls": len(ms.graphs),
+                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))},
+        "batched": {"value": upd_all / t_batched, "unit": UNIT, "seconds": t_batched, "calls": ws,
+                    "launches": int(launches_batched)},
+        "batched_over_plain": t_plain / t_batched,
+        "counts_identical": n_diff == 0,
+    }))
+
+
+# ---------------------------------------------------------------------------
+# temporal stream with expirations
+# ---------------------------------------------------------------------------
+
+def run_temporal(args):
+    """Time-ordered stream (batches of 2^16 inserts; every live hyperedge older
+    than T - delta, T the batch's last timestamp, is deleted in the same batch)
+    with the temporal family kept.  --scale shrinks the vertex count, the
+    stream length and the arrival rate together, so the window holds the same
+    share of the stream."""
+    import torch
+    from paper_2512_21009_gb300 import escher as E
+    torch.cuda.set_device(0)
+    ts = gen.temporal(seed=3, scale=args.scale, rate_per_s=1e3 * args.scale)
+    delta = ts.delta
+    nv = ts.n_vertices
+    n_total = sum(b.n for b in ts.batches)
+    nnz_total = sum(b.nnz for b in ts.batches)
+    bmax = max(b.n for b in ts.batches)
+    g = E.Graph(nv, None, None, None, capacity_hyperedges=n_total + 64, capacity_incidences=nnz_total + 1024,
+                max_batch_hyperedges=4 * bmax, max_batch_incidences=max(b.nnz for b in ts.batches) + 1024,
+                families=4, delta=delta)
+    g.set_profiling(True)
+    # timestamps grow along the stream, so the live hyperedges in insertion
+    # order have sorted timestamps and each batch's expirations are a prefix
+    live_ids = np.zeros(0, np.int32)
+    live_ts = np.zeros(0, np.int64)
+    lat, upd, t_all = [], [], 0.0
+    for k, b in enumerate(ts.batches):
+        t_cut = int(b.timestamps.max()) - delta
+        n_exp = int(np.searchsorted(live_ts, t_cut, side="left"))
+        dels = np.sort(live_ids[:n_exp])
+        t1 = time.perf_counter()
+        ids = g.apply_batch(b.offsets, b.members, b.timestamps, dels)
+        dt = time.perf_counter() - t1
+        live_ids = np.concatenate([live_ids[n_exp:], ids.astype(np.int32)])
+        live_ts = np.concatenate([live_ts[n_exp:], b.timestamps])
+        if k >= args.warmup:
+            lat.append(dt * 1e3)
+            upd.append(b.n + n_exp)
+            t_all += dt
+    counts = g.triads(E.TRIAD_TEMPORAL)
+    g.close()
+    print(json.dumps({
+        "metric": METRIC, "value": sum(upd) / t_all, "unit": UNIT, "n_gpus": 1, "steps": len(upd),
+        "warmup": args.warmup, "ms_per_step": t_all * 1e3 / len(upd), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts", "data": "synthetic",
+        "config": {"workload": (f"temporal: {n_total:,} hyperedges over {nv:,} vertices, cardinality Zipf(2.0) in "
+                                f"[2,500], timestamps with Exp gaps (rate {1e3 * args.scale:g}/s), batches of "
+                                f"{ts.meta['batch']:,} inserts plus expirations, delta = 3600 s"),
+                   "families": "temporal (96)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "live_at_end": int(len(live_ids)), "temporal_triads": int(counts.sum()),
+    }))
+
+
+# ---------------------------------------------------------------------------
+# serving loop: Poisson arrivals over many resident graphs
+# ---------------------------------------------------------------------------
+
+class _IdModel:
+    """Client-side copy of one graph's live IDs under the library's ID rule
+    (deletes first; the j-th insert takes the j-th smallest free ID below the
+    high-water mark, then fresh IDs), so that a request can delete hyperedges
+    inserted by earlier requests that are still queued."""
+
+    def __init__(self, n0: int):
+        self.live = np.arange(n0, dtype=np.int32)
+        self.n = n0
+        self.free = np.zeros(0, np.int32)
+        self.hw = n0
+
+    def pick(self, rng, n_del):
+        idx = rng.choice(self.n, size=min(n_del, self.n), replace=False)
+        return idx, self.live[idx]
+
+    def commit(self, idx, dels, n_ins):
+        n, k = self.n, len(idx)
+        tail = np.arange(n - k, n)
+        moved = tail[~np.isin(tail, idx)]
+        holes = np.sort(idx[idx < n - k])
+        self.live[holes] = self.live[moved]
+        self.n = n - k
+        free = np.union1d(self.free, dels)
+        take = min(n_ins, len(free))
+        ids = np.concatenate([free[:take], np.arange(self.hw, self.hw + n_ins - take, dtype=np.int32)])
+        self.free = free[take:].astype(np.int32)
+        self.hw += n_ins - take
+        if self.n + n_ins > len(self.live):
+            self.live = np.concatenate([self.live, np.zeros(max(n_ins, len(self.live) // 2), np.int32)])
+        self.live[self.n:self.n + n_ins] = ids
+        self.n += n_ins
+        return ids.astype(np.int32)
+
+
+def _drive(E, srv, models, nvs, pool, rng, rate, duration, max_pending, t_clock, log=None):
+    """Offer Poisson arrivals at ``rate`` requests/s for ``duration`` s: each
+    request is one batch for a uniform graph, size floor(10**U(1, 4)), half
+    inserts (cardinality Zipf(2.0) in [2,256], uniform members) and half
+    deletes of uniform live hyperedges.  A request that does not fit the
+    server's bounded queue is refused and dropped.  Returns the run's record."""
+    G = len(models)
+    n = max(1, int(rate * duration))
+    gaps = rng.exponential(1.0 / rate, size=n)
+    t_rel = np.cumsum(gaps)
+    graphs = rng.integers(0, G, size=n)
+    sizes = np.floor(10 ** rng.uniform(1, 4, size=n)).astype(np.int64)
+    poff, pu = pool
+    npool = len(poff) - 1
+    cursor = int(rng.integers(0, npool))
+    tickets, outs, refused = [], [], 0
+    t0 = time.monotonic_ns()
+    for k in range(n):
+        ta = t0 + int(t_rel[k] * 1e9)
+        now = time.monotonic_ns()
+        if ta > now:
+            dt = (ta - now) / 1e9
+            if dt > 3e-4:
+                time.sleep(dt - 2e-4)
+            while time.monotonic_ns() < ta:
+                pass
+        size = int(sizes[k])
+        if E.esc_server_get_stats(srv)["pending_updates"] + size > max_pending:
+            refused += 1
+            continue
+        g = int(graphs[k])
+        m = models[g]
+        n_ins = size // 2
+        idx, dels = m.pick(rng, size - n_ins)
+        if cursor + n_ins > npool:
+            cursor = 0
+        a, b = int(poff[cursor]), int(poff[cursor + n_ins])
+        off = (poff[cursor:cursor + n_ins + 1] - a).astype(np.int64)
+        mem = np.minimum((pu[a:b] * nvs[g]).astype(np.int32), nvs[g] - 1)
+        cursor += n_ins
+        ts = (ta // 1000 - t_clock) + np.arange(n_ins, dtype=np.int64)
+        dsort = np.sort(dels)
+        out = np.zeros(max(n_ins, 1), np.int32)
+        tk = E.esc_server_submit(srv, g, off, mem, ts, dsort, out, t_arrival_ns=ta)
+        if tk < 0:
+            refused += 1
+            continue
+        want = m.commit(idx, dels, n_ins)
+        tickets.append((tk, size))
+        outs.append((out, want))
+        if log is not None and g in log:
+            log[g].append((off, mem, ts, dsort))
+    t_sub = time.monotonic_ns()
+    E.esc_server_drain(srv)
+    lat, done, t_end, calls_b = [], 0, t0, []
+    for tk, size in tickets:
+        inf = E.esc_server_wait(srv, tk)
+        if inf["status"] != 0:
+            raise RuntimeError(f"request failed with status {inf['status']}")
+        lat.append((inf["t_done_ns"] - inf["t_arrival_ns"]) / 1e6)
+        done += size
+        t_end = max(t_end, inf["t_done_ns"])
+        calls_b.append(inf["call_batches"])
+    ids_ok = all(np.array_equal(o[:len(w)], w) for o, w in outs)
+    wall = (t_end - t0) / 1e9
+    lat = np.asarray(lat) if lat else np.zeros(1)
+    return {"offered_per_s": rate, "requests": n, "served": len(tickets), "refused": refused,
+            "updates_per_s": done / wall if wall > 0 else 0.0, "seconds": wall,
+            "submit_seconds": (t_sub - t0) / 1e9,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batches_per_call": float(np.mean(calls_b)) if calls_b else 0.0, "ids_ok": bool(ids_ok)}
+
+
+def run_serving(args):
+    """Resident hypergraphs (sizes as the batched workload, times --scale),
+    admitted while their device memory fits; Poisson request arrivals.
+    Two server policies over the same group: continuous batching and one
+    request per call.  For each: an overload run at --rate requests/s, then
+    runs at 0.25, 0.5 and 1.0 of the capacity it sustained.  Afterwards a
+    few graphs are rebuilt alone from their logged requests and their counts
+    compared with the served ones."""
+    import torch
+    from paper_2512_21009_gb300 import escher as E
+    torch.cuda.set_device(0)
+    n_graphs = args.graphs or 1024
+    ms = gen.resident_graphs(seed=5, n_graphs=n_graphs, e_hi=1e6 * args.scale)
+    streams, delta, fam = ms.graphs, ms.delta, 1 | 4
+    max_bh, max_bi = 1 << 20, 1 << 24
+    shared, cfgs = _group_cfgs_resident(E, streams, delta, fam, max_bh, max_bi)
+    free = torch.cuda.mem_get_info()[0]
+    budget = min(free - (16 << 30), 120 << 30)
+    lo, hi = 1, len(cfgs)
+    while lo < hi:  # admission: most graphs whose group fits the budget
+        mid = (lo + hi + 1) // 2
+        if E.esc_group_bytes(shared, cfgs[:mid]) <= budget:
+            lo = mid
+        else:
+            hi = mid - 1
+    G = lo
+    streams, cfgs = streams[:G], cfgs[:G]
+    t0 = time.time()
+    grp = E.esc_group_create(shared, cfgs)
+    _load_group(E, grp, streams, max_bh, max_bi)
+    torch.cuda.synchronize()
+    t_load = time.time() - t0
+    models = [_IdModel(st.initial.n) for st in streams]
+    nvs = [st.n_vertices for st in streams]
+    t_clock = time.monotonic_ns() // 1000 - 3600 * 10 ** 6   # timestamps after every initial one
+    pool = gen.insert_pool(6, 1 << 21)
+    rng = np.random.default_rng(args.seed + 100)
+    order = np.argsort([st.initial.n for st in streams])
+    sample = [int(order[0]), int(order[len(order) // 3]), int(order[2 * len(order) // 3])]
+    log = {g: [] for g in sample}
+    max_pending = args.queue
+    runs = {}
+    for policy, per_call in (("continuous", 0), ("one_per_call", 1)):
+        srv = E.esc_server_create(grp, max_pending, per_call)
+        try:
+            over = _drive(E, srv, models, nvs, pool, rng, args.rate, args.duration, max_pending, t_clock, log)
+            cap = max(over["updates_per_s"], 1.0)
+            mean_size = float(np.mean(np.floor(10 ** np.random.default_rng(0).uniform(1, 4, 100000))))
+            curve = []
+            for f in (0.25, 0.5, 1.0):
+                curve.append(dict(fraction=f, **_drive(E, srv, models, nvs, pool, rng, f * cap / mean_size,
+                                                        args.duration, max_pending, t_clock, log)))
+            runs[policy] = {"overload": over, "curve": curve, "stats": E.esc_server_get_stats(srv)}
+        finally:
+            E.esc_server_destroy(srv)
+    # each sampled graph alone, from its initial hyperedges and logged requests
+    same = True
+    for g in sample:
+        st = streams[g]
+        alone = E.Graph(st.n_vertices, st.initial.offsets, st.initial.members, st.initial.timestamps,
+                        capacity_hyperedges=cfgs[g].capacity_hyperedges,
+                        capacity_incidences=cfgs[g].capacity_incidences, max_batch_hyperedges=max_bh,
+                        max_batch_incidences=max_bi, families=fam, delta=delta)
+        for off, mem, ts, dels in log[g]:
+            alone.apply_batch(off, mem, ts, dels, return_ids=False)
+        for tt in (E.TRIAD_HYPEREDGE, E.TRIAD_TEMPORAL):
+            same &= bool(np.array_equal(alone.triads(tt), E.esc_group_triads(grp, g, tt, delta)))
+        alone.close()
+    E.esc_group_destroy(grp)
+    cont = runs["continuous"]["overload"]
+    print(json.dumps({
+        "metric": METRIC, "value": cont["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32 ids / uint64 counts", "data": "synthetic",
+        "config": {"workload": (f"serving: {G} of {n_graphs} resident hypergraphs admitted (initial sizes "
+                                f"log-uniform [1e3, {1e6 * args.scale:.0e}], vertices = hyperedges/2, cardinality "
+                                "Zipf(2.0) in [2,256]); Poisson arrivals, uniform graph, sizes log-uniform "
+                                "[10, 1e4], 1:1 insert/delete; hyperedge + temporal families"),
+                   "offered_per_s": args.rate, "seconds_per_run": args.duration, "queue_updates": max_pending,
+                   "load_s": round(t_load, 1), "hyperedges": int(sum(st.initial.n for st in streams))},
+        "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
+        "runs": runs,
+        "continuous_over_one_per_call": cont["updates_per_s"] / max(runs["one_per_call"]["overload"]["updates_per_s"], 1e-9),
+        "alone_equals_served": same,
+        "ids_ok": all(r["ids_ok"] for p in runs.values() for r in [p["overload"]] + p["curve"]),
+    }))
+
+
+def _group_cfgs_resident(E, streams, delta, fam, max_bh, max_bi):
+    """Per-graph capacities for a long request stream: the live count stays
+    near the initial one (1:1 requests), the incidences drift."""
+    shared = E.make_config(1, 1, 1, max_bh, max_bi, fam, delta)
+    cfgs = [E.make_config(st.n_vertices, int(st.initial.n * 1.25) + 6000, int(st.initial.nnz * 2) + 60000,
+                          0, 0, fam, delta) for st in streams]
+    return shared, cfgs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large_uniform", choices=["large_uniform", "tiny"])
+    ap.add_argument("--workload", default="large_uniform",
+                    choices=["large_uniform", "tiny", "batched", "temporal", "serving"])
+    ap.add_argument("--graphs", type=int, default=None)
+    ap.add_argument("--rate", type=float, default=5e4, help="serving: offered requests/s")
+    ap.add_argument("--duration", type=float, default=8.0, help="serving: seconds per run")
+    ap.add_argument("--queue", type=int, default=1 << 20, help="serving: queued updates admitted")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--batch", type=int, default=100_000)
     ap.add_argument("--seed", type=int, default=2)
@@ -405,6 +799,12 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "temporal":
+        run_temporal(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

@@ -37,7 +37,8 @@ __all__ = [
     "CSR", "Batch", "Stream", "TemporalStream", "MultiStream",
     "zipf_cardinalities", "uniform_cardinalities", "sample_members",
     "exp_gap_timestamps",
-    "tiny", "large", "temporal", "batched", "serving_arrivals", "random_small",
+    "tiny", "large", "temporal", "batched", "resident_graphs", "insert_pool", "serving_arrivals",
+    "random_small",
 ]
 
 
@@ -319,6 +320,36 @@ def batched(seed: int = 4, n_graphs: int = 256, e_lo: float = 1e3, e_hi: float =
         graphs.append(Stream(f"g{g}", seed, nv, init, b, dict(e0=e0)))
     return MultiStream("batched", seed, graphs, int(round(delta_s * 1e6)),
                        dict(n_graphs=n_graphs, kmax=kmax))
+
+
+def resident_graphs(seed: int = 5, n_graphs: int = 1024, e_lo: float = 1e3, e_hi: float = 1e6,
+                    kmax: int = 256, delta_s: float = 3600.0) -> MultiStream:
+    """Initial hypergraphs of the serving workload, drawn as in ``batched``
+    (initial hyperedge count floor(10**U(log10 e_lo, log10 e_hi)), vertices
+    = hyperedges / 2, cardinality Zipf(2.0) in [2, kmax], uniform members,
+    Exp(1e3/s) timestamp gaps) but without a batch of their own."""
+    rng = np.random.default_rng(seed)
+    graphs = []
+    for g in range(n_graphs):
+        e0 = int(math.floor(10 ** rng.uniform(math.log10(e_lo), math.log10(e_hi))))
+        nv = max(kmax, e0 // 2)
+        sampler = _VertexSampler(rng, nv, "uniform")
+        ts0 = exp_gap_timestamps(rng, e0, 0)
+        init = _csr(rng, zipf_cardinalities(rng, e0, 2.0, 2, kmax), nv, sampler, ts0)
+        graphs.append(Stream(f"g{g}", seed, nv, init, [], dict(e0=e0)))
+    return MultiStream("resident", seed, graphs, int(round(delta_s * 1e6)), dict(n_graphs=n_graphs, kmax=kmax))
+
+
+def insert_pool(seed: int, n: int, kmax: int = 256):
+    """A pool of ``n`` hyperedges for update requests: cardinalities
+    Zipf(2.0) in [2, kmax] and members as uniform fractions in [0, 1), to be
+    scaled to a graph's vertex count (floor(u * n_vertices); repeats within a
+    hyperedge are legal input and are removed on ingest)."""
+    rng = np.random.default_rng(seed)
+    cards = zipf_cardinalities(rng, n, 2.0, 2, kmax)
+    offs = np.zeros(n + 1, np.int64)
+    np.cumsum(cards, out=offs[1:])
+    return offs, rng.random(int(offs[-1]), dtype=np.float32)
 
 
 def serving_arrivals(seed: int, n_graphs: int, n_requests: int, rate_per_s: float,

@@ -71,7 +71,8 @@ typedef enum {
     ESC_ERR_UNSUPPORTED = 4,   /* a size beyond a documented engine limit, a
                                   family not maintained, another window   */
     ESC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out              */
-    ESC_ERR_CUDA = 6           /* a CUDA runtime call failed                 */
+    ESC_ERR_CUDA = 6,          /* a CUDA runtime call failed                 */
+    ESC_ERR_BUSY = 7           /* a server's queue is full; nothing was kept */
 } esc_status;
 
 typedef enum {
@@ -242,6 +243,14 @@ typedef struct {
 esc_status esc_group_create(const esc_config* shared_cfg, int32_t n_graphs,
                             const esc_config* graph_cfg, void* cuda_stream, esc_group** out);
 
+/* Device bytes that esc_group_create would allocate for the same arguments
+ * (a sizing pass: nothing is allocated, no kernel runs).  A caller admits
+ * graphs while this figure stays within the free device memory
+ * (cudaMemGetInfo) or its own budget.  Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA (no device). */
+esc_status esc_group_bytes(const esc_config* shared_cfg, int32_t n_graphs, const esc_config* graph_cfg,
+                           int64_t* out_bytes);
+
 /* Apply n batches (each graph at most once per call) in one pass.  Returns
  * when every store and count is updated.  Errors as esc_apply_batch; the
  * failing batch is named by esc_group_last_error. */
@@ -254,6 +263,72 @@ const char* esc_group_last_error(const esc_group* grp);
 esc_status esc_group_set_profiling(esc_group* grp, int32_t on);
 esc_status esc_group_last_stats(esc_group* grp, esc_batch_stats* out);
 int64_t esc_group_launch_count(const esc_group* grp);
+
+/* ------------------------------------------------------------------------
+ * Serving loop over a group's resident graphs.  The paper applies one batch
+ * at a time (Alg. 3); the server adds the request layer around that step:
+ * update requests (one batch for one graph) are queued as they arrive, and
+ * one worker thread applies them by continuous batching -- each call takes
+ * the oldest pending request of as many distinct graphs as fit the group's
+ * max_batch_hyperedges / max_batch_incidences (and max_batches_per_call
+ * when > 0), so that requests arriving during a call join the next one.
+ * Requests of one graph are applied in submission order, so a graph's IDs
+ * and counts are those of its batches applied one by one with esc_group_apply.
+ * ------------------------------------------------------------------------ */
+typedef struct esc_server esc_server;
+
+typedef struct {
+    int32_t status;        /* esc_status of the request                              */
+    int32_t call_batches;  /* requests applied by the same call                      */
+    int64_t t_arrival_ns;  /* CLOCK_MONOTONIC times (ns): arrival, call start, done  */
+    int64_t t_start_ns;
+    int64_t t_done_ns;
+    int64_t call_updates;  /* inserts + deletes applied by the same call             */
+} esc_request_info;
+
+typedef struct {
+    int64_t submitted, rejected, completed, failed;
+    int64_t calls;    /* esc_group_apply calls made by the worker (retries of a failed call not counted) */
+    int64_t updates;  /* inserts + deletes of completed requests                              */
+    int64_t pending_updates;  /* inserts + deletes of submitted, unfinished requests          */
+} esc_server_stats;
+
+/* Start a server on grp.  While it runs, the group must not be used except
+ * through the server.  max_pending_updates bounds the inserts + deletes of
+ * submitted, unfinished requests (admission: a submit beyond it returns
+ * ESC_ERR_BUSY); max_batches_per_call 0 = as many as fit, 1 = one request
+ * per call.  Errors: INVALID_ARG. */
+esc_status esc_server_create(esc_group* grp, int64_t max_pending_updates, int32_t max_batches_per_call,
+                             esc_server** out);
+
+/* Queue one request.  All pointers are host memory and are copied before
+ * the call returns, except out_ins_ids (host int32[n_ins] or NULL), which
+ * receives the inserted IDs before the request is reported done and must
+ * stay valid until then.  t_arrival_ns: CLOCK_MONOTONIC time of arrival in
+ * ns (0: now), used for the request's latency.  *ticket identifies the
+ * request for esc_server_wait.  Errors: INVALID_ARG (bad graph, empty
+ * request, device pointers, offsets not starting at 0), OUT_OF_MEMORY (the
+ * request alone exceeds the per-call limits), BUSY (queue full). */
+esc_status esc_server_submit(esc_server* srv, const esc_batch* batch, int64_t t_arrival_ns, int64_t* ticket);
+
+/* Block until request `ticket` is done; fill *info (may be NULL) and return
+ * the request's own status.  Each ticket is collected once; a second wait
+ * returns NOT_FOUND.  A request that fails changes nothing in its graph
+ * (the worker applies the requests of a failed call one by one). */
+esc_status esc_server_wait(esc_server* srv, int64_t ticket, esc_request_info* info);
+
+/* Block until every submitted request is done. */
+esc_status esc_server_drain(esc_server* srv);
+
+/* esc_group_triads through the server (serialised with the worker's calls). */
+esc_status esc_server_triads(esc_server* srv, int32_t graph, esc_triad_type type, int64_t window,
+                             uint64_t* out, int32_t n_out);
+
+esc_status esc_server_get_stats(esc_server* srv, esc_server_stats* out);
+
+/* Finish every queued request, stop the worker and free the server (not the
+ * group). */
+esc_status esc_server_destroy(esc_server* srv);
 
 /* Allocation-free counting.  The paper has no counterpart of this call; it
  * exists for callers that cannot allocate device memory -- code running

@@ -21,15 +21,19 @@ namespace {
 
 thread_local std::string t_create_error;
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+// 0: pageable host memory, 1: page-locked host memory, 2: device memory
+int ptr_kind(const void* p) {
+    if (!p) return 0;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 2;
+    return a.type == cudaMemoryTypeHost ? 1 : 0;
 }
+
+bool is_device_ptr(const void* p) { return ptr_kind(p) == 2; }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -65,7 +69,17 @@ struct Engine {
     int32_t* st_del = nullptr;
     CountScratch cs{};
     int64_t max_u = 0;
+    // pinned host copies of host-pointer inputs, grown on demand, so that a
+    // call with many batches moves each input array with one copy
+    struct Pinned {
+        void* p = nullptr;
+        size_t bytes = 0;
+    } hs[4];
+    size_t hs_lo[4] = {};  // first element of hs[k] not yet copied in this call
     bool profiling = false;
+    // sizing pass: alloc() only adds up the bytes it would take
+    bool dry = false;
+    int64_t dry_bytes = 0;
     cudaEvent_t ev[6] = {};
     esc_batch_stats last{};
     LaunchCounter lc;
@@ -75,6 +89,11 @@ struct Engine {
     cudaError_t alloc(T** p, size_t n, int fill = 0) {
         size_t bytes = n * sizeof(T);
         if (bytes == 0) bytes = 16;
+        if (dry) {
+            dry_bytes += int64_t((bytes + 511) & ~size_t(511));
+            *p = nullptr;
+            return cudaSuccess;
+        }
         void* q = nullptr;
         cudaError_t e = cudaMalloc(&q, bytes);
         if (e != cudaSuccess) return e;
@@ -92,6 +111,8 @@ struct Engine {
         if (h_counts) cudaFreeHost(h_counts);
         if (h_ids) cudaFreeHost(h_ids);
         if (h_word) cudaFreeHost(h_word);
+        for (auto& h : hs)
+            if (h.p) cudaFreeHost(h.p);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -132,6 +153,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     E->st = st;
     ESC_CU(cudaGetDevice(&E->dev), "cudaGetDevice");
     ESC_CU(cudaDeviceGetAttribute(&E->sm_count, cudaDevAttrMultiProcessorCount, E->dev), "attribute");
+    const bool dry = E->dry;
     E->vbase.resize(G);
     E->ebase.resize(G);
     E->ecap.resize(G);
@@ -159,11 +181,13 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     ESC_CU(E->alloc(&eb, G), "alloc");
     ESC_CU(E->alloc(&ec, G), "alloc");
     ESC_CU(E->alloc(&nvp, G), "alloc");
-    ESC_CU(cudaMemcpyAsync(vb, E->vbase.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
-    ESC_CU(cudaMemcpyAsync(eb, E->ebase.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
-    ESC_CU(cudaMemcpyAsync(ec, E->ecap.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
-    ESC_CU(cudaMemcpyAsync(nvp, E->nv.data(), G * 4, cudaMemcpyHostToDevice, st), "copy");
-    ESC_CU(cudaStreamSynchronize(st), "sync");
+    if (!dry) {
+        ESC_CU(cudaMemcpyAsync(vb, E->vbase.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
+        ESC_CU(cudaMemcpyAsync(eb, E->ebase.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
+        ESC_CU(cudaMemcpyAsync(ec, E->ecap.data(), G * 8, cudaMemcpyHostToDevice, st), "copy");
+        ESC_CU(cudaMemcpyAsync(nvp, E->nv.data(), G * 4, cudaMemcpyHostToDevice, st), "copy");
+        ESC_CU(cudaStreamSynchronize(st), "sync");
+    }
     S.vbase = vb;
     S.ebase = eb;
     S.ecap = ec;
@@ -237,11 +261,13 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     ESC_CU(E->alloc(&E->st_mem, E->max_nnz), "alloc");
     ESC_CU(E->alloc(&E->st_ts, E->max_ins), "alloc");
     ESC_CU(E->alloc(&E->st_del, E->max_ins), "alloc");
-    ESC_CU(cudaMallocHost(&E->h_batches, sizeof(BatchIn) * G), "pinned");
-    ESC_CU(cudaMallocHost(&E->h_lo, sizeof(int64_t) * 2 * (G + 1)), "pinned");
-    ESC_CU(cudaMallocHost(&E->h_sc, sizeof(Scalars)), "pinned");
-    ESC_CU(cudaMallocHost(&E->h_counts, sizeof(uint64_t) * kCStride), "pinned");
-    ESC_CU(cudaMallocHost(&E->h_ids, sizeof(int32_t) * E->max_ins), "pinned");
+    if (!dry) {
+        ESC_CU(cudaMallocHost(&E->h_batches, sizeof(BatchIn) * G), "pinned");
+        ESC_CU(cudaMallocHost(&E->h_lo, sizeof(int64_t) * 2 * (G + 1)), "pinned");
+        ESC_CU(cudaMallocHost(&E->h_sc, sizeof(Scalars)), "pinned");
+        ESC_CU(cudaMallocHost(&E->h_counts, sizeof(uint64_t) * kCStride), "pinned");
+        ESC_CU(cudaMallocHost(&E->h_ids, sizeof(int32_t) * E->max_ins), "pinned");
+    }
     // counter scratch: neighbour lists for a run of changed hyperedges (runs
     // are split when the lists would not fit), per-ID inversion arrays, and
     // per-block overflow hash tables
@@ -259,15 +285,31 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     }
     sh.n_cta_nh = E->sm_count * 2;
     sh.n_cta_c = E->sm_count;
+    // restricted-list pool of a count run: 16 entries per incidence of the
+    // store, at least 2^24 and below 2^31 entries (int32 list offsets)
+    sh.r_cap = std::min<int64_t>(std::max<int64_t>(16 * inc, int64_t(1) << 24), (int64_t(1) << 31) - 64);
+    if (const char* env = getenv("ESC_COUNT_RPOOL")) {
+        long long v = atoll(env);
+        if (v >= 0 && v < (1ll << 31)) sh.r_cap = v;
+    }
+    if (dry) {
+        E->dry_bytes += int64_t(count_scratch_bytes(sh));
+        return ESC_OK;
+    }
     void* csmem = nullptr;
     ESC_CU(cudaMalloc(&csmem, count_scratch_bytes(sh)), "alloc count scratch");
     E->allocs.push_back(csmem);
     ESC_CU(cudaMallocHost(&E->h_word, sizeof(int64_t)), "pinned");
     ESC_CU(count_scratch_init(&E->cs, csmem, sh, E->h_word, st), "scratch init");
     E->max_u = count_max_u(sh);
-    // test knob: shrink the shared-memory tables so that the global-table
-    // and partitioned paths run on small inputs
+    // test knobs: shrink the shared-memory tables so that the global-table
+    // and partitioned paths run on small inputs; lower the neighbourhood size
+    // from which restricted lists are built
     if (const char* env = getenv("ESC_CENTER_SMALL")) E->cs.center_small = atoi(env) != 0;
+    if (const char* env = getenv("ESC_COUNT_RMIN")) {
+        long long v = atoll(env);
+        if (v >= 1) E->cs.r_min = v;
+    }
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
         long long v = atoll(env);
         if (v >= 64 && (v & (v - 1)) == 0) E->cs.smem_slots = v;
@@ -308,19 +350,65 @@ static std::string describe(const Scalars& s) {
     return buf;
 }
 
-// Stage one input array to the device if it is a host pointer.
+// Copy the packed elements [hs_lo[k], used) of hs[k] to the device.
 template <typename T>
-static esc_status stage(Engine* E, const T* src, size_t n, T* dst_area, size_t& used, size_t cap, const T** out) {
+static esc_status flush_staged(Engine* E, T* dst_area, int k, size_t used) {
+    const size_t lo = E->hs_lo[k];
+    if (used > lo)
+        ESC_CU(cudaMemcpyAsync(dst_area + lo, static_cast<T*>(E->hs[k].p) + lo, (used - lo) * sizeof(T),
+                               cudaMemcpyHostToDevice, E->st),
+               "stage");
+    E->hs_lo[k] = used;
+    return ESC_OK;
+}
+
+// Stage one input array: a device pointer is used in place; page-locked host
+// memory is copied directly to dst_area + used; pageable host memory is
+// packed into the pinned buffer hs[k] at element offset `used`, and the packed
+// runs go to the device by flush_staged() (one copy per run, normally one per
+// array per call).
+template <typename T>
+static esc_status stage(Engine* E, const T* src, size_t n, T* dst_area, int k, size_t& used, size_t cap,
+                        const T** out) {
     if (n == 0 || src == nullptr) {
         *out = src;
         return ESC_OK;
     }
-    if (is_device_ptr(src)) {
+    const int kind = ptr_kind(src);
+    if (kind == 2) {
         *out = src;
         return ESC_OK;
     }
     if (used + n > cap) return E->fail(ESC_ERR_OUT_OF_MEMORY, "batch larger than the staging capacity");
-    ESC_CU(cudaMemcpyAsync(dst_area + used, src, n * sizeof(T), cudaMemcpyHostToDevice, E->st), "stage");
+    if (kind == 1) {
+        // page-locked already: copy straight from the caller's buffer (the
+        // call synchronises before it returns), after the packed run before it
+        esc_status s = flush_staged(E, dst_area, k, used);
+        if (s != ESC_OK) return s;
+        E->hs_lo[k] = used + n;
+        ESC_CU(cudaMemcpyAsync(dst_area + used, src, n * sizeof(T), cudaMemcpyHostToDevice, E->st), "stage");
+        *out = dst_area + used;
+        used += n;
+        return ESC_OK;
+    }
+    Engine::Pinned& h = E->hs[k];
+    const size_t need = (used + n) * sizeof(T);
+    if (need > h.bytes) {
+        // earlier calls have synchronised; a run of this call already sent
+        // from the old buffer must land before the buffer is freed
+        if (E->hs_lo[k] > 0) ESC_CU(cudaStreamSynchronize(E->st), "sync");
+        size_t nb = std::max(need, std::max(2 * h.bytes, size_t(1) << 20));
+        nb = std::min(nb, std::max(need, cap * sizeof(T)));
+        void* q = nullptr;
+        ESC_CU(cudaMallocHost(&q, nb), "pinned staging");
+        if (h.p) {
+            memcpy(q, h.p, used * sizeof(T));
+            cudaFreeHost(h.p);
+        }
+        h.p = q;
+        h.bytes = nb;
+    }
+    memcpy(static_cast<T*>(h.p) + used, src, n * sizeof(T));
     *out = dst_area + used;
     used += n;
     return ESC_OK;
@@ -349,6 +437,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     cudaStream_t st = E->st;
     // stage host inputs
     size_t u_off = 0, u_mem = 0, u_ts = 0, u_del = 0;
+    for (auto& lo : E->hs_lo) lo = 0;
     int64_t* bins = E->h_lo;
     int64_t* bdel = E->h_lo + (E->G + 1);
     bins[0] = bdel[0] = 0;
@@ -369,25 +458,33 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
         B.del = nullptr;
         if (x.n_ins > 0) {
             bool off_dev = is_device_ptr(x.ins_offsets);
-            if ((s = stage(E, x.ins_offsets, size_t(x.n_ins + 1), E->st_off, u_off, size_t(E->max_ins + E->G + 1),
-                           &B.off)) != ESC_OK)
+            if ((s = stage(E, x.ins_offsets, size_t(x.n_ins + 1), E->st_off, 0, u_off,
+                           size_t(E->max_ins + E->G + 1), &B.off)) != ESC_OK)
                 return s;
             if (!off_dev) {
                 int64_t nnz = x.ins_offsets[x.n_ins] - x.ins_offsets[0];
                 if (x.ins_offsets[0] != 0 || nnz < 0) return E->fail(ESC_ERR_INVALID_ARG, "offsets must start at 0");
                 if (nnz > E->max_nnz) return E->fail(ESC_ERR_OUT_OF_MEMORY, "batch members exceed max_batch_incidences");
-                if ((s = stage(E, x.ins_members, size_t(nnz), E->st_mem, u_mem, size_t(E->max_nnz), &B.mem)) != ESC_OK)
+                if ((s = stage(E, x.ins_members, size_t(nnz), E->st_mem, 1, u_mem, size_t(E->max_nnz), &B.mem)) !=
+                    ESC_OK)
                     return s;
             } else {
                 if (is_device_ptr(x.ins_members)) B.mem = x.ins_members;
                 else return E->fail(ESC_ERR_INVALID_ARG, "device offsets need device members");
             }
-            if ((s = stage(E, x.ins_timestamps, size_t(x.n_ins), E->st_ts, u_ts, size_t(E->max_ins), &B.ts)) != ESC_OK)
+            if ((s = stage(E, x.ins_timestamps, size_t(x.n_ins), E->st_ts, 2, u_ts, size_t(E->max_ins), &B.ts)) !=
+                ESC_OK)
                 return s;
         }
         if (x.n_del > 0)
-            if ((s = stage(E, x.del_ids, size_t(x.n_del), E->st_del, u_del, size_t(E->max_ins), &B.del)) != ESC_OK)
+            if ((s = stage(E, x.del_ids, size_t(x.n_del), E->st_del, 3, u_del, size_t(E->max_ins), &B.del)) != ESC_OK)
                 return s;
+    }
+    {
+        esc_status s;
+        if ((s = flush_staged(E, E->st_off, 0, u_off)) != ESC_OK || (s = flush_staged(E, E->st_mem, 1, u_mem)) != ESC_OK ||
+            (s = flush_staged(E, E->st_ts, 2, u_ts)) != ESC_OK || (s = flush_staged(E, E->st_del, 3, u_del)) != ESC_OK)
+            return s;
     }
     ESC_CU(cudaMemcpyAsync(E->d_batches, E->h_batches, sizeof(BatchIn) * n, cudaMemcpyHostToDevice, st), "copy");
     ESC_CU(cudaMemcpyAsync(E->d_bins_lo, bins, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st), "copy");
@@ -564,6 +661,20 @@ struct esc_group {
     Engine* e;
 };
 
+namespace esc {
+esc_status group_limits(const esc_group* grp, int32_t* n_graphs, int64_t* max_updates, int64_t* max_nnz,
+                        uint32_t* families, int* device) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    const Engine* E = grp->e;
+    *n_graphs = E->G;
+    *max_updates = E->max_ins;
+    *max_nnz = E->max_nnz;
+    *families = E->shared.families;
+    *device = E->dev;
+    return ESC_OK;
+}
+}  // namespace esc
+
 extern "C" {
 
 const char* esc_version(void) { return "escher-gb300 0.1 (sm_103a)"; }
@@ -590,6 +701,22 @@ esc_status esc_group_create(const esc_config* shared, int32_t n_graphs, const es
         return s;
     }
     *out = new esc_group{E};
+    return ESC_OK;
+}
+
+esc_status esc_group_bytes(const esc_config* shared, int32_t n_graphs, const esc_config* graph_cfg,
+                           int64_t* out_bytes) {
+    if (!out_bytes) return ESC_ERR_INVALID_ARG;
+    *out_bytes = 0;
+    esc_status s = esc::check_cfg(shared, false);
+    if (s != ESC_OK || n_graphs <= 0 || !graph_cfg) return s != ESC_OK ? s : ESC_ERR_INVALID_ARG;
+    for (int g = 0; g < n_graphs; ++g)
+        if ((s = esc::check_cfg(&graph_cfg[g], true)) != ESC_OK) return s;
+    Engine E;
+    E.dry = true;
+    s = esc::build_engine(&E, *shared, n_graphs, graph_cfg, nullptr);
+    if (s != ESC_OK) return s;
+    *out_bytes = E.dry_bytes;
     return ESC_OK;
 }
 

@@ -120,6 +120,38 @@ __device__ __forceinline__ int tab_insert(const Tab& T, int32_t k, uint32_t inc,
     return int(s);
 }
 
+// Insert into a table kept in the neighbour-list arena: key in keys[s], and
+// x (count) and the smallest shared vertex packed into one 64-bit word xv[s]
+// (x in the low half, the vertex in the high half) -- the layout in which a
+// large N(h) is handed to k_center, so the table needs no copy.
+__device__ __forceinline__ void tab_insert_packed(const Tab& T, uint64_t* xv, int32_t k, int32_t aux_min,
+                                                  Scalars* sc) {
+    uint32_t s = fmix32(uint32_t(k)) & T.mask;
+    volatile int32_t* vk = T.keys;
+    for (uint32_t probe = 0;; ++probe) {
+        int32_t cur = vk[s];
+        if (cur == k) break;
+        if (cur == EMPTY) {
+            int32_t old = atomicCAS(&T.keys[s], EMPTY, k);
+            if (old == EMPTY) {
+                int p = atomicAdd(T.n, 1);
+                if (p < T.list_cap) T.list[p] = int32_t(s);
+                else set_error(sc, kErrUnsupported, -6, p, T.list_cap);
+                break;
+            }
+            if (old == k) break;
+        }
+        s = (s + 1) & T.mask;
+        if (probe > T.mask) {
+            set_error(sc, kErrUnsupported, -7, k, T.mask);
+            return;
+        }
+    }
+    unsigned int* w = reinterpret_cast<unsigned int*>(xv + s);  // little-endian halves
+    atomicAdd(w, 1u);
+    atomicMin(w + 1, unsigned(aux_min));
+}
+
 __device__ __forceinline__ int tab_find(const Tab& T, int32_t k) {
     uint32_t s = fmix32(uint32_t(k)) & T.mask;
     for (uint32_t probe = 0; probe <= T.mask; ++probe) {
@@ -351,6 +383,7 @@ struct SmemNH {
     int warp_tmp[32];
     long long red[NT_NH / 32];
     long long item;
+    long long r_at;
     int n_list;
     unsigned long long acc[128];      // open-at-h class counts of this block
     uint32_t hx[2][kHistSmem + 1];    // x histograms of N'(h), split by [g inside h]
@@ -362,6 +395,79 @@ struct SmemNH {
 // |g2| - x2, h&g1 and h&g2 non-empty, the rest empty.
 __device__ __forceinline__ int open_at_h_mask(int kh, int x1, int x2, int k1, int k2) {
     return (kh != x1 + x2 ? 1 : 0) | (k1 != x1 ? 2 : 0) | (k2 != x2 ? 4 : 0) | (1 << 3) | (1 << 5);
+}
+
+// Restricted incidence lists of a large N(h): R(u) = {f in N(h) : u in f}
+// for every vertex u of h's graph, as a dense index idx[0..nv] and the lists
+// ent[idx[u] .. idx[u+1]).  k_center walks R(u) for the members u of a
+// candidate g1 instead of all of N(g1): N(g1) and N(h) then meet in
+// sum over u in g1 of |R(u)| steps rather than sum of member degrees.
+// Entries are counted per vertex, prefix-summed (idx[u] = end of R(u)) and
+// scattered downwards (idx[u] ends at the start of R(u)).
+__device__ void build_rlist(const CountArgs& A, SmemNH& s, int64_t i, int g, int64_t base, int nn) {
+    const Store& S = A.S;
+    const CountScratch& cs = A.cs;
+    const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
+    constexpr int NW = NT_NH / 32;
+    __syncthreads();
+    long long eh = 0;
+    for (int q = tid; q < nn; q += NT_NH) eh += S.h_card[cs.nh_g[base + q]];
+    eh = block_sum<NT_NH>(eh, s.red);
+    const int64_t nvg = S.nv[g];
+    if (tid == 0) {
+        s.r_at = -1;
+        const unsigned long long need = (unsigned long long)((nvg + 1 + eh + 3) & ~3ll);
+        if (nvg <= 4 * eh) {
+            const unsigned long long at = atomicAdd(&A.sc->r_used[A.side], need);
+            if (at + need <= (unsigned long long)cs.r_cap) s.r_at = (long long)at;
+        }
+        cs.r_off[i] = s.r_at;
+    }
+    __syncthreads();
+    const long long at = s.r_at;
+    if (at < 0) return;
+    int32_t* idx = cs.r_pool + at;
+    int32_t* ent = idx + nvg + 1;
+    const int64_t vb = S.vbase[g];
+    const int32_t* h2v = S.hp.arena;
+    for (int64_t t = tid; t < nvg; t += NT_NH) idx[t] = 0;
+    if (tid == 0) idx[nvg] = int32_t(eh);
+    __syncthreads();
+    for (int q = wid; q < nn; q += NW) {
+        const int32_t f = cs.nh_g[base + q];
+        const int32_t* fm = h2v + S.h_off[f];
+        const int kf = S.h_card[f];
+        for (int m = lane; m < kf; m += 32) atomicAdd(&idx[fm[m] - vb], 1);
+    }
+    __syncthreads();
+    // inclusive prefix over idx[0..nvg), in tiles of 4 entries per thread
+    int carry = 0;
+    for (int64_t t0 = 0; t0 < nvg; t0 += NT_NH * 4) {
+        int v[4], loc = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t j = t0 + tid * 4 + k;
+            v[k] = j < nvg ? idx[j] : 0;
+            loc += v[k];
+        }
+        int tot;
+        int pre = block_exclusive_scan<NT_NH>(loc, &tot, s.warp_tmp) + carry;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t j = t0 + tid * 4 + k;
+            pre += v[k];
+            if (j < nvg) idx[j] = pre;
+        }
+        carry += tot;
+    }
+    __syncthreads();
+    for (int q = wid; q < nn; q += NW) {
+        const int32_t f = cs.nh_g[base + q];
+        const int32_t* fm = h2v + S.h_off[f];
+        const int kf = S.h_card[f];
+        for (int m = lane; m < kf; m += 32) ent[atomicSub(&idx[fm[m] - vb], 1) - 1] = f;
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
@@ -382,6 +488,9 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
     if (tid == 0) s.n_list = 0;
     // open-at-h triads are counted in aggregate unless the temporal family is kept
     const bool agg = (fam & kFamH) && !(fam & kFamT);
+    // without the temporal family k_center may meet N(g1) and a large N(h)
+    // through restricted lists
+    const bool use_r = !(fam & kFamT) && cs.r_cap > 0;
     uint32_t* ghx = cs.onh_hist + int64_t(blockIdx.x) * 2 * (kMaxCard + 1);
     __syncthreads();
     const int64_t gs = cs.gs_nh;
@@ -409,18 +518,23 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         uh = block_sum<NT_NH>(uh, s.red);
         Tab NH;
         const uint32_t cap = pow2_at_least(2 * uh);
+        const int64_t base = cs.nh_off[i];
+        // a neighbourhood too large for the block's tables is built in place,
+        // in the table part of its own list region (see k_nh_size)
+        const bool huge = cap > A.nh_smem_cap && (int64_t)cap > gs;
+        uint64_t* const xv_t = cs.nh_xv + base + uh;
         if (cap <= A.nh_smem_cap) {
             NH = Tab{s.keys, s.vals, s.aux, s.list, &s.n_list, cap - 1, NH_S / 2};
-        } else if ((int64_t)cap <= gs) {
+        } else if (!huge) {
             NH = gNH;
             NH.mask = cap - 1;
         } else {
-            if (tid == 0) {
-                set_error(A.sc, kErrUnsupported, -8, h, uh);
-                cs.nh_n[i] = 0;
-                cs.nh_tcap[i] = 0;
+            NH = Tab{cs.nh_g + base + uh, nullptr, nullptr, cs.nh_g + base, &s.n_list, cap - 1, int(uh)};
+            for (uint32_t t = tid; t < cap; t += NT_NH) {
+                NH.keys[t] = EMPTY;
+                xv_t[t] = uint64_t(uint32_t(INT_MAX)) << 32;
             }
-            continue;
+            __syncthreads();
         }
         acc.n_h2v += (tid < kh) ? (kh - tid + NT_NH - 1) / NT_NH : 0;
         if (tid == 0) acc.n_alg += (unsigned long long)(uh + kh);
@@ -430,7 +544,9 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             for (int e = tid; e < tot; e += NT_NH) {
                 const int m = seg_member(s.seg_pre, n, e);
                 const int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
-                if (f != h) tab_insert(NH, f, 1u, s.seg_v[m], A.sc);
+                if (f == h) continue;
+                if (huge) tab_insert_packed(NH, xv_t, f, s.seg_v[m], A.sc);
+                else tab_insert(NH, f, 1u, s.seg_v[m], A.sc);
             }
             acc.n_v2h += (tid < tot) ? (tot - tid + NT_NH - 1) / NT_NH : 0;
             __syncthreads();
@@ -438,13 +554,15 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         // distinct neighbours never outnumber the region reserved for them
         // (sum of member degrees); the clamp only matters after an error
         const int nn = int(min((long long)min(s.n_list, NH.list_cap), uh));
-        const int64_t base = cs.nh_off[i];
         for (int q = tid; q < nn; q += NT_NH) {
+            // in place, the list of taken slots is the list region itself:
+            // each entry is read and then overwritten by the same thread
             const int sl = NH.list[q];
             const int32_t gg = NH.keys[sl];
-            const uint32_t x = NH.vals[sl];
+            const uint64_t xvq = huge ? xv_t[sl] : uint64_t(NH.vals[sl]) | (uint64_t(uint32_t(NH.aux[sl])) << 32);
+            const uint32_t x = uint32_t(xvq);
             cs.nh_g[base + q] = gg;
-            cs.nh_xv[base + q] = uint64_t(x) | (uint64_t(uint32_t(NH.aux[sl])) << 32);
+            cs.nh_xv[base + q] = xvq;
             if (gg < h && bit_test(A.chg, gg)) continue;  // pair attributed elsewhere
             if (atomicAdd(&cs.lcnt[gg], 1) == 0) cs.d_list[atomicAdd(&A.sc->n_d[A.side], 1)] = gg;
             if ((fam & kFamV) && x >= 2)
@@ -452,7 +570,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         }
         // a large N(h) also goes out as its hash table, probed by k_center
         const bool big = uh > kBigNH;
-        if (big) {
+        if (big && !huge) {
             const int64_t toff = base + uh;
             for (uint32_t t = tid; t <= NH.mask; t += NT_NH) {
                 const int32_t key = NH.keys[t];
@@ -467,6 +585,21 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             cs.nh_tcap[i] = big ? int32_t(NH.mask + 1) : 0;
             if ((fam & kFamV) && kh >= 3) acc.v1 += (unsigned long long)kh * (kh - 1) * (kh - 2) / 6;
         }
+        if (use_r && big && uh >= cs.r_min) build_rlist(A, s, i, g, base, nn);
+        else if (tid == 0) cs.r_off[i] = -1;
+        // entry q of N(h): from the block's table, or from the list just
+        // written when the table was built in place
+        if (huge) __syncthreads();
+        auto entry = [&](int q, int32_t& gg, int& x) {
+            if (huge) {
+                gg = cs.nh_g[base + q];
+                x = int(uint32_t(cs.nh_xv[base + q]));
+            } else {
+                const int sl = NH.list[q];
+                gg = NH.keys[sl];
+                x = int(NH.vals[sl]);
+            }
+        };
         if (agg) {
             // open triads centred at h, in aggregate over the pairs of N'(h)
             // (N(h) without the neighbours attributed elsewhere): the class is
@@ -476,10 +609,10 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             const int hstride = kh <= kHistSmem ? kHistSmem + 1 : kMaxCard + 1;
             unsigned long long n1w = 0, n0w = 0;
             for (int q = tid; q < nn; q += NT_NH) {
-                const int sl = NH.list[q];
-                const int32_t gg = NH.keys[sl];
+                int32_t gg;
+                int x;
+                entry(q, gg, x);
                 if (gg < h && bit_test(A.chg, gg)) continue;
-                const int x = int(NH.vals[sl]);
                 const int in = S.h_card[gg] == x ? 1 : 0;
                 atomicAdd(&H[in * hstride + x], 1u);
                 if (in) ++n1w; else ++n0w;
@@ -523,14 +656,15 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             }
             __syncthreads();
             for (int q = tid; q < nn; q += NT_NH) {
-                const int sl = NH.list[q];
-                const int x = int(NH.vals[sl]);
+                int32_t gg;
+                int x;
+                entry(q, gg, x);
                 H[x] = 0;
                 H[hstride + x] = 0;
             }
         }
         __syncthreads();
-        tab_clear<NT_NH>(NH, nn);
+        if (!huge) tab_clear<NT_NH>(NH, nn);
         __syncthreads();
         if (tid == 0) s.n_list = 0;
     }
@@ -624,7 +758,8 @@ struct SmemC {
     int32_t hh[LCH], hk[LCH], hx[LCH], hvf[LCH], hli[LCH], hnn[LCH], htcap[LCH];
     int64_t hts[LCH], hnb[LCH], htoff[LCH];
     const int32_t* hmem[LCH];
-    int32_t hfrom[LCH];        // 1: visit N(g1) probing N(h)'s table, 0: visit N(h)
+    int32_t hfrom[LCH];        // 0: visit N(h); 1: visit N(g1) probing N(h)'s table; 2: restricted lists
+    int64_t hr[LCH];           // start of h's restricted lists in the pool, -1: none
     int32_t hpre[LCH + 1];     // prefix of the per-h work of pass (i)
     uint32_t sub[LCH][4];
     uint32_t xc[LCH][2];
@@ -794,6 +929,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
             s.hnn[tid] = cs.nh_n[li];
             s.htcap[tid] = cs.nh_tcap[li];
             s.htoff[tid] = cs.nh_toff[li];
+            s.hr[tid] = cs.r_off[li];
             s.hIn[tid] = 0;
         }
         __syncthreads();
@@ -872,9 +1008,18 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 int run = 0;
                 for (int l = 0; l < nh; ++l) {
                     s.hpre[l] = run;
-                    const bool from = agg && s.htcap[l] > 0 && s.hnn[l] > n1;
-                    s.hfrom[l] = from ? 1 : 0;
-                    run += from ? n1 : s.hnn[l];
+                    int mode = 0, work = s.hnn[l];
+                    if (!want_t && s.htcap[l] > 0) {
+                        if (s.hr[l] >= 0 && k1 < min(s.hnn[l], n1)) {
+                            mode = 2;
+                            work = k1;
+                        } else if (s.hnn[l] > n1) {
+                            mode = 1;
+                            work = n1;
+                        }
+                    }
+                    s.hfrom[l] = mode;
+                    run += work;
                 }
                 s.hpre[nh] = run;
             }
@@ -884,11 +1029,38 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
             // ---- (i) the pairs {g1, g2}, g2 in N(h), for every h of the item.
             // Every g2 also in N(g1) (a closed pair) is marked for that h and
             // counted at g1 < g2 unless g2 is a changed hyperedge of smaller
-            // ID than h.  In aggregate mode the open pairs were counted by
-            // k_nh_build and only the closed ones are visited: from the
-            // smaller of N(h) and N(g1), probing the other's hash table.
+            // ID than h.  With the temporal family every g2 of N(h) is visited
+            // (the open pairs centred at h are enumerated); otherwise the
+            // closed pairs are found from the smaller of N(h) and N(g1),
+            // probing the other's hash table, or, for an h with restricted
+            // lists, from R(u) for the members u of g1.
             const int wtot = s.hpre[nh];
             if (tid == 0) acc.w[2] += (unsigned long long)wtot;
+            // a closed pair {g1, g2} for the item's l-th h
+            auto closed = [&](int l, int32_t h, int32_t g2, int sl, int xh2, int32_t vf2, int k2, bool chg2,
+                              int& skey, bool direct) {
+                const int kh = s.hk[l], xh1 = s.hx[l];
+                const int x12 = int(T1.vals[sl]);
+                if (want_open && !direct) atomicOr(&mark[sl], 1u << l);
+                if (agg) {
+                    const int b = (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 1 : 0);
+                    if (direct) atomicAdd(&s.sub[l][b], 1u);
+                    else skey = l * 4 + b;
+                }
+                if (g2 > g1 && !(g2 < h && chg2)) {
+                    ++acc.n_meta;
+                    ++acc.w[3];
+                    const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
+                                              kh, s.hI[l], s.hIn[l], acc.w[4]);
+                    if (want_open)
+                        classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l], ts1,
+                                 want_t ? S.h_ts[g2] : 0, acc);
+                    if (agg) atomicAdd(&s.hneg[wid][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
+                    if (fam & kFamV)
+                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
+                                  2ull * t;
+                }
+            };
             for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
                 const int idx = idx0 + tid;
                 int skey = -1;
@@ -901,62 +1073,56 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                     }
                     const int q = idx - s.hpre[l];
                     const int32_t h = s.hh[l];
-                    int32_t g2;
-                    int sl = -1, x12 = 0, xh2, k2 = 0;
-                    int32_t vf2;
-                    bool chg2;
-                    if (s.hfrom[l]) {
-                        sl = T1.list[q];
-                        g2 = T1.keys[sl];
-                        const int ps =
-                            probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), g2);
-                        if (ps < 0) {
-                            sl = -1;
-                        } else {
+                    const int mode = s.hfrom[l];
+                    if (mode == 2) {
+                        // the neighbours f of h holding the q-th member u of g1:
+                        // each is in N(g1); one met through several shared
+                        // vertices is taken once (its mark bit)
+                        const int32_t* ridx = cs.r_pool + s.hr[l];
+                        const int32_t* ent = ridx + S.nv[g] + 1;
+                        const int64_t lu = int64_t(g1mem[q]) - S.vbase[g];
+                        const int e1 = ridx[lu + 1];
+                        for (int e = ridx[lu]; e < e1; ++e) {
+                            ++acc.w[2];
+                            const int32_t f = ent[e];
+                            if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
+                            const int sl = tab_find(T1, f);
+                            if (sl < 0) continue;
+                            if ((atomicOr(&mark[sl], 1u << l) >> l) & 1u) continue;
+                            const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), f);
+                            if (ps < 0) continue;
                             const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
-                            xh2 = int(xv2 & kXMask);
-                            vf2 = int32_t(uint32_t(xv2 >> 32));
+                            int unused;
+                            closed(l, h, f, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), S.h_card[f],
+                                   bit_test(A.chg, f), unused, true);
+                        }
+                    } else if (mode == 1) {
+                        const int sl = T1.list[q];
+                        const int32_t g2 = T1.keys[sl];
+                        const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), g2);
+                        if (ps >= 0) {
+                            const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
                             const int32_t meta = lk[q];
-                            k2 = meta & 0x7fffffff;
-                            chg2 = meta < 0;
+                            closed(l, h, g2, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), meta & 0x7fffffff,
+                                   meta < 0, skey, false);
                         }
                     } else {
-                        g2 = cs.nh_g[s.hnb[l] + q];
+                        const int32_t g2 = cs.nh_g[s.hnb[l] + q];
                         if (P == 1 || part_of(g2, P) == p) {
-                            sl = tab_find(T1, g2);
+                            const int sl = tab_find(T1, g2);
                             if (sl >= 0 || (!agg && want_open)) {
                                 const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
-                                xh2 = int(xv2 & kXMask);
-                                vf2 = int32_t(uint32_t(xv2 >> 32));
+                                const int xh2 = int(xv2 & kXMask);
+                                const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
+                                if (sl >= 0) {
+                                    closed(l, h, g2, sl, xh2, vf2, S.h_card[g2], bit_test(A.chg, g2), skey, false);
+                                } else if (g2 > g1 && !(g2 < h && bit_test(A.chg, g2))) {
+                                    // open pair centred at h, enumerated (temporal family kept)
+                                    ++acc.n_meta;
+                                    classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, S.h_card[g2], s.hx[l],
+                                             0, xh2, 0, s.hts[l], ts1, want_t ? S.h_ts[g2] : 0, acc);
+                                }
                             }
-                            if (sl >= 0) {
-                                k2 = S.h_card[g2];
-                                chg2 = bit_test(A.chg, g2);
-                            } else if (!agg && want_open && g2 > g1 && !(g2 < h && bit_test(A.chg, g2))) {
-                                // open pair centred at h, enumerated (temporal family kept)
-                                ++acc.n_meta;
-                                classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, S.h_card[g2], s.hx[l], 0,
-                                         xh2, 0, s.hts[l], ts1, want_t ? S.h_ts[g2] : 0, acc);
-                            }
-                        }
-                    }
-                    if (sl >= 0) {
-                        const int kh = s.hk[l], xh1 = s.hx[l];
-                        x12 = int(T1.vals[sl]);
-                        if (want_open) atomicOr(&mark[sl], 1u << l);
-                        if (agg) skey = l * 4 + ((x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 1 : 0));
-                        if (g2 > g1 && !(g2 < h && chg2)) {
-                            ++acc.n_meta;
-                            ++acc.w[3];
-                            const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2,
-                                                      s.hmem[l], kh, s.hI[l], s.hIn[l], acc.w[4]);
-                            if (want_open)
-                                classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l],
-                                         ts1, want_t ? S.h_ts[g2] : 0, acc);
-                            if (agg) atomicAdd(&s.hneg[wid][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
-                            if (fam & kFamV)
-                                acc.v3 += (unsigned long long)xh1 * x12 * xh2 -
-                                          (unsigned long long)t * (xh1 + x12 + xh2) + 2ull * t;
                         }
                     }
                 }
@@ -1155,6 +1321,7 @@ __global__ void k_scan_apply(const In* in, int64_t n_host, const int32_t* n_dev,
 }
 
 __global__ void k_run_begin(Scalars* sc, int side) {
+    sc->r_used[side] = 0;
     sc->qnh[side] = 0;
     sc->queue[side] = 0;
     sc->n_d[side] = 0;
@@ -1181,6 +1348,7 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 2 * al(sizeof(int32_t) * sh.e_cap) + al(sizeof(int64_t) * sh.e_cap);
     b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
     b += al(sizeof(int64_t) * nbs);
+    b += al(sizeof(int32_t) * sh.r_cap) + al(sizeof(int64_t) * sh.cap);
     const int64_t rn = sh.n_cta_nh, rc = 2 * int64_t(sh.n_cta_c);  // centre grid is up to 2 blocks per SM
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
     b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
@@ -1226,6 +1394,9 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->d_item_start = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.e_cap + 1)));
     cs->block_sums = static_cast<int64_t*>(take(sizeof(int64_t) * nbs));
     cs->n_block_sums = nbs;
+    cs->r_cap = sh.r_cap;
+    cs->r_pool = static_cast<int32_t*>(take(sizeof(int32_t) * sh.r_cap));
+    cs->r_off = static_cast<int64_t*>(take(sizeof(int64_t) * sh.cap));
     const int64_t rn = sh.n_cta_nh, rc = 2 * int64_t(sh.n_cta_c);  // centre grid is up to 2 blocks per SM
     cs->onh_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
     cs->onh_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rn * sh.gs_nh));

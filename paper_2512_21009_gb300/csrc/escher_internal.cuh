@@ -72,6 +72,7 @@ struct Scalars {
     unsigned long long qnh[2];    // neighbourhood-build queues
     int64_t items[2];     // centre work items
     int32_t n_d[2];       // distinct candidate neighbours g1 of one count run
+    unsigned long long r_used[2];  // int32 entries of the restricted-list pool taken in this run
     unsigned long long stats[16]; // v2h, h2v, meta reads, triads, algorithmic entries, then counter work
 };
 

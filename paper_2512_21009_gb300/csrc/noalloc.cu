@@ -41,6 +41,7 @@ CountShape na_shape() {
     sh.e_cap = kNAMaxHyperedges;
     sh.gs_nh = sh.gs_c = kNATableSlots;
     sh.n_cta_nh = sh.n_cta_c = kNABlocks;
+    sh.r_cap = 0;  // no restricted lists
     return sh;
 }
 

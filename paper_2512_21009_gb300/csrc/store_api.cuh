@@ -59,6 +59,13 @@ struct CountScratch {
     int32_t* oc_list = nullptr;
     int32_t* oc_lk = nullptr;
     int64_t* oc_lts = nullptr;
+    // restricted incidence lists of a large N(h): for each vertex u of the
+    // graph, the neighbours f of h that hold u (a dense index over the
+    // graph's vertices, then the lists)
+    int32_t* r_pool = nullptr;       // [r_cap] int32 entries
+    int64_t r_cap = 0;
+    int64_t* r_off = nullptr;        // [cap] start of h's index in the pool, -1: none
+    int64_t r_min = 4096;            // sum of member degrees from which h gets the lists
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 1;            // 1: two 256-thread centre blocks per SM, 0: one 512-thread block
     int64_t* h_total = nullptr;      // pinned host word for the list total
@@ -70,13 +77,14 @@ struct CountShape {
     int64_t e_cap;      // hyperedge IDs of the store
     int64_t gs_nh, gs_c;
     int n_cta_nh, n_cta_c;
+    int64_t r_cap;      // int32 entries of the restricted-list pool (0: none)
 };
 
 // Largest neighbour-entry count sum(deg) of a changed hyperedge the counter
 // accepts with the given shape.
 inline int64_t count_max_u(const CountShape& sh) {
-    int64_t a = sh.gs_nh / 2;
-    return a < sh.list_cap / 8 ? a : sh.list_cap / 8;
+    // a neighbourhood takes at most 5 u list entries (list + table)
+    return sh.list_cap / 8;
 }
 
 size_t count_scratch_bytes(const CountShape& sh);

@@ -26,7 +26,8 @@ FAMILY_TEMPORAL = 4
 TRIAD_HYPEREDGE, TRIAD_VERTEX, TRIAD_TEMPORAL = 0, 1, 2
 N_CLASSES = {TRIAD_HYPEREDGE: 30, TRIAD_VERTEX: 3, TRIAD_TEMPORAL: 96}
 STATUS = {0: "ESC_OK", 1: "ESC_ERR_INVALID_ARG", 2: "ESC_ERR_NOT_FOUND", 3: "ESC_ERR_OUT_OF_MEMORY",
-          4: "ESC_ERR_UNSUPPORTED", 5: "ESC_ERR_TIMEOUT", 6: "ESC_ERR_CUDA"}
+          4: "ESC_ERR_UNSUPPORTED", 5: "ESC_ERR_TIMEOUT", 6: "ESC_ERR_CUDA", 7: "ESC_ERR_BUSY"}
+ESC_ERR_BUSY = 7
 
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = [
@@ -34,6 +35,8 @@ EXPORTED = [
     "esc_export_sizes", "esc_export", "esc_set_profiling", "esc_last_stats", "esc_launch_count",
     "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
     "esc_group_last_error", "esc_group_set_profiling", "esc_group_last_stats", "esc_group_launch_count",
+    "esc_group_bytes", "esc_server_create", "esc_server_submit", "esc_server_wait", "esc_server_drain",
+    "esc_server_triads", "esc_server_get_stats", "esc_server_destroy",
     "esc_version", "esc_count_static_noalloc",
 ]
 
@@ -63,6 +66,17 @@ class esc_batch(C.Structure):
     _fields_ = [("graph", C.c_int32), ("n_ins", C.c_int64), ("ins_offsets", C.c_void_p),
                 ("ins_members", C.c_void_p), ("ins_timestamps", C.c_void_p), ("n_del", C.c_int64),
                 ("del_ids", C.c_void_p), ("out_ins_ids", C.c_void_p)]
+
+
+class esc_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("call_batches", C.c_int32), ("t_arrival_ns", C.c_int64),
+                ("t_start_ns", C.c_int64), ("t_done_ns", C.c_int64), ("call_updates", C.c_int64)]
+
+
+class esc_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("rejected", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("calls", C.c_int64), ("updates", C.c_int64),
+                ("pending_updates", C.c_int64)]
 
 
 _lib = None
@@ -102,13 +116,23 @@ def load(path: str = LIB_PATH):
     L.esc_group_last_stats.argtypes = [vp, C.POINTER(esc_batch_stats)]
     L.esc_group_launch_count.argtypes = [vp]
     L.esc_group_launch_count.restype = i64
+    L.esc_group_bytes.argtypes = [C.POINTER(esc_config), i32, C.POINTER(esc_config), C.POINTER(i64)]
+    L.esc_server_create.argtypes = [vp, i64, i32, C.POINTER(vp)]
+    L.esc_server_submit.argtypes = [vp, C.POINTER(esc_batch), i64, C.POINTER(i64)]
+    L.esc_server_wait.argtypes = [vp, i64, C.POINTER(esc_request_info)]
+    L.esc_server_drain.argtypes = [vp]
+    L.esc_server_triads.argtypes = [vp, i32, C.c_int, i64, vp, i32]
+    L.esc_server_get_stats.argtypes = [vp, C.POINTER(esc_server_stats)]
+    L.esc_server_destroy.argtypes = [vp]
     L.esc_version.restype = C.c_char_p
     L.esc_count_static_noalloc.argtypes = [i32, i64, vp, vp, vp, u32, i64, vp, vp]
     L.esc_count_static_noalloc.restype = st
     for name in ("esc_create", "esc_apply_batch", "esc_triads", "esc_local_triads", "esc_destroy",
                  "esc_export_sizes", "esc_export", "esc_set_profiling", "esc_last_stats",
                  "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
-                 "esc_group_set_profiling", "esc_group_last_stats"):
+                 "esc_group_set_profiling", "esc_group_last_stats", "esc_group_bytes", "esc_server_create",
+                 "esc_server_submit", "esc_server_wait", "esc_server_drain", "esc_server_triads",
+                 "esc_server_get_stats", "esc_server_destroy"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -249,6 +273,17 @@ def esc_group_create(shared: esc_config, graph_cfgs: Sequence[esc_config], strea
     return h.value
 
 
+def esc_group_bytes(shared: esc_config, graph_cfgs: Sequence[esc_config]) -> int:
+    """Device bytes esc_group_create would allocate (nothing is allocated)."""
+    L = load()
+    arr = (esc_config * len(graph_cfgs))(*graph_cfgs)
+    out = C.c_int64(0)
+    rc = L.esc_group_bytes(C.byref(shared), len(graph_cfgs), arr, C.byref(out))
+    if rc != 0:
+        raise EscError(rc, "esc_group_bytes failed")
+    return int(out.value)
+
+
 def esc_group_apply(grp: int, batches: Sequence[dict]) -> None:
     """batches: dicts with graph, ins_offsets, ins_members, ins_timestamps,
     del_ids and optionally out_ids (a writable int32 numpy array)."""
@@ -304,6 +339,79 @@ def esc_group_last_stats(grp: int) -> dict:
 
 def esc_group_launch_count(grp: int) -> int:
     return int(load().esc_group_launch_count(grp))
+
+
+# ---------------------------------------------------------------------------
+# serving loop
+# ---------------------------------------------------------------------------
+
+def esc_server_create(grp: int, max_pending_updates: int, max_batches_per_call: int = 0) -> int:
+    L = load()
+    h = C.c_void_p()
+    rc = L.esc_server_create(grp, int(max_pending_updates), int(max_batches_per_call), C.byref(h))
+    if rc != 0:
+        raise EscError(rc, "esc_server_create failed")
+    return h.value
+
+
+def esc_server_submit(srv: int, graph: int, ins_offsets=None, ins_members=None, ins_timestamps=None,
+                      del_ids=None, out_ids: Optional[np.ndarray] = None, t_arrival_ns: int = 0) -> int:
+    """Queue one request (host arrays; they are copied).  Returns the ticket,
+    or -1 when the queue is full (ESC_ERR_BUSY).  ``out_ids`` (int32 numpy
+    array) must stay alive until the request is collected."""
+    L = load()
+    b = esc_batch()
+    b.graph = int(graph)
+    po, ko = _ptr(ins_offsets, np.int64)
+    pm, km = _ptr(ins_members, np.int32)
+    pt, kt = _ptr(ins_timestamps, np.int64)
+    pd, kd = _ptr(del_ids, np.int32)
+    b.n_ins = (len(ins_offsets) - 1) if ins_offsets is not None and len(ins_offsets) else 0
+    b.ins_offsets, b.ins_members, b.ins_timestamps = po, pm, pt
+    b.n_del = len(del_ids) if del_ids is not None else 0
+    b.del_ids = pd
+    b.out_ins_ids = out_ids.ctypes.data if out_ids is not None and b.n_ins else None
+    t = C.c_int64(-1)
+    rc = L.esc_server_submit(srv, C.byref(b), int(t_arrival_ns), C.byref(t))
+    if rc == ESC_ERR_BUSY:
+        return -1
+    if rc != 0:
+        raise EscError(rc, "esc_server_submit failed")
+    return int(t.value)
+
+
+def esc_server_wait(srv: int, ticket: int) -> dict:
+    """Block until the request is done; returns its record (status included)."""
+    L = load()
+    inf = esc_request_info()
+    L.esc_server_wait(srv, int(ticket), C.byref(inf))
+    return {k: getattr(inf, k) for k, _ in esc_request_info._fields_}
+
+
+def esc_server_drain(srv: int) -> None:
+    load().esc_server_drain(srv)
+
+
+def esc_server_triads(srv: int, graph: int, triad_type: int, window: int = 0) -> np.ndarray:
+    L = load()
+    n = N_CLASSES[triad_type]
+    out = np.zeros(n, np.uint64)
+    rc = L.esc_server_triads(srv, int(graph), triad_type, int(window), out.ctypes.data, n)
+    if rc != 0:
+        raise EscError(rc, "esc_server_triads failed")
+    return out
+
+
+def esc_server_get_stats(srv: int) -> dict:
+    L = load()
+    s = esc_server_stats()
+    L.esc_server_get_stats(srv, C.byref(s))
+    return {k: getattr(s, k) for k, _ in esc_server_stats._fields_}
+
+
+def esc_server_destroy(srv: int) -> None:
+    if srv:
+        load().esc_server_destroy(srv)
 
 
 def esc_count_static_noalloc(n_vertices: int, offsets, members, timestamps, families: int, delta: int,

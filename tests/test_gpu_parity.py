@@ -137,6 +137,62 @@ def test_multi_pass_and_global_tables(E, monkeypatch, families):
     assert_store_equal(g, og)
 
 
+def _big_hyperedge_stream(E, families, seed):
+    """Large hyperedges over popular vertices are inserted and, in the next
+    batch, deleted again; counts, IDs and the store are compared with the
+    oracle after every batch."""
+    rng = np.random.default_rng(seed)
+    nv = 300
+    edges = [sorted(rng.choice(nv, size=rng.integers(2, 7), replace=False).tolist()) for _ in range(400)]
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    ts = np.arange(len(edges), dtype=np.int64)
+    og = OracleHypergraph(nv, off, mem, ts)
+    g = E.Graph(nv, off, mem, ts, families=families, delta=1 << 40, **caps_for(nv, 2000, 20000, 1000, 20000))
+    assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "initial")
+    big_ids = None
+    for step in range(3):
+        ins = [sorted(rng.choice(nv, size=int(rng.integers(120, 200)), replace=False).tolist()) for _ in range(4)]
+        ins += [sorted(rng.choice(nv, size=int(rng.integers(2, 5)), replace=False).tolist()) for _ in range(20)]
+        ioff = np.zeros(len(ins) + 1, np.int64)
+        ioff[1:] = np.cumsum([len(e) for e in ins])
+        imem = np.array([v for e in ins for v in e], np.int32)
+        its = np.full(len(ins), 1000 + step, np.int64)
+        live = og.live_ids()
+        dels = np.sort(np.concatenate([big_ids if big_ids is not None else np.zeros(0, np.int64),
+                                       rng.choice(live[:300], size=10, replace=False)])).astype(np.int64)
+        dels = np.unique(dels)
+        ids_o = og.apply_batch(ioff, imem, its, dels)
+        ids_g = g.apply_batch(ioff, imem, its, dels.astype(np.int32))
+        assert np.array_equal(ids_g, ids_o)
+        big_ids = np.asarray(ids_o[:2], np.int64)
+        assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), f"step {step}")
+    assert_store_equal(g, og)
+
+
+@pytest.mark.parametrize("families", [ALL, 3])
+def test_neighbourhoods_built_in_place(E, monkeypatch, families):
+    """A changed hyperedge whose neighbourhood is larger than the block's
+    hash table (1024 slots here) has its table built in place, in its own
+    region of the neighbour lists."""
+    monkeypatch.setenv("ESC_COUNT_TABLE_SLOTS", "1024")
+    monkeypatch.setenv("ESC_COUNT_SMEM_SLOTS", "64")
+    _big_hyperedge_stream(E, families, 17)
+
+
+@pytest.mark.parametrize("families", [1, 2, 3])
+def test_restricted_lists(E, monkeypatch, families):
+    """Without the temporal family, a large N(h) (here from 600 neighbour
+    entries on) gets restricted incidence lists R(u), through which the
+    centre kernel meets N(g1) and N(h); with the pool too small for some of
+    them the rest take the hash-probing path in the same run."""
+    monkeypatch.setenv("ESC_COUNT_RMIN", "600")
+    _big_hyperedge_stream(E, families, 19)
+    monkeypatch.setenv("ESC_COUNT_RPOOL", "12000")
+    _big_hyperedge_stream(E, families, 23)
+
+
 @pytest.mark.parametrize("families", [1, 2, 4, 3, 5, 6])
 def test_family_subsets(E, families):
     s = gen.random_small(9, 300, 200, 2, 7, n_batches=1, n_ins=30, n_del=30)
