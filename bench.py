@@ -539,6 +539,7 @@ def run_temporal(args):
     live_ids = np.zeros(0, np.int32)
     live_ts = np.zeros(0, np.int64)
     lat, upd, t_all = [], [], 0.0
+    cnt_ms, triads, work = [], 0, [0] * 6
     for k, b in enumerate(ts.batches):
         t_cut = int(b.timestamps.max()) - delta
         n_exp = int(np.searchsorted(live_ts, t_cut, side="left"))
@@ -552,6 +553,10 @@ def run_temporal(args):
             lat.append(dt * 1e3)
             upd.append(b.n + n_exp)
             t_all += dt
+            sts = g.stats()
+            cnt_ms.append(sts["ms_count_del"] + sts["ms_count_ins"])
+            triads += sts["triads"]
+            work = [a + c for a, c in zip(work, sts["work"])]
     counts = g.triads(E.TRIAD_TEMPORAL)
     g.close()
     print(json.dumps({
@@ -564,6 +569,11 @@ def run_temporal(args):
                    "families": "temporal (96)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "live_at_end": int(len(live_ids)), "temporal_triads": int(counts.sum()),
+        "count_ms_per_step": sum(cnt_ms) / max(len(cnt_ms), 1),
+        "triads_per_step": triads / max(len(cnt_ms), 1),
+        "counter_work_per_step": {k: v / max(len(cnt_ms), 1) for k, v in zip(
+            ["centre_items", "n_g1_build_entries", "pair_pass_visits", "closed_pairs", "slow_t_steps",
+             "aggregate_visits"], work)},
     }))
 
 

@@ -354,7 +354,7 @@ esc_status esc_server_destroy(esc_server* srv);
  *
  * Limits: n_he <= 262,144; offsets[n_he] <= 2,097,152; n_vertices <=
  * 524,288; each hyperedge at most ESC_MAX_CARDINALITY members; for every
- * hyperedge, the sum of its members' degrees at most 1,024.
+ * hyperedge, the sum of its members' degrees at most 65,536.
  * Errors: INVALID_ARG (bad arguments, host pointers, malformed hypergraph),
  * UNSUPPORTED (a limit exceeded), CUDA. */
 esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int64_t* offsets,

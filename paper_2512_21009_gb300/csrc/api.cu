@@ -273,7 +273,14 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     // per-block overflow hash tables
     CountShape sh;
     sh.cap = E->max_ins;
-    sh.list_cap = std::max<int64_t>(int64_t(1) << 22, 128 * sh.cap);
+    // neighbour-list arena of one count run (24 B per entry): a batch whose
+    // lists do not fit is counted in several runs, each rebuilding the N(g1)
+    // it needs, so the arena is sized for whole batches
+    sh.list_cap = std::min<int64_t>(std::max<int64_t>(int64_t(1) << 22, 512 * sh.cap), int64_t(1) << 29);
+    if (const char* env = getenv("ESC_COUNT_LIST")) {
+        long long v = atoll(env);
+        if (v >= 4096) sh.list_cap = v;
+    }
     sh.e_cap = Ecap;
     int64_t slots = int64_t(1) << 15;
     while (slots < 2 * std::min<int64_t>(inc, int64_t(1) << 20) && slots < (int64_t(1) << 16)) slots <<= 1;
@@ -285,9 +292,10 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     }
     sh.n_cta_nh = E->sm_count * 2;
     sh.n_cta_c = E->sm_count;
-    // restricted-list pool of a count run: 16 entries per incidence of the
-    // store, at least 2^24 and below 2^31 entries (int32 list offsets)
-    sh.r_cap = std::min<int64_t>(std::max<int64_t>(16 * inc, int64_t(1) << 24), (int64_t(1) << 31) - 64);
+    // restricted-list pool of a count run (int32 entries, below 2^31): none
+    // unless asked for -- building the lists costs more than the probes they
+    // save on the measured workloads
+    sh.r_cap = 0;
     if (const char* env = getenv("ESC_COUNT_RPOOL")) {
         long long v = atoll(env);
         if (v >= 0 && v < (1ll << 31)) sh.r_cap = v;
@@ -305,7 +313,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     // test knobs: shrink the shared-memory tables so that the global-table
     // and partitioned paths run on small inputs; lower the neighbourhood size
     // from which restricted lists are built
-    if (const char* env = getenv("ESC_CENTER_SMALL")) E->cs.center_small = atoi(env) != 0;
+    if (const char* env = getenv("ESC_CENTER_SMALL")) E->cs.center_small = atoi(env);
     if (const char* env = getenv("ESC_COUNT_RMIN")) {
         long long v = atoll(env);
         if (v >= 1) E->cs.r_min = v;

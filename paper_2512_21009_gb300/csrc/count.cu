@@ -59,7 +59,8 @@ constexpr int NH_S = 4096;           // shared-memory N(h) table slots
 // centre kernel: threads NT and shared N(g1) table slots TS are template
 // parameters (CenterBig: one 512-thread block per SM; CenterSmall: two
 // 256-thread blocks per SM with half the table)
-constexpr int LCH = 32;              // changed hyperedges per centre work item
+constexpr int LCH = 32;              // changed hyperedges per chunk of a centre work item
+constexpr int kSuper = 8;            // chunks of one g1 served by one build of N(g1)
 constexpr int kWin = 64;             // |h & g1| values served from the histogram window
 constexpr int kBigNH = 512;          // N(h) with more entries also gets a hash table in the lists
 constexpr int kIC = 32;              // |h & g1| up to which h & g1 is listed for the triple sizes
@@ -503,8 +504,8 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         __syncthreads();
         if (tid == 0) s.item = (long long)atomicAdd(&A.sc->qnh[A.side], 1ull);
         __syncthreads();
-        const int64_t i = s.item;
-        if (i >= A.n) break;
+        if (s.item >= A.n) break;
+        const int64_t i = cs.order[s.item];
         const int32_t h = A.changed[A.lo + i];
         const int g = A.changed_g ? A.changed_g[A.lo + i] : 0;
         if (g != cur_g) {
@@ -677,13 +678,74 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
 // 2. invert candidate pairs into L(g1)
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// processing order: the persistent blocks take the longest work first, so
+// that no block starts a large neighbourhood when the others run dry
+// ---------------------------------------------------------------------------
+
+constexpr int32_t kBigFirst = 4096;  // neighbour-region entries from which h goes first
+constexpr int kOrderBuckets = 16;    // log2 buckets of |g1| for the centre items
+
+__global__ void k_order_flags(const int32_t* sizes, int64_t n, int32_t* flag) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = sizes[i] >= kBigFirst ? 1 : 0;
+}
+
+// stable partition: the flagged indices in order, then the others in order
+__global__ void k_order_place(const int32_t* flag, const int64_t* pre, int64_t n, int32_t* order) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t nb = pre[n];
+    order[flag[i] ? pre[i] : nb + (i - pre[i])] = int32_t(i);
+}
+
+__device__ __forceinline__ int g1_bucket(int k1) { return min(kOrderBuckets - 1, 31 - __clz(max(k1, 1))); }
+
+// distinct candidate neighbours g1 by descending log2 |g1| (the cost of an
+// item grows with the neighbourhood of g1 built for it)
+__global__ void k_dsort_count(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(cs.block_sums);
+    const int nd = A.sc->n_d[A.side];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[g1_bucket(A.S.h_card[cs.d_list[j]])], 1ull);
+}
+
+__global__ void k_dsort_scan(CountArgs A) {
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(A.cs.block_sums);
+    if (threadIdx.x != 0) return;
+    unsigned long long pos = 0;
+    for (int b = kOrderBuckets - 1; b >= 0; --b) {
+        const unsigned long long c = cnt[b];
+        cnt[b] = pos;
+        pos += c;
+    }
+}
+
+__global__ void k_dsort_scatter(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(cs.block_sums);
+    const int nd = A.sc->n_d[A.side];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
+        const int32_t g1 = cs.d_list[j];
+        cs.d_items[atomicAdd(&cnt[g1_bucket(A.S.h_card[g1])], 1ull)] = g1;
+    }
+}
+
+__global__ void k_dsort_copy(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    const int nd = A.sc->n_d[A.side];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x)
+        cs.d_list[j] = cs.d_items[j];
+}
+
 __global__ void k_d_prep(CountArgs A) {
     const CountScratch& cs = A.cs;
     const int nd = A.sc->n_d[A.side];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x) {
         const int c = cs.lcnt[cs.d_list[j]];
         cs.d_cnt[j] = c;
-        cs.d_items[j] = (c + LCH - 1) / LCH;
+        cs.d_items[j] = ((c + LCH - 1) / LCH + kSuper - 1) / kSuper;
     }
 }
 
@@ -870,11 +932,15 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
         const int64_t item = s.item;
         if (item >= n_items) break;
         const int64_t j = upper_bound_dev(cs.d_item_start, int64_t(nd) + 1, item) - 1;
-        const int64_t chunk = item - cs.d_item_start[j];
+        // this item: chunks [c_beg, c_end) of L(g1), LCH changed hyperedges
+        // each, all served by one build of N(g1)
+        const int64_t sup = item - cs.d_item_start[j];
         const int32_t g1 = cs.d_list[j];
-        const int64_t lbeg = cs.d_loff[j] + chunk * LCH;
-        const int nh = int(min(lbeg + LCH, cs.d_loff[j + 1]) - lbeg);
-        const int g = A.changed_g ? A.changed_g[A.lo + cs.l_i[lbeg]] : 0;
+        const int64_t l_lo = cs.d_loff[j], l_hi = cs.d_loff[j + 1];
+        const int64_t n_chunks = (l_hi - l_lo + LCH - 1) / LCH;
+        const int64_t c_beg = sup * kSuper, c_end = min(c_beg + kSuper, n_chunks);
+        const int64_t nh_all = min(l_lo + c_end * LCH, l_hi) - (l_lo + c_beg * LCH);
+        const int g = A.changed_g ? A.changed_g[A.lo + cs.l_i[l_lo + c_beg * LCH]] : 0;
         if (g != cur_g) {
             if (cur_g >= 0) flush<NT_C>(A, s.acc, s.hist, NW_C, cur_g, acc, s.red);
             cur_g = g;
@@ -889,7 +955,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
         acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
         // the method reads N(g1) (sum of member degrees) once per pair (h, g1)
         if (tid == 0) {
-            acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)nh;
+            acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)nh_all;
             ++acc.w[0];
             acc.w[1] += (unsigned long long)u1;
         }
@@ -899,7 +965,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
         int64_t* lts;
         int P = 1;
         const uint32_t t1_cap = pow2_at_least(2 * u1);
-        if (t1_cap <= A.c_smem_cap) {
+        if (t1_cap <= min(A.c_smem_cap, uint32_t(T1_S))) {  // the block's table holds T1_S slots
             T1 = Tab{s.keys, s.vals, nullptr, s.list, &s.n_list, t1_cap - 1, T1_S / 2};
             mark = s.mark;
             lk = s.lk;
@@ -911,45 +977,6 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
             lts = g_lts;
             if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
             else P = int((4 * u1 + gs - 1) / gs);
-        }
-        // the item's changed hyperedges
-        if (tid < nh) {
-            const int64_t e = lbeg + tid;
-            const int32_t li = cs.l_i[e];
-            const uint64_t xv1 = cs.l_xv[e];
-            const int32_t h = A.changed[A.lo + li];
-            s.hh[tid] = h;
-            s.hk[tid] = S.h_card[h];
-            s.hx[tid] = int(xv1 & kXMask);
-            s.hvf[tid] = int32_t(uint32_t(xv1 >> 32));
-            s.hli[tid] = li;
-            s.hts[tid] = S.h_ts[h];
-            s.hmem[tid] = h2v + S.h_off[h];
-            s.hnb[tid] = cs.nh_off[li];
-            s.hnn[tid] = cs.nh_n[li];
-            s.htcap[tid] = cs.nh_tcap[li];
-            s.htoff[tid] = cs.nh_toff[li];
-            s.hr[tid] = cs.r_off[li];
-            s.hIn[tid] = 0;
-        }
-        __syncthreads();
-        // h & g1 for the h sharing 2..kIC vertices with g1: the smaller list is
-        // searched in the larger
-        for (int l = 0; l < nh; ++l) {
-            const int xh1 = s.hx[l];
-            if (xh1 < 2 || xh1 > kIC) continue;
-            const int kh = s.hk[l];
-            const bool from_h = kh <= k1;
-            const int32_t* a = from_h ? s.hmem[l] : g1mem;
-            const int32_t* b = from_h ? g1mem : s.hmem[l];
-            const int na = from_h ? kh : k1, nb = from_h ? k1 : kh;
-            for (int i = tid; i < na; i += NT_C) {
-                const int32_t u = a[i];
-                if (contains_sorted(b, nb, u)) {
-                    const int c = atomicAdd(&s.hIn[l], 1);
-                    if (c < kIC) s.hI[l][c] = u;
-                }
-            }
         }
         for (int p = 0; p < P; ++p) {
             // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p)
@@ -1002,207 +1029,321 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 }
             }
             acc.n_meta += (tid < n1) ? (n1 - tid + NT_C - 1) / NT_C : 0;
-            if (tid == 0) {
-                // work of pass (i) per h: the smaller of N(h) and N(g1) when N(h)
-                // has a table to probe (aggregate mode), else all of N(h)
-                int run = 0;
+            for (int64_t ch = c_beg; ch < c_end; ++ch) {
+                const int64_t lbeg = l_lo + ch * LCH;
+                const int nh = int(min(lbeg + LCH, l_hi) - lbeg);
+                __syncthreads();
+                // the chunk's changed hyperedges
+                if (tid < nh) {
+                    const int64_t e = lbeg + tid;
+                    const int32_t li = cs.l_i[e];
+                    const uint64_t xv1 = cs.l_xv[e];
+                    const int32_t h = A.changed[A.lo + li];
+                    s.hh[tid] = h;
+                    s.hk[tid] = S.h_card[h];
+                    s.hx[tid] = int(xv1 & kXMask);
+                    s.hvf[tid] = int32_t(uint32_t(xv1 >> 32));
+                    s.hli[tid] = li;
+                    s.hts[tid] = S.h_ts[h];
+                    s.hmem[tid] = h2v + S.h_off[h];
+                    s.hnb[tid] = cs.nh_off[li];
+                    s.hnn[tid] = cs.nh_n[li];
+                    s.htcap[tid] = cs.nh_tcap[li];
+                    s.htoff[tid] = cs.nh_toff[li];
+                    s.hr[tid] = cs.r_off[li];
+                    s.hIn[tid] = 0;
+                }
+                __syncthreads();
+                // h & g1 for the h sharing 2..kIC vertices with g1: the smaller list is
+                // searched in the larger
                 for (int l = 0; l < nh; ++l) {
-                    s.hpre[l] = run;
-                    int mode = 0, work = s.hnn[l];
-                    if (!want_t && s.htcap[l] > 0) {
-                        if (s.hr[l] >= 0 && k1 < min(s.hnn[l], n1)) {
-                            mode = 2;
-                            work = k1;
-                        } else if (s.hnn[l] > n1) {
-                            mode = 1;
-                            work = n1;
+                    const int xh1 = s.hx[l];
+                    if (xh1 < 2 || xh1 > kIC) continue;
+                    const int kh = s.hk[l];
+                    const bool from_h = kh <= k1;
+                    const int32_t* a = from_h ? s.hmem[l] : g1mem;
+                    const int32_t* b = from_h ? g1mem : s.hmem[l];
+                    const int na = from_h ? kh : k1, nb = from_h ? k1 : kh;
+                    for (int i = tid; i < na; i += NT_C) {
+                        const int32_t u = a[i];
+                        if (contains_sorted(b, nb, u)) {
+                            const int c = atomicAdd(&s.hIn[l], 1);
+                            if (c < kIC) s.hI[l][c] = u;
                         }
                     }
-                    s.hfrom[l] = mode;
-                    run += work;
                 }
-                s.hpre[nh] = run;
-            }
-            __syncthreads();
-            const int n_cl = s.n_cl;
+                if (tid == 0) {
+                    // work of pass (i) per h: the smaller of N(h) and N(g1) when N(h)
+                    // has a table to probe (aggregate mode), else all of N(h)
+                    int run = 0;
+                    for (int l = 0; l < nh; ++l) {
+                        s.hpre[l] = run;
+                        int mode = 0, work = s.hnn[l];
+                        if (!want_t && s.htcap[l] > 0) {
+                            if (s.hr[l] >= 0 && k1 < min(s.hnn[l], n1)) {
+                                mode = 2;
+                                work = k1;
+                            } else if (s.hnn[l] > n1) {
+                                mode = 1;
+                                work = n1;
+                            }
+                        }
+                        s.hfrom[l] = mode;
+                        run += work;
+                    }
+                    s.hpre[nh] = run;
+                }
+                __syncthreads();
+                const int n_cl = s.n_cl;
 
-            // ---- (i) the pairs {g1, g2}, g2 in N(h), for every h of the item.
-            // Every g2 also in N(g1) (a closed pair) is marked for that h and
-            // counted at g1 < g2 unless g2 is a changed hyperedge of smaller
-            // ID than h.  With the temporal family every g2 of N(h) is visited
-            // (the open pairs centred at h are enumerated); otherwise the
-            // closed pairs are found from the smaller of N(h) and N(g1),
-            // probing the other's hash table, or, for an h with restricted
-            // lists, from R(u) for the members u of g1.
-            const int wtot = s.hpre[nh];
-            if (tid == 0) acc.w[2] += (unsigned long long)wtot;
-            // a closed pair {g1, g2} for the item's l-th h
-            auto closed = [&](int l, int32_t h, int32_t g2, int sl, int xh2, int32_t vf2, int k2, bool chg2,
-                              int& skey, bool direct) {
-                const int kh = s.hk[l], xh1 = s.hx[l];
-                const int x12 = int(T1.vals[sl]);
-                if (want_open && !direct) atomicOr(&mark[sl], 1u << l);
-                if (agg) {
-                    const int b = (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 1 : 0);
-                    if (direct) atomicAdd(&s.sub[l][b], 1u);
-                    else skey = l * 4 + b;
-                }
-                if (g2 > g1 && !(g2 < h && chg2)) {
-                    ++acc.n_meta;
-                    ++acc.w[3];
-                    const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
-                                              kh, s.hI[l], s.hIn[l], acc.w[4]);
-                    if (want_open)
-                        classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l], ts1,
-                                 want_t ? S.h_ts[g2] : 0, acc);
-                    if (agg) atomicAdd(&s.hneg[wid][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
-                    if (fam & kFamV)
-                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
-                                  2ull * t;
-                }
-            };
-            for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
-                const int idx = idx0 + tid;
-                int skey = -1;
-                if (idx < wtot) {
-                    int l = 0, hi_l = nh - 1;  // the h of this work index: last l with hpre[l] <= idx
-                    while (l < hi_l) {
-                        const int mid = (l + hi_l + 1) >> 1;
-                        if (s.hpre[mid] <= idx) l = mid;
-                        else hi_l = mid - 1;
+                // ---- (i) the pairs {g1, g2}, g2 in N(h), for every h of the item.
+                // Every g2 also in N(g1) (a closed pair) is marked for that h and
+                // counted at g1 < g2 unless g2 is a changed hyperedge of smaller
+                // ID than h.  With the temporal family every g2 of N(h) is visited
+                // (the open pairs centred at h are enumerated); otherwise the
+                // closed pairs are found from the smaller of N(h) and N(g1),
+                // probing the other's hash table, or, for an h with restricted
+                // lists, from R(u) for the members u of g1.
+                const int wtot = s.hpre[nh];
+                if (tid == 0) acc.w[2] += (unsigned long long)wtot;
+                // a closed pair {g1, g2} for the item's l-th h
+                auto closed = [&](int l, int32_t h, int32_t g2, int sl, int xh2, int32_t vf2, int k2, bool chg2,
+                                  int& skey, bool direct) {
+                    const int kh = s.hk[l], xh1 = s.hx[l];
+                    const int x12 = int(T1.vals[sl]);
+                    if (want_open && !direct) atomicOr(&mark[sl], 1u << l);
+                    if (agg) {
+                        const int b = (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 1 : 0);
+                        if (direct) atomicAdd(&s.sub[l][b], 1u);
+                        else skey = l * 4 + b;
                     }
-                    const int q = idx - s.hpre[l];
-                    const int32_t h = s.hh[l];
-                    const int mode = s.hfrom[l];
-                    if (mode == 2) {
-                        // the neighbours f of h holding the q-th member u of g1:
-                        // each is in N(g1); one met through several shared
-                        // vertices is taken once (its mark bit)
-                        const int32_t* ridx = cs.r_pool + s.hr[l];
-                        const int32_t* ent = ridx + S.nv[g] + 1;
-                        const int64_t lu = int64_t(g1mem[q]) - S.vbase[g];
-                        const int e1 = ridx[lu + 1];
-                        for (int e = ridx[lu]; e < e1; ++e) {
-                            ++acc.w[2];
-                            const int32_t f = ent[e];
-                            if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
-                            const int sl = tab_find(T1, f);
-                            if (sl < 0) continue;
-                            if ((atomicOr(&mark[sl], 1u << l) >> l) & 1u) continue;
-                            const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), f);
-                            if (ps < 0) continue;
-                            const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
-                            int unused;
-                            closed(l, h, f, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), S.h_card[f],
-                                   bit_test(A.chg, f), unused, true);
+                    if (g2 > g1 && !(g2 < h && chg2)) {
+                        ++acc.n_meta;
+                        ++acc.w[3];
+                        const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
+                                                  kh, s.hI[l], s.hIn[l], acc.w[4]);
+                        if (want_open)
+                            classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l], ts1,
+                                     want_t ? S.h_ts[g2] : 0, acc);
+                        if (agg) atomicAdd(&s.hneg[wid][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
+                        if (fam & kFamV)
+                            acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
+                                      2ull * t;
+                    }
+                };
+                for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
+                    const int idx = idx0 + tid;
+                    int skey = -1;
+                    if (idx < wtot) {
+                        int l = 0, hi_l = nh - 1;  // the h of this work index: last l with hpre[l] <= idx
+                        while (l < hi_l) {
+                            const int mid = (l + hi_l + 1) >> 1;
+                            if (s.hpre[mid] <= idx) l = mid;
+                            else hi_l = mid - 1;
                         }
-                    } else if (mode == 1) {
-                        const int sl = T1.list[q];
-                        const int32_t g2 = T1.keys[sl];
-                        const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), g2);
-                        if (ps >= 0) {
-                            const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
+                        const int q = idx - s.hpre[l];
+                        const int32_t h = s.hh[l];
+                        const int mode = s.hfrom[l];
+                        if (mode == 2) {
+                            // the neighbours f of h holding the q-th member u of g1:
+                            // each is in N(g1); one met through several shared
+                            // vertices is taken once (its mark bit)
+                            const int32_t* ridx = cs.r_pool + s.hr[l];
+                            const int32_t* ent = ridx + S.nv[g] + 1;
+                            const int64_t lu = int64_t(g1mem[q]) - S.vbase[g];
+                            const int e1 = ridx[lu + 1];
+                            for (int e = ridx[lu]; e < e1; ++e) {
+                                ++acc.w[2];
+                                const int32_t f = ent[e];
+                                if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
+                                const int sl = tab_find(T1, f);
+                                if (sl < 0) continue;
+                                if ((atomicOr(&mark[sl], 1u << l) >> l) & 1u) continue;
+                                const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), f);
+                                if (ps < 0) continue;
+                                const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
+                                int unused;
+                                closed(l, h, f, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), S.h_card[f],
+                                       bit_test(A.chg, f), unused, true);
+                            }
+                        } else if (mode == 1) {
+                            const int sl = T1.list[q];
+                            const int32_t g2 = T1.keys[sl];
+                            const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), g2);
+                            if (ps >= 0) {
+                                const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
+                                const int32_t meta = lk[q];
+                                closed(l, h, g2, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), meta & 0x7fffffff,
+                                       meta < 0, skey, false);
+                            }
+                        } else {
+                            const int32_t g2 = cs.nh_g[s.hnb[l] + q];
+                            if (P == 1 || part_of(g2, P) == p) {
+                                const int sl = tab_find(T1, g2);
+                                if (sl >= 0 || (!agg && want_open)) {
+                                    const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
+                                    const int xh2 = int(xv2 & kXMask);
+                                    const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
+                                    if (sl >= 0) {
+                                        closed(l, h, g2, sl, xh2, vf2, S.h_card[g2], bit_test(A.chg, g2), skey, false);
+                                    } else if (g2 > g1 && !(g2 < h && bit_test(A.chg, g2))) {
+                                        // open pair centred at h, enumerated (temporal family kept)
+                                        ++acc.n_meta;
+                                        classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, S.h_card[g2], s.hx[l],
+                                                 0, xh2, 0, s.hts[l], ts1, want_t ? S.h_ts[g2] : 0, acc);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    if (agg) warp_count(&s.sub[0][0], skey);
+                }
+                __syncthreads();
+                if (agg) {
+                    // (ii) in aggregate.  An open triad {h, g1, f} (f in N(g1),
+                    // f outside N(h), f != h) has regions h-only |h| - |h&g1|,
+                    // g1-only |g1| - |h&g1| - |g1&f|, f-only |f| - |g1&f|, h&g1
+                    // and g1&f non-empty, the rest empty: its class is set by
+                    // A = [h not inside g1] and the bucket b = 2B + C of f, with
+                    // B = [|g1&f| != |g1| - |h&g1|], C = [f not inside g1].  The
+                    // buckets over all of N(g1) come from the totals and the x
+                    // window; subtracted are the f in N(h) (marked in (i)), f = h,
+                    // and the changed f < h (attributed to f).
+                    const int wc = nh * n_cl;
+                    if (tid == 0) acc.w[5] += (unsigned long long)wc;
+                    for (int idx0 = 0; idx0 < wc; idx0 += NT_C) {
+                        const int idx = idx0 + tid;
+                        int skey = -1;
+                        if (idx < wc) {
+                            const int l = idx / n_cl, c = idx - l * n_cl;
+                            const int64_t v = lts[c];
+                            const int sl = int(uint32_t(v));
+                            const int32_t f = T1.keys[sl];
+                            if (f < s.hh[l] && !((mark[sl] >> l) & 1u)) {
+                                const int x = int(T1.vals[sl]);
+                                skey = l * 4 + ((x != k1 - s.hx[l] ? 2 : 0) | (int(v >> 32) > x ? 1 : 0));
+                            }
+                        }
+                        warp_count(&s.sub[0][0], skey);
+                    }
+                    if (tid < nh && (P == 1 || part_of(s.hh[tid], P) == p)) {
+                        const int xh1 = s.hx[tid];
+                        atomicAdd(&s.sub[tid][(xh1 != k1 - xh1 ? 2 : 0) | (s.hk[tid] > xh1 ? 1 : 0)], 1u);
+                    }
+                    for (int l = 0; l < nh; ++l) {  // x = |g1| - |h&g1| outside the window
+                        if (s.hx[l] <= kWin) continue;
+                        const int xstar = k1 - s.hx[l];
+                        for (int q = tid; q < n1; q += NT_C)
+                            if (int(T1.vals[T1.list[q]]) == xstar)
+                                atomicAdd(&s.xc[l][(lk[q] & 0x7fffffff) > xstar ? 1 : 0], 1u);
+                    }
+                    __syncthreads();
+                    if (tid < nh) {
+                        const int xh1 = s.hx[tid], kh = s.hk[tid];
+                        const int A_bit = kh > xh1 ? 1 : 0;
+                        for (int b = 0; b < 4; ++b) {
+                            const int B = b >> 1, C = b & 1;
+                            const uint32_t h0 = xh1 <= kWin ? s.win[kWin - xh1][C] : s.xc[tid][C];
+                            const uint32_t total = B == 0 ? h0 : s.tot[C] - h0;
+                            const uint32_t n = total - s.sub[tid][b];
+                            if (n) {
+                                const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
+                                atomicAdd(&hist[s.tb.cls30[m]], n);
+                                acc.n_tri += n;
+                            }
+                            s.sub[tid][b] = 0;
+                        }
+                        s.xc[tid][0] = s.xc[tid][1] = 0;
+                    }
+                } else if (want_open) {
+                    // (ii) open triads {h, g1, f} centred at g1: f in N(g1),
+                    // outside N(h) (unmarked), f != h, f not a changed
+                    // hyperedge of smaller ID than h.  Their class is set by
+                    // A = [h not inside g1], the bucket 2B + C of f (as in
+                    // aggregate mode) and, for the temporal family, by where f
+                    // falls in time against h and g1 (before both, between,
+                    // after both) and whether that triple fits the window; so
+                    // one warp per h counts its f by (position, bucket) and
+                    // classifies each count once.
+                    for (int l = wid; l < nh; l += NW_C) {
+                        const int32_t h = s.hh[l];
+                        const int xh1 = s.hx[l], xstar = k1 - xh1;
+                        const int64_t th = s.hts[l];
+                        const bool h_first = th < ts1 || (th == ts1 && h < g1);
+                        const int64_t tp = h_first ? th : ts1, tq = h_first ? ts1 : th;
+                        const int32_t ip = h_first ? h : g1, iq = h_first ? g1 : h;
+                        uint32_t cst[4] = {0, 0, 0, 0};
+                        uint32_t ctm[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+                        for (int q = lane; q < n1; q += 32) {
+                            const int sl = T1.list[q];
+                            const int32_t f = T1.keys[sl];
+                            if (f == h) continue;
                             const int32_t meta = lk[q];
-                            closed(l, h, g2, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), meta & 0x7fffffff,
-                                   meta < 0, skey, false);
+                            if (meta < 0 && f < h) continue;  // changed, smaller ID: attributed to f
+                            if ((mark[sl] >> l) & 1u) continue;
+                            const int x = int(T1.vals[sl]);
+                            const int b = (x != xstar ? 2 : 0) | ((meta & 0x7fffffff) > x ? 1 : 0);
+                            int r = -1;  // position in time, -1: outside the window
+                            if (want_t) {
+                                const int64_t tf = lts[q];
+                                if (tf < tp || (tf == tp && f < ip)) r = tq - tf <= delta ? 0 : -1;
+                                else if (tf < tq || (tf == tq && f < iq)) r = tq - tp <= delta ? 1 : -1;
+                                else r = tf - tp <= delta ? 2 : -1;
+                            }
+                            // constant indices keep the counters in registers
+#pragma unroll
+                            for (int bb = 0; bb < 4; ++bb) {
+                                cst[bb] += b == bb ? 1u : 0u;
+#pragma unroll
+                                for (int rr = 0; rr < 3; ++rr) ctm[rr][bb] += (b == bb && r == rr) ? 1u : 0u;
+                            }
                         }
-                    } else {
-                        const int32_t g2 = cs.nh_g[s.hnb[l] + q];
-                        if (P == 1 || part_of(g2, P) == p) {
-                            const int sl = tab_find(T1, g2);
-                            if (sl >= 0 || (!agg && want_open)) {
-                                const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
-                                const int xh2 = int(xv2 & kXMask);
-                                const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
-                                if (sl >= 0) {
-                                    closed(l, h, g2, sl, xh2, vf2, S.h_card[g2], bit_test(A.chg, g2), skey, false);
-                                } else if (g2 > g1 && !(g2 < h && bit_test(A.chg, g2))) {
-                                    // open pair centred at h, enumerated (temporal family kept)
-                                    ++acc.n_meta;
-                                    classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, S.h_card[g2], s.hx[l],
-                                             0, xh2, 0, s.hts[l], ts1, want_t ? S.h_ts[g2] : 0, acc);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                cst[b] += __shfl_xor_sync(0xffffffffu, cst[b], o);
+#pragma unroll
+                                for (int r = 0; r < 3; ++r) ctm[r][b] += __shfl_xor_sync(0xffffffffu, ctm[r][b], o);
+                            }
+                        }
+                        if (lane == 0) {
+                            const int A_bit = s.hk[l] > xh1 ? 1 : 0;
+                            // labels 0 = h, 1 = g1, 2 = f; p and q are h and g1 in time order
+                            const int lp = h_first ? 0 : 1, lq = h_first ? 1 : 0;
+                            for (int b = 0; b < 4; ++b) {
+                                const int m = A_bit | ((b >> 1) << 1) | ((b & 1) << 2) | (1 << 3) | (1 << 4);
+                                acc.n_tri += cst[b];
+                                if ((fam & kFamH) && cst[b] && s.tb.cls30[m] >= 0)
+                                    atomicAdd(&hist[s.tb.cls30[m]], cst[b]);
+                                if (!want_t) continue;
+                                for (int r = 0; r < 3; ++r) {
+                                    if (!ctm[r][b]) continue;
+                                    const int o0 = r == 0 ? 2 : lp, o1 = r == 0 ? lp : (r == 1 ? 2 : lq);
+                                    const int c = s.tb.cls96[s.tb.perm[perm_index(o0, o1)][m]];
+                                    if (c >= 0) atomicAdd(&hist[kHistT + c], ctm[r][b]);
                                 }
                             }
                         }
                     }
                 }
-                if (agg) warp_count(&s.sub[0][0], skey);
-            }
-            __syncthreads();
-            if (agg) {
-                // (ii) in aggregate.  An open triad {h, g1, f} (f in N(g1),
-                // f outside N(h), f != h) has regions h-only |h| - |h&g1|,
-                // g1-only |g1| - |h&g1| - |g1&f|, f-only |f| - |g1&f|, h&g1
-                // and g1&f non-empty, the rest empty: its class is set by
-                // A = [h not inside g1] and the bucket b = 2B + C of f, with
-                // B = [|g1&f| != |g1| - |h&g1|], C = [f not inside g1].  The
-                // buckets over all of N(g1) come from the totals and the x
-                // window; subtracted are the f in N(h) (marked in (i)), f = h,
-                // and the changed f < h (attributed to f).
-                const int wc = nh * n_cl;
-                if (tid == 0) acc.w[5] += (unsigned long long)wc;
-                for (int idx0 = 0; idx0 < wc; idx0 += NT_C) {
-                    const int idx = idx0 + tid;
-                    int skey = -1;
-                    if (idx < wc) {
-                        const int l = idx / n_cl, c = idx - l * n_cl;
-                        const int64_t v = lts[c];
-                        const int sl = int(uint32_t(v));
-                        const int32_t f = T1.keys[sl];
-                        if (f < s.hh[l] && !((mark[sl] >> l) & 1u)) {
-                            const int x = int(T1.vals[sl]);
-                            skey = l * 4 + ((x != k1 - s.hx[l] ? 2 : 0) | (int(v >> 32) > x ? 1 : 0));
+                __syncthreads();
+                for (int i = tid; i < n1; i += NT_C) mark[T1.list[i]] = 0;
+                // fold the warp histograms of this chunk
+                for (int b = tid; b < kHistN; b += NT_C) {
+                    unsigned long long v = 0;
+                    for (int w = 0; w < NW_C; ++w) {
+                        v += s.hist[w][b];
+                        s.hist[w][b] = 0;
+                        if (b < 32) {
+                            v -= s.hneg[w][b];
+                            s.hneg[w][b] = 0;
                         }
                     }
-                    warp_count(&s.sub[0][0], skey);
-                }
-                if (tid < nh && (P == 1 || part_of(s.hh[tid], P) == p)) {
-                    const int xh1 = s.hx[tid];
-                    atomicAdd(&s.sub[tid][(xh1 != k1 - xh1 ? 2 : 0) | (s.hk[tid] > xh1 ? 1 : 0)], 1u);
-                }
-                for (int l = 0; l < nh; ++l) {  // x = |g1| - |h&g1| outside the window
-                    if (s.hx[l] <= kWin) continue;
-                    const int xstar = k1 - s.hx[l];
-                    for (int q = tid; q < n1; q += NT_C)
-                        if (int(T1.vals[T1.list[q]]) == xstar)
-                            atomicAdd(&s.xc[l][(lk[q] & 0x7fffffff) > xstar ? 1 : 0], 1u);
+                    s.acc[b] += v;
                 }
                 __syncthreads();
-                if (tid < nh) {
-                    const int xh1 = s.hx[tid], kh = s.hk[tid];
-                    const int A_bit = kh > xh1 ? 1 : 0;
-                    for (int b = 0; b < 4; ++b) {
-                        const int B = b >> 1, C = b & 1;
-                        const uint32_t h0 = xh1 <= kWin ? s.win[kWin - xh1][C] : s.xc[tid][C];
-                        const uint32_t total = B == 0 ? h0 : s.tot[C] - h0;
-                        const uint32_t n = total - s.sub[tid][b];
-                        if (n) {
-                            const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
-                            atomicAdd(&hist[s.tb.cls30[m]], n);
-                            acc.n_tri += n;
-                        }
-                        s.sub[tid][b] = 0;
-                    }
-                    s.xc[tid][0] = s.xc[tid][1] = 0;
-                }
-            } else if (want_open) {
-                // (ii) f in N(g1), not in N(h), f != h: open at g1
-                const int wc = nh * n1;
-                for (int idx = tid; idx < wc; idx += NT_C) {
-                    const int l = idx / n1, q = idx - l * n1;
-                    const int sl = T1.list[q];
-                    const int32_t f = T1.keys[sl];
-                    const int32_t h = s.hh[l];
-                    if (f == h) continue;
-                    const int32_t meta = lk[q];
-                    if (meta < 0 && f < h) continue;  // changed, smaller ID: attributed to f
-                    if ((mark[sl] >> l) & 1u) continue;
-                    classify(s.tb, hist, fam, delta, h, g1, f, s.hk[l], k1, meta & 0x7fffffff, s.hx[l],
-                             int(T1.vals[sl]), 0, 0, s.hts[l], ts1, want_t ? lts[q] : 0, acc);
-                }
-            }
-            __syncthreads();
-            for (int i = tid; i < n1; i += NT_C) mark[T1.list[i]] = 0;
+            }  // chunks
             tab_clear<NT_C>(T1, n1);
             if (agg) {
                 if (tid < 2) s.tot[tid] = 0;
@@ -1213,20 +1354,6 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 s.n_list = 0;
                 s.n_cl = 0;
             }
-        }
-        // fold the warp histograms of this item
-        __syncthreads();
-        for (int b = tid; b < kHistN; b += NT_C) {
-            unsigned long long v = 0;
-            for (int w = 0; w < NW_C; ++w) {
-                v += s.hist[w][b];
-                s.hist[w][b] = 0;
-                if (b < 32) {
-                    v -= s.hneg[w][b];
-                    s.hneg[w][b] = 0;
-                }
-            }
-            s.acc[b] += v;
         }
     }
     __syncthreads();
@@ -1349,7 +1476,8 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
     b += al(sizeof(int64_t) * nbs);
     b += al(sizeof(int32_t) * sh.r_cap) + al(sizeof(int64_t) * sh.cap);
-    const int64_t rn = sh.n_cta_nh, rc = 2 * int64_t(sh.n_cta_c);  // centre grid is up to 2 blocks per SM
+    b += 2 * al(sizeof(int32_t) * sh.cap) + al(sizeof(int64_t) * (sh.cap + 1));
+    const int64_t rn = sh.n_cta_nh, rc = 4 * int64_t(sh.n_cta_c);  // centre grid is up to 4 blocks per SM
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
     b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
@@ -1397,7 +1525,10 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->r_cap = sh.r_cap;
     cs->r_pool = static_cast<int32_t*>(take(sizeof(int32_t) * sh.r_cap));
     cs->r_off = static_cast<int64_t*>(take(sizeof(int64_t) * sh.cap));
-    const int64_t rn = sh.n_cta_nh, rc = 2 * int64_t(sh.n_cta_c);  // centre grid is up to 2 blocks per SM
+    cs->order = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
+    cs->oflag = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
+    cs->opre = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.cap + 1)));
+    const int64_t rn = sh.n_cta_nh, rc = 4 * int64_t(sh.n_cta_c);  // centre grid is up to 4 blocks per SM
     cs->onh_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
     cs->onh_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rn * sh.gs_nh));
     cs->onh_aux = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
@@ -1437,11 +1568,22 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
                              const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
     CountArgs A{S, sc, changed, changed_g, chg_bits, lo, n, side, dcounts_side, cs,
                 uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
-                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small ? 4096 : 8192))};
+                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small == 0 ? 8192 : 4096))};
     const unsigned gd = blocks_for(cs.e_cap, kScanBlock);
     const unsigned ge = capped(blocks_for(cs.e_cap, 256));
+    const unsigned gn = blocks_for(n, kScanBlock);
     k_run_begin<<<1, 1, 0, st>>>(sc, side);
+    k_order_flags<<<blocks_for(n, 256), 256, 0, st>>>(cs.sizes, n, cs.oflag);
+    k_scan_sums<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, nullptr, cs.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gn, nullptr);
+    k_scan_apply<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, nullptr, cs.block_sums, cs.opre);
+    k_order_place<<<blocks_for(n, 256), 256, 0, st>>>(cs.oflag, cs.opre, n, cs.order);
     k_nh_build<<<cs.n_cta_nh, NT_NH, sizeof(SmemNH), st>>>(A);
+    cudaMemsetAsync(cs.block_sums, 0, sizeof(int64_t) * kOrderBuckets, st);
+    k_dsort_count<<<ge, 256, 0, st>>>(A);
+    k_dsort_scan<<<1, 32, 0, st>>>(A);
+    k_dsort_scatter<<<ge, 256, 0, st>>>(A);
+    k_dsort_copy<<<ge, 256, 0, st>>>(A);
     k_d_prep<<<ge, 256, 0, st>>>(A);
     k_scan_sums<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_cnt, 0, &sc->n_d[side], cs.block_sums);
     k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, 0, &sc->n_d[side]);
@@ -1451,12 +1593,14 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
     k_set_loffg<<<ge, 256, 0, st>>>(A);
     k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
-    if (cs.center_small)
-        k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A);
-    else
-        k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A);
+    switch (cs.center_small) {
+        case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;
+        case 2: k_center<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemC<512, 4096>), st>>>(A); break;
+        case 3: k_center<256, 2048, 4><<<cs.n_cta_c * 4, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;
+        default: k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A); break;
+    }
     k_d_clean<<<ge, 256, 0, st>>>(A);
-    lc.total += 13;
+    lc.total += 22;
     lc.count += 2;
     return cudaGetLastError();
 }
@@ -1471,6 +1615,10 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
                              int(sizeof(SmemC<512, 8192>)));
         cudaFuncSetAttribute(k_center<256, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(sizeof(SmemC<256, 4096>)));
+        cudaFuncSetAttribute(k_center<512, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(SmemC<512, 4096>)));
+        cudaFuncSetAttribute(k_center<256, 2048, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(sizeof(SmemC<256, 2048>)));
         attr_done = true;
     }
     for (int64_t a = lo; a < hi; a += cs.cap) {

@@ -27,6 +27,9 @@ struct CountScratch {
     int32_t* nh_n = nullptr;         // [cap] length of each N(h) list
     int64_t* nh_toff = nullptr;      // [cap] start of the hash table of a large N(h)
     int32_t* nh_tcap = nullptr;      // [cap] its slots (0: no table)
+    int32_t* order = nullptr;        // [cap] processing order of k_nh_build: large neighbourhoods first
+    int32_t* oflag = nullptr;        // [cap]
+    int64_t* opre = nullptr;         // [cap+1]
     // neighbour lists N(h) and the inverted candidate lists L(g1)
     int64_t list_cap = 0;            // entries
     int32_t* nh_g = nullptr;         // [list_cap] neighbour g
@@ -67,7 +70,7 @@ struct CountScratch {
     int64_t* r_off = nullptr;        // [cap] start of h's index in the pool, -1: none
     int64_t r_min = 4096;            // sum of member degrees from which h gets the lists
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
-    int center_small = 1;            // 1: two 256-thread centre blocks per SM, 0: one 512-thread block
+    int center_small = 3;            // centre blocks per SM x threads: 3: 4 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     int64_t* h_total = nullptr;      // pinned host word for the list total
 };
 

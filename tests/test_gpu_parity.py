@@ -183,11 +183,13 @@ def test_neighbourhoods_built_in_place(E, monkeypatch, families):
 
 @pytest.mark.parametrize("families", [1, 2, 3])
 def test_restricted_lists(E, monkeypatch, families):
-    """Without the temporal family, a large N(h) (here from 600 neighbour
-    entries on) gets restricted incidence lists R(u), through which the
-    centre kernel meets N(g1) and N(h); with the pool too small for some of
-    them the rest take the hash-probing path in the same run."""
+    """Without the temporal family and with a list pool configured, a large
+    N(h) (here from 600 neighbour entries on) gets restricted incidence lists
+    R(u), through which the centre kernel meets N(g1) and N(h); with the pool
+    too small for some of them the rest take the hash-probing path in the
+    same run."""
     monkeypatch.setenv("ESC_COUNT_RMIN", "600")
+    monkeypatch.setenv("ESC_COUNT_RPOOL", str(1 << 22))
     _big_hyperedge_stream(E, families, 19)
     monkeypatch.setenv("ESC_COUNT_RPOOL", "12000")
     _big_hyperedge_stream(E, families, 23)
