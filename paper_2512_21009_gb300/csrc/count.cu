@@ -78,6 +78,11 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
     return x;
 }
 
+// bit of key k in the membership filter of a large N(h) (8 bits per table slot)
+__device__ __forceinline__ uint32_t filter_bit(int32_t k, uint32_t tcap) {
+    return fmix32(uint32_t(k) ^ 0x27d4eb2fu) & (8u * tcap - 1u);
+}
+
 __device__ __forceinline__ int part_of(int32_t k, int P) {
     return int((fmix32(uint32_t(k) ^ 0x9e3779b9u) >> 8) % uint32_t(P));
 }
@@ -369,7 +374,11 @@ __global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t 
             u = 0;
         }
         // list of up to u entries, plus a hash table for a large N(h)
-        sizes[i] = int32_t(u > kBigNH ? u + pow2_at_least(2 * u) : u);
+        // list of up to u entries; a large N(h) also gets its hash table
+        // (2u rounded up to a power of two slots) and a one-hash membership
+        // filter of 8 bits per slot (a quarter of the slots, as words)
+        const long long t = u > kBigNH ? (long long)pow2_at_least(2 * u) : 0;
+        sizes[i] = int32_t(u + t + t / 4);
     }
 }
 
@@ -537,6 +546,10 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             }
             __syncthreads();
         }
+        const bool big = uh > kBigNH;
+        uint32_t* const filt = reinterpret_cast<uint32_t*>(cs.nh_g + base + uh + cap);
+        if (big)
+            for (uint32_t t = tid; t < cap / 4; t += NT_NH) filt[t] = 0;
         acc.n_h2v += (tid < kh) ? (kh - tid + NT_NH - 1) / NT_NH : 0;
         if (tid == 0) acc.n_alg += (unsigned long long)(uh + kh);
         for (int m0 = 0; m0 < kh; m0 += NT_NH) {
@@ -560,17 +573,25 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             // each entry is read and then overwritten by the same thread
             const int sl = NH.list[q];
             const int32_t gg = NH.keys[sl];
-            const uint64_t xvq = huge ? xv_t[sl] : uint64_t(NH.vals[sl]) | (uint64_t(uint32_t(NH.aux[sl])) << 32);
-            const uint32_t x = uint32_t(xvq);
+            const uint64_t xvt = huge ? xv_t[sl] : uint64_t(NH.vals[sl]) | (uint64_t(uint32_t(NH.aux[sl])) << 32);
+            const uint32_t x = uint32_t(xvt) & kXMask;
+            const int kg = S.h_card[gg];
+            const bool chg_g = bit_test(A.chg, gg);
+            // the list entry also carries |g| and whether g changed, read
+            // in order by k_center instead of gathered per visit
             cs.nh_g[base + q] = gg;
-            cs.nh_xv[base + q] = xvq;
-            if (gg < h && bit_test(A.chg, gg)) continue;  // pair attributed elsewhere
+            cs.nh_xv[base + q] = (xvt & 0xffffffff00000000ull) | x | (uint64_t(kg) << 16) | (chg_g ? 1ull << 31 : 0ull);
+            if (cs.nh_ts) cs.nh_ts[base + q] = S.h_ts[gg];
+            if (big) {
+                const uint32_t fb = filter_bit(gg, cap);
+                atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+            }
+            if (gg < h && chg_g) continue;  // pair attributed elsewhere
             if (atomicAdd(&cs.lcnt[gg], 1) == 0) cs.d_list[atomicAdd(&A.sc->n_d[A.side], 1)] = gg;
             if ((fam & kFamV) && x >= 2)
-                acc.v2 += (unsigned long long)(x * (x - 1) / 2) * (unsigned long long)(kh + S.h_card[gg] - 4);
+                acc.v2 += (unsigned long long)(x * (x - 1) / 2) * (unsigned long long)(kh + kg - 4);
         }
         // a large N(h) also goes out as its hash table, probed by k_center
-        const bool big = uh > kBigNH;
         if (big && !huge) {
             const int64_t toff = base + uh;
             for (uint32_t t = tid; t <= NH.mask; t += NT_NH) {
@@ -594,7 +615,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         auto entry = [&](int q, int32_t& gg, int& x) {
             if (huge) {
                 gg = cs.nh_g[base + q];
-                x = int(uint32_t(cs.nh_xv[base + q]));
+                x = int(uint32_t(cs.nh_xv[base + q]) & kXMask);
             } else {
                 const int sl = NH.list[q];
                 gg = NH.keys[sl];
@@ -1169,7 +1190,15 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                         } else if (mode == 1) {
                             const int sl = T1.list[q];
                             const int32_t g2 = T1.keys[sl];
-                            const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), g2);
+                            // most g2 are not in N(h): the filter answers them
+                            // with one load; the rest probe the table
+                            const uint32_t tcap = uint32_t(s.htcap[l]);
+                            const uint32_t fb = filter_bit(g2, tcap);
+                            const uint32_t fw =
+                                reinterpret_cast<const uint32_t*>(cs.nh_g + s.htoff[l] + tcap)[fb >> 5];
+                            const int ps = ((fw >> (fb & 31)) & 1u)
+                                               ? probe_list_table(cs.nh_g + s.htoff[l], tcap - 1, g2)
+                                               : -1;
                             if (ps >= 0) {
                                 const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
                                 const int32_t meta = lk[q];
@@ -1183,14 +1212,16 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                                 if (sl >= 0 || (!agg && want_open)) {
                                     const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
                                     const int xh2 = int(xv2 & kXMask);
+                                    const int k2 = int((xv2 >> 16) & 0x7fffu);
+                                    const bool chg2 = ((xv2 >> 31) & 1u) != 0;
                                     const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
                                     if (sl >= 0) {
-                                        closed(l, h, g2, sl, xh2, vf2, S.h_card[g2], bit_test(A.chg, g2), skey, false);
-                                    } else if (g2 > g1 && !(g2 < h && bit_test(A.chg, g2))) {
+                                        closed(l, h, g2, sl, xh2, vf2, k2, chg2, skey, false);
+                                    } else if (g2 > g1 && !(g2 < h && chg2)) {
                                         // open pair centred at h, enumerated (temporal family kept)
                                         ++acc.n_meta;
-                                        classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, S.h_card[g2], s.hx[l],
-                                                 0, xh2, 0, s.hts[l], ts1, want_t ? S.h_ts[g2] : 0, acc);
+                                        classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, k2, s.hx[l], 0, xh2,
+                                                 0, s.hts[l], ts1, want_t ? cs.nh_ts[s.hnb[l] + q] : 0, acc);
                                     }
                                 }
                             }
@@ -1472,12 +1503,13 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += al(sizeof(int64_t) * sh.cap) + al(sizeof(int32_t) * sh.cap);
     b += al(sizeof(uint32_t) * sh.n_cta_nh * 2 * (kMaxCard + 1));
     b += 2 * (al(sizeof(int32_t) * sh.list_cap) + al(sizeof(uint64_t) * sh.list_cap));
+    b += sh.with_ts ? al(sizeof(int64_t) * sh.list_cap) : 0;
     b += 2 * al(sizeof(int32_t) * sh.e_cap) + al(sizeof(int64_t) * sh.e_cap);
     b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
     b += al(sizeof(int64_t) * nbs);
     b += al(sizeof(int32_t) * sh.r_cap) + al(sizeof(int64_t) * sh.cap);
     b += 2 * al(sizeof(int32_t) * sh.cap) + al(sizeof(int64_t) * (sh.cap + 1));
-    const int64_t rn = sh.n_cta_nh, rc = 4 * int64_t(sh.n_cta_c);  // centre grid is up to 4 blocks per SM
+    const int64_t rn = sh.n_cta_nh, rc = int64_t(sh.c_per_sm) * sh.n_cta_c;
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
     b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
@@ -1510,6 +1542,7 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->onh_hist = static_cast<uint32_t*>(take(sizeof(uint32_t) * sh.n_cta_nh * 2 * (kMaxCard + 1)));
     cs->nh_g = static_cast<int32_t*>(take(sizeof(int32_t) * sh.list_cap));
     cs->nh_xv = static_cast<uint64_t*>(take(sizeof(uint64_t) * sh.list_cap));
+    cs->nh_ts = sh.with_ts ? static_cast<int64_t*>(take(sizeof(int64_t) * sh.list_cap)) : nullptr;
     cs->l_i = static_cast<int32_t*>(take(sizeof(int32_t) * sh.list_cap));
     cs->l_xv = static_cast<uint64_t*>(take(sizeof(uint64_t) * sh.list_cap));
     cs->lcnt = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
@@ -1528,7 +1561,8 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->order = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
     cs->oflag = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
     cs->opre = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.cap + 1)));
-    const int64_t rn = sh.n_cta_nh, rc = 4 * int64_t(sh.n_cta_c);  // centre grid is up to 4 blocks per SM
+    const int64_t rn = sh.n_cta_nh, rc = int64_t(sh.c_per_sm) * sh.n_cta_c;
+    cs->c_per_sm = sh.c_per_sm;
     cs->onh_keys = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
     cs->onh_vals = static_cast<uint32_t*>(take(sizeof(uint32_t) * rn * sh.gs_nh));
     cs->onh_aux = static_cast<int32_t*>(take(sizeof(int32_t) * rn * sh.gs_nh));
@@ -1593,7 +1627,8 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
     k_set_loffg<<<ge, 256, 0, st>>>(A);
     k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
-    switch (cs.center_small) {
+    // four blocks per SM need the tables sized for them
+    switch (cs.center_small == 3 && cs.c_per_sm < 4 ? 1 : cs.center_small) {
         case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;
         case 2: k_center<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemC<512, 4096>), st>>>(A); break;
         case 3: k_center<256, 2048, 4><<<cs.n_cta_c * 4, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;

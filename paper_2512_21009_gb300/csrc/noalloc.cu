@@ -42,6 +42,8 @@ CountShape na_shape() {
     sh.gs_nh = sh.gs_c = kNATableSlots;
     sh.n_cta_nh = sh.n_cta_c = kNABlocks;
     sh.r_cap = 0;  // no restricted lists
+    sh.with_ts = true;
+    sh.c_per_sm = 2;
     return sh;
 }
 

@@ -33,7 +33,9 @@ struct CountScratch {
     // neighbour lists N(h) and the inverted candidate lists L(g1)
     int64_t list_cap = 0;            // entries
     int32_t* nh_g = nullptr;         // [list_cap] neighbour g
-    uint64_t* nh_xv = nullptr;       // [list_cap] |h & g| (low 16 bits), smallest shared vertex (high 32)
+    uint64_t* nh_xv = nullptr;       // [list_cap] |h & g| (bits 0-15), |g| (16-30), g changed (31),
+                                     // smallest shared vertex (32-63); a table slot holds |h & g| and the vertex
+    int64_t* nh_ts = nullptr;        // [list_cap] timestamp of g (temporal family only)
     int32_t* l_i = nullptr;          // [list_cap] index of h in the run
     uint64_t* l_xv = nullptr;        // [list_cap] as nh_xv
     // per hyperedge ID
@@ -71,6 +73,7 @@ struct CountScratch {
     int64_t r_min = 4096;            // sum of member degrees from which h gets the lists
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 4 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
+    int c_per_sm = 4;                // centre blocks per SM the overflow tables were sized for
     int64_t* h_total = nullptr;      // pinned host word for the list total
 };
 
@@ -81,6 +84,8 @@ struct CountShape {
     int64_t gs_nh, gs_c;
     int n_cta_nh, n_cta_c;
     int64_t r_cap;      // int32 entries of the restricted-list pool (0: none)
+    bool with_ts;       // keep the neighbours' timestamps in the lists (temporal family)
+    int c_per_sm;       // centre blocks per SM the overflow tables are sized for (2 or 4)
 };
 
 // Largest neighbour-entry count sum(deg) of a changed hyperedge the counter
