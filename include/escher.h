@@ -204,6 +204,11 @@ typedef struct {
     int64_t work[6];         /* counter work: centre items, N(g1) build entries,
                                 pair-pass visits, closed pairs, slow-path
                                 triple-intersection steps, aggregate-pass visits */
+    float ms_center;         /* device time of the centre kernel launches      */
+    int32_t center_launches; /* centre kernel launches timed in ms_center      */
+    int64_t alg_center;      /* the part of alg_entries read on behalf of the
+                                candidate neighbours g1 (the centre kernel's
+                                share: |g1| + sum of member degrees per pair)  */
 } esc_batch_stats;
 
 esc_status esc_set_profiling(esc_graph* g, int32_t on);
@@ -360,6 +365,28 @@ esc_status esc_server_destroy(esc_server* srv);
 esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int64_t* offsets,
                                     const int32_t* members, const int64_t* timestamps, uint32_t families,
                                     int64_t delta, uint64_t* out_counts, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Autotuning.  The counter's launch shape (centre blocks per SM x threads:
+ * 0: 1 x 512, 1: 2 x 256, 2: 2 x 512, 3: 4 x 256) and, without the temporal
+ * family, whether large neighbourhoods get restricted incidence lists, are
+ * timed on the graph's own data: the triads holding a sample of live
+ * hyperedges (ids: that graph's IDs, host or device memory) are counted and
+ * discarded, `reps` timed runs per candidate after one warm-up run, and the
+ * fastest candidate is kept for later calls.  Counts and store are left
+ * unchanged.  The paper fixes no such choice; it is a property of this
+ * implementation.  Errors: INVALID_ARG, NOT_FOUND (an ID not live), CUDA.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t center_shape;  /* the chosen shape, 0..3 as above                    */
+    int32_t restricted;    /* 1: restricted lists chosen                          */
+    float ms[8];           /* best time of each candidate: shapes 0..3 without,
+                              then with restricted lists (-1: not run)            */
+} esc_tune_result;
+
+esc_status esc_autotune(esc_graph* g, int64_t n_ids, const int32_t* ids, int32_t reps, esc_tune_result* out);
+esc_status esc_group_autotune(esc_group* grp, int32_t graph, int64_t n_ids, const int32_t* ids, int32_t reps,
+                              esc_tune_result* out);
 
 /* Library version string. */
 const char* esc_version(void);

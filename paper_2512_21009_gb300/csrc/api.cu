@@ -47,6 +47,7 @@ struct Engine {
     int32_t G = 0;
     std::vector<int64_t> vbase, ebase, ecap;
     std::vector<int32_t> nv;
+    int64_t inc_cap = 0;  // incidences of all graphs (capacity)
     Store S{};
     std::vector<void*> allocs;
     // call staging
@@ -77,6 +78,8 @@ struct Engine {
     } hs[4];
     size_t hs_lo[4] = {};  // first element of hs[k] not yet copied in this call
     bool profiling = false;
+    cudaEvent_t cev[32] = {};          // centre-kernel launch events (profiling)
+    int n_cev = 0;
     // sizing pass: alloc() only adds up the bytes it would take
     bool dry = false;
     int64_t dry_bytes = 0;
@@ -114,6 +117,8 @@ struct Engine {
         for (auto& h : hs)
             if (h.p) cudaFreeHost(h.p);
         for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto& e : cev)
             if (e) cudaEventDestroy(e);
     }
 
@@ -169,6 +174,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
         inc += per[g].capacity_incidences;
     }
     if (V > 0x7fffffffLL || Ecap > 0x7fffffffLL) return E->fail(ESC_ERR_UNSUPPORTED, "ID spaces exceed int32");
+    E->inc_cap = inc;
     Store& S = E->S;
     S.n_graphs = G;
     S.nv_total = V;
@@ -326,6 +332,9 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     }
     ESC_CU(upload_tables(st), "tables");
     for (auto& e : E->ev) ESC_CU(cudaEventCreate(&e), "event");
+    for (auto& e : E->cev) ESC_CU(cudaEventCreate(&e), "event");
+    E->cs.max_cev = 16;
+    E->cs.n_cev = &E->n_cev;
     ESC_CU(cudaStreamSynchronize(st), "sync");
     return ESC_OK;
 }
@@ -507,6 +516,8 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     const Store& S = E->S;
     LaunchCounter lc;
     const bool prof = E->profiling;
+    E->cs.cev = prof ? E->cev : nullptr;
+    E->n_cev = 0;
     if (prof) cudaEventRecord(E->ev[0], st);
     ESC_CU(store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc), "ingest");
     if (prof) cudaEventRecord(E->ev[1], st);
@@ -535,6 +546,13 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
         cudaEventElapsedTime(&L.ms_count_del, E->ev[1], E->ev[2]);
         cudaEventElapsedTime(&L.ms_store, E->ev[2], E->ev[3]);
         cudaEventElapsedTime(&L.ms_count_ins, E->ev[3], E->ev[4]);
+        L.ms_center = 0.f;
+        for (int k = 0; k < E->n_cev; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, E->cev[2 * k], E->cev[2 * k + 1]);
+            L.ms_center += ms;
+        }
+        L.center_launches = E->n_cev;
     }
     E->last.launches = lc.total;
     E->last.count_launches = lc.count;
@@ -544,6 +562,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     E->last.triads = int64_t(E->h_sc->stats[3]);
     E->last.alg_entries = int64_t(E->h_sc->stats[4]);
     for (int k = 0; k < 6; ++k) E->last.work[k] = int64_t(E->h_sc->stats[5 + k]);
+    E->last.alg_center = int64_t(E->h_sc->stats[11]);
     if (E->h_sc->status != 0) {
         E->err = describe(*E->h_sc);
         return esc_status(E->h_sc->status);
@@ -589,7 +608,7 @@ __global__ void k_mark_sel(Store S, Scalars* sc, const int32_t* ids, int64_t n, 
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t h = ids[i];
-    if (h < 0 || h >= S.ecap[0] || !bit_test(S.live, h)) {
+    if (h < 0 || h >= S.e_total || !bit_test(S.live, h)) {
         set_error(sc, kErrNotFound, -1, i, h);
         out_global[i] = 0;
         return;
@@ -603,17 +622,19 @@ __global__ void k_unmark_sel(Store S, const int32_t* ids, int64_t n) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t h = ids[i];
-    if (h >= 0 && h < S.ecap[0]) atomicAnd(&S.insb[h >> 5], ~(1u << (h & 31)));
+    if (h >= 0 && h < S.e_total) atomicAnd(&S.insb[h >> 5], ~(1u << (h & 31)));
 }
 
 __global__ void k_latch_api(Scalars* sc) { sc->gate = sc->status; }
 
 }  // namespace
 
-static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_t* oh, uint64_t* ov, uint64_t* ot) {
+static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_t* oh, uint64_t* ov, uint64_t* ot,
+                               float* ms_out = nullptr) {
     if (n < 0 || (n > 0 && !ids)) return E->fail(ESC_ERR_INVALID_ARG, "bad id list");
     cudaStream_t st = E->st;
     const Store& S = E->S;
+    E->cs.cev = nullptr;  // not timed
     int32_t* d_ids = nullptr;
     int32_t* d_glob = nullptr;
     ESC_CU(cudaMalloc(&d_ids, sizeof(int32_t) * (n > 0 ? n : 1)), "alloc");
@@ -631,6 +652,7 @@ static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_
     uint64_t* dside = S.dcounts + int64_t(S.n_graphs) * kCStride;
     cudaMemsetAsync(dside, 0, sizeof(uint64_t) * kCStride, st);
     LaunchCounter lc;
+    if (ms_out) cudaEventRecord(E->ev[0], st);
     if (n > 0) {
         k_mark_sel<<<unsigned((n + 255) / 256), 256, 0, st>>>(S, E->d_sc, d_ids, n, d_glob);
         k_latch_api<<<1, 1, 0, st>>>(E->d_sc);
@@ -642,12 +664,14 @@ static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_
         }
         k_unmark_sel<<<unsigned((n + 255) / 256), 256, 0, st>>>(S, d_glob, n);
     }
+    if (ms_out) cudaEventRecord(E->ev[1], st);
     cudaMemcpyAsync(E->h_counts, dside, sizeof(uint64_t) * kCStride, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(E->h_sc, E->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
     cudaMemsetAsync(dside, 0, sizeof(uint64_t) * kCStride, st);
     cudaError_t e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) return E->cuda_fail(e, "sync");
+    if (ms_out) cudaEventElapsedTime(ms_out, E->ev[0], E->ev[1]);
     E->lc.total += lc.total + (n > 0 ? 3 : 0);
     E->lc.count += lc.count;
     if (E->h_sc->status) {
@@ -657,6 +681,71 @@ static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_
     if (oh && (E->shared.families & kFamH)) memcpy(oh, E->h_counts, sizeof(uint64_t) * kNH);
     if (ov && (E->shared.families & kFamV)) memcpy(ov, E->h_counts + kOffV, sizeof(uint64_t) * kNV);
     if (ot && (E->shared.families & kFamT)) memcpy(ot, E->h_counts + kOffT, sizeof(uint64_t) * kNT);
+    return ESC_OK;
+}
+
+// Time the counter's launch shapes (and, without the temporal family, the
+// restricted lists) on the engine's own data -- the triads of a sample of
+// live hyperedges, counted and discarded -- and keep the fastest.
+static esc_status autotune(Engine* E, int64_t n, const int32_t* ids, int32_t reps, esc_tune_result* out) {
+    if (n <= 0 || !ids || reps <= 0 || !out) return E->fail(ESC_ERR_INVALID_ARG, "bad sample");
+    CountScratch& cs = E->cs;
+    const int shapes[4] = {0, 1, 2, 3};
+    const int64_t r_cap0 = cs.r_cap;
+    int32_t* const r_pool0 = cs.r_pool;
+    int32_t* extra = nullptr;
+    const bool try_r = !(E->shared.families & kFamT);
+    if (try_r && r_cap0 == 0) {
+        const int64_t want =
+            std::min<int64_t>(std::max<int64_t>(16 * E->inc_cap, int64_t(1) << 24), (int64_t(1) << 31) - 64);
+        if (cudaMalloc(&extra, sizeof(int32_t) * want) != cudaSuccess) {
+            cudaGetLastError();
+            extra = nullptr;
+        } else {
+            cs.r_pool = extra;
+            cs.r_cap = want;
+        }
+    }
+    for (int k = 0; k < 8; ++k) out->ms[k] = -1.f;
+    float best = 3.4e38f;
+    int best_shape = cs.center_small, best_r = r_cap0 > 0 ? 1 : 0;
+    for (int r = 0; r < 2; ++r) {
+        if (r == 1 && (!try_r || cs.r_cap == 0)) break;
+        const int64_t cap_now = cs.r_cap;
+        if (r == 0) cs.r_cap = 0;
+        for (int k = 0; k < 4; ++k) {
+            cs.center_small = shapes[k];
+            float t = 3.4e38f;
+            for (int rep = 0; rep <= reps; ++rep) {  // the first run warms up
+                float ms = 0.f;
+                esc_status s = local_triads(E, n, ids, nullptr, nullptr, nullptr, &ms);
+                if (s != ESC_OK) {
+                    cs.r_cap = r_cap0;
+                    cs.r_pool = r_pool0;
+                    if (extra) cudaFree(extra);
+                    return s;
+                }
+                if (rep > 0) t = std::min(t, ms);
+            }
+            out->ms[r * 4 + k] = t;
+            if (t < best) {
+                best = t;
+                best_shape = shapes[k];
+                best_r = r;
+            }
+        }
+        if (r == 0) cs.r_cap = cap_now;
+    }
+    cs.center_small = best_shape;
+    if (best_r == 1) {
+        if (extra) E->allocs.push_back(extra);  // kept for the engine's life
+    } else {
+        cs.r_cap = r_cap0;
+        cs.r_pool = r_pool0;
+        if (extra) cudaFree(extra);
+    }
+    out->center_shape = best_shape;
+    out->restricted = best_r;
     return ESC_OK;
 }
 
@@ -739,6 +828,16 @@ esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, 
                             int32_t n_out) {
     if (!grp) return ESC_ERR_INVALID_ARG;
     return esc::read_counts(grp->e, graph, type, window, out, n_out);
+}
+
+esc_status esc_group_autotune(esc_group* grp, int32_t graph, int64_t n_ids, const int32_t* ids, int32_t reps,
+                              esc_tune_result* out) {
+    if (!grp || graph < 0 || graph >= grp->e->G || n_ids <= 0 || !ids) return ESC_ERR_INVALID_ARG;
+    // the sample's IDs are the graph's own; the counter works on global IDs
+    std::vector<int32_t> glob(ids, ids + n_ids);
+    const int64_t base = grp->e->ebase[graph];
+    for (auto& h : glob) h = int32_t(h + base);
+    return esc::autotune(grp->e, n_ids, glob.data(), reps, out);
 }
 
 esc_status esc_group_destroy(esc_group* grp) {
@@ -865,6 +964,11 @@ esc_status esc_local_triads(esc_graph* g, int64_t n_ids, const int32_t* ids, uin
                             uint64_t* out_vertex, uint64_t* out_temporal) {
     if (!g) return ESC_ERR_INVALID_ARG;
     return esc::local_triads(g->e, n_ids, ids, out_hyperedge, out_vertex, out_temporal);
+}
+
+esc_status esc_autotune(esc_graph* g, int64_t n_ids, const int32_t* ids, int32_t reps, esc_tune_result* out) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    return esc::autotune(g->e, n_ids, ids, reps, out);
 }
 
 esc_status esc_destroy(esc_graph* g) {

@@ -243,6 +243,7 @@ struct Accum {
     unsigned long long v1, v2, v3;
     unsigned long long n_v2h, n_h2v, n_meta, n_tri, n_alg;
     unsigned long long w[6];  // items, build entries, pair visits, closed pairs, slow t steps, agg visits
+    unsigned long long n_alg_c;  // the part of n_alg counted by the centre kernel
 };
 
 struct Tables {
@@ -335,6 +336,7 @@ __device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
     long long r2 = block_sum<NT>((long long)acc.n_meta, red);
     long long r3 = block_sum<NT>((long long)acc.n_tri, red);
     long long r4 = block_sum<NT>((long long)acc.n_alg, red);
+    long long r5 = block_sum<NT>((long long)acc.n_alg_c, red);
     long long wk[6];
     for (int k = 0; k < 6; ++k) wk[k] = block_sum<NT>((long long)acc.w[k], red);
     if (threadIdx.x == 0) {
@@ -345,6 +347,7 @@ __device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
         atomicAdd(&A.sc->stats[2], (unsigned long long)r2);
         atomicAdd(&A.sc->stats[3], (unsigned long long)r3);
         atomicAdd(&A.sc->stats[4], (unsigned long long)r4);
+        if (r5) atomicAdd(&A.sc->stats[11], (unsigned long long)r5);
     }
 }
 
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
     const int64_t gs = cs.gs_nh;
     Tab gNH{cs.onh_keys + blockIdx.x * gs, cs.onh_vals + blockIdx.x * gs, cs.onh_aux + blockIdx.x * gs,
             cs.onh_list + blockIdx.x * (gs / 2), &s.n_list, uint32_t(gs - 1), int(gs / 2)};
-    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0};
     int cur_g = -1;
     const int32_t* v2h = S.vp.arena;
     for (;;) {
@@ -941,7 +944,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
     int32_t* g_lk = cs.oc_lk + blockIdx.x * (gs / 2);
     int64_t* g_lts = cs.oc_lts + blockIdx.x * (gs / 2);
     uint32_t* hist = s.hist[wid];
-    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}};
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0};
     const int64_t n_items = A.sc->items[A.side];
     const int nd = A.sc->n_d[A.side];
     int cur_g = -1;
@@ -977,6 +980,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
         // the method reads N(g1) (sum of member degrees) once per pair (h, g1)
         if (tid == 0) {
             acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)nh_all;
+            acc.n_alg_c += (unsigned long long)(u1 + k1) * (unsigned long long)nh_all;
             ++acc.w[0];
             acc.w[1] += (unsigned long long)u1;
         }
@@ -1155,13 +1159,23 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
                     const int idx = idx0 + tid;
                     int skey = -1;
-                    if (idx < wtot) {
-                        int l = 0, hi_l = nh - 1;  // the h of this work index: last l with hpre[l] <= idx
-                        while (l < hi_l) {
-                            const int mid = (l + hi_l + 1) >> 1;
-                            if (s.hpre[mid] <= idx) l = mid;
+                    // the h of a work index is the last l with hpre[l] <= idx:
+                    // one lane searches for the warp's first index, the others
+                    // step forward from there (a warp spans few h)
+                    const int iw = idx0 + (tid & ~31);
+                    int lw = 0;
+                    if (lane == 0 && iw < wtot) {
+                        int hi_l = nh - 1;
+                        while (lw < hi_l) {
+                            const int mid = (lw + hi_l + 1) >> 1;
+                            if (s.hpre[mid] <= iw) lw = mid;
                             else hi_l = mid - 1;
                         }
+                    }
+                    lw = __shfl_sync(0xffffffffu, lw, 0);
+                    if (idx < wtot) {
+                        int l = lw;
+                        while (l + 1 < nh && s.hpre[l + 1] <= idx) ++l;
                         const int q = idx - s.hpre[l];
                         const int32_t h = s.hh[l];
                         const int mode = s.hfrom[l];
@@ -1627,6 +1641,8 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
     k_set_loffg<<<ge, 256, 0, st>>>(A);
     k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
+    const bool timed = cs.cev && cs.n_cev && *cs.n_cev < cs.max_cev;
+    if (timed) cudaEventRecord(cs.cev[2 * *cs.n_cev], st);
     // four blocks per SM need the tables sized for them
     switch (cs.center_small == 3 && cs.c_per_sm < 4 ? 1 : cs.center_small) {
         case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;
@@ -1634,6 +1650,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
         case 3: k_center<256, 2048, 4><<<cs.n_cta_c * 4, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;
         default: k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A); break;
     }
+    if (timed) cudaEventRecord(cs.cev[2 * (*cs.n_cev)++ + 1], st);
     k_d_clean<<<ge, 256, 0, st>>>(A);
     lc.total += 22;
     lc.count += 2;

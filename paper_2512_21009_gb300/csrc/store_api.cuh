@@ -75,6 +75,10 @@ struct CountScratch {
     int center_small = 3;            // centre blocks per SM x threads: 3: 4 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     int c_per_sm = 4;                // centre blocks per SM the overflow tables were sized for
     int64_t* h_total = nullptr;      // pinned host word for the list total
+    // profiling: events around each centre-kernel launch of a call
+    cudaEvent_t* cev = nullptr;      // [2 * max_cev] or null
+    int max_cev = 0;
+    int* n_cev = nullptr;            // launches recorded in the current call
 };
 
 struct CountShape {

@@ -36,7 +36,7 @@ EXPORTED = [
     "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
     "esc_group_last_error", "esc_group_set_profiling", "esc_group_last_stats", "esc_group_launch_count",
     "esc_group_bytes", "esc_server_create", "esc_server_submit", "esc_server_wait", "esc_server_drain",
-    "esc_server_triads", "esc_server_get_stats", "esc_server_destroy",
+    "esc_server_triads", "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
     "esc_version", "esc_count_static_noalloc",
 ]
 
@@ -59,7 +59,8 @@ class esc_batch_stats(C.Structure):
                 ("ms_store", C.c_float), ("ms_count_ins", C.c_float), ("launches", C.c_int64),
                 ("count_launches", C.c_int64), ("v2h_reads", C.c_int64), ("h2v_reads", C.c_int64),
                 ("meta_reads", C.c_int64), ("triads", C.c_int64), ("alg_entries", C.c_int64),
-                ("work", C.c_int64 * 6)]
+                ("work", C.c_int64 * 6), ("ms_center", C.c_float), ("center_launches", C.c_int32),
+                ("alg_center", C.c_int64)]
 
 
 class esc_batch(C.Structure):
@@ -77,6 +78,10 @@ class esc_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("rejected", C.c_int64), ("completed", C.c_int64),
                 ("failed", C.c_int64), ("calls", C.c_int64), ("updates", C.c_int64),
                 ("pending_updates", C.c_int64)]
+
+
+class esc_tune_result(C.Structure):
+    _fields_ = [("center_shape", C.c_int32), ("restricted", C.c_int32), ("ms", C.c_float * 8)]
 
 
 _lib = None
@@ -124,6 +129,8 @@ def load(path: str = LIB_PATH):
     L.esc_server_triads.argtypes = [vp, i32, C.c_int, i64, vp, i32]
     L.esc_server_get_stats.argtypes = [vp, C.POINTER(esc_server_stats)]
     L.esc_server_destroy.argtypes = [vp]
+    L.esc_autotune.argtypes = [vp, i64, vp, i32, C.POINTER(esc_tune_result)]
+    L.esc_group_autotune.argtypes = [vp, i32, i64, vp, i32, C.POINTER(esc_tune_result)]
     L.esc_version.restype = C.c_char_p
     L.esc_count_static_noalloc.argtypes = [i32, i64, vp, vp, vp, u32, i64, vp, vp]
     L.esc_count_static_noalloc.restype = st
@@ -132,7 +139,7 @@ def load(path: str = LIB_PATH):
                  "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
                  "esc_group_set_profiling", "esc_group_last_stats", "esc_group_bytes", "esc_server_create",
                  "esc_server_submit", "esc_server_wait", "esc_server_drain", "esc_server_triads",
-                 "esc_server_get_stats", "esc_server_destroy"):
+                 "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -341,6 +348,30 @@ def esc_group_launch_count(grp: int) -> int:
     return int(load().esc_group_launch_count(grp))
 
 
+def _tune_dict(r: "esc_tune_result") -> dict:
+    return {"center_shape": r.center_shape, "restricted": r.restricted, "ms": list(r.ms)}
+
+
+def esc_autotune(h: int, ids, reps: int = 2) -> dict:
+    """Time the counter's launch shapes on the triads of the live hyperedges
+    ``ids`` and keep the fastest; returns the choice and every timing."""
+    L = load()
+    p, keep = _ptr(ids, np.int32)
+    r = esc_tune_result()
+    rc = L.esc_autotune(h, len(ids), p, int(reps), C.byref(r))
+    _check(rc, L.esc_last_error, h)
+    return _tune_dict(r)
+
+
+def esc_group_autotune(grp: int, graph: int, ids, reps: int = 2) -> dict:
+    L = load()
+    p, keep = _ptr(ids, np.int32)
+    r = esc_tune_result()
+    rc = L.esc_group_autotune(grp, int(graph), len(ids), p, int(reps), C.byref(r))
+    _check(rc, L.esc_group_last_error, grp)
+    return _tune_dict(r)
+
+
 # ---------------------------------------------------------------------------
 # serving loop
 # ---------------------------------------------------------------------------
@@ -499,6 +530,9 @@ class Graph:
 
     def launch_count(self) -> int:
         return esc_launch_count(self.h)
+
+    def autotune(self, ids, reps: int = 2) -> dict:
+        return esc_autotune(self.h, ids, reps)
 
     def close(self) -> None:
         if self.h:

@@ -8,7 +8,7 @@ import pytest
 import gen
 from oracle import OracleHypergraph
 from oracle import oracle as O
-from tests.harness import assert_counts_equal, assert_store_equal, caps_for, run_stream
+from tests.harness import GpuLive, assert_counts_equal, assert_store_equal, caps_for, run_stream
 
 pytestmark = pytest.mark.gpu
 
@@ -383,3 +383,34 @@ def test_large_overlaps(E, families):
     ids_g = g.apply_batch(ioff, imem, its, dels.astype(np.int32))
     assert np.array_equal(ids_g, ids_o)
     assert_counts_equal(g.counts(), O.counts(og, families, 1 << 40), "after")
+
+
+@pytest.mark.parametrize("families", [3, ALL])
+def test_autotune_keeps_counts_exact(E, families):
+    """The autotuner times every launch shape (and, without the temporal
+    family, restricted lists) on a sample of live hyperedges and keeps the
+    fastest; counts are untouched by it and stay exact afterwards."""
+    s = gen.random_small(31, 500, 700, 2, 12, membership="zipf", n_batches=2, n_ins=60, n_del=60)
+    init = s.initial
+    og = OracleHypergraph(s.n_vertices, init.offsets, init.members, init.timestamps)
+    delta = int(init.timestamps[-1] // 2)
+    g = E.Graph(s.n_vertices, init.offsets, init.members, init.timestamps, families=families, delta=delta,
+                **caps_for(s.n_vertices, 2000, 20000, 1000, 20000))
+    before = g.counts()
+    res = g.autotune(np.arange(0, init.n, 3, dtype=np.int32), reps=1)
+    assert 0 <= res["center_shape"] <= 3
+    assert all(m >= 0 for m in res["ms"][:4])
+    if families & 4:
+        assert res["restricted"] == 0 and all(m == -1 for m in res["ms"][4:])
+    assert_counts_equal(g.counts(), before, "after tuning")
+    live = GpuLive(init.n, init.timestamps)
+    for b in s.batches:
+        dels_o = og.resolve_ranks(b.del_ranks)
+        dels_g = live.resolve(b.del_ranks)
+        ids_o = og.apply_batch(b.inserts.offsets, b.inserts.members, b.inserts.timestamps, dels_o)
+        ids_g = g.apply_batch(b.inserts.offsets, b.inserts.members, b.inserts.timestamps, dels_g.astype(np.int32))
+        assert np.array_equal(ids_g, ids_o)
+        live.apply(dels_g, ids_g, b.inserts.timestamps)
+        assert_counts_equal(g.counts(), O.counts(og, families, delta), "after a batch")
+    with pytest.raises(E.EscError):
+        g.autotune(np.array([10 ** 6], np.int32))
