@@ -322,6 +322,14 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     // and partitioned paths run on small inputs; lower the neighbourhood size
     // from which restricted lists are built
     if (const char* env = getenv("ESC_CENTER_SMALL")) E->cs.center_small = atoi(env);
+    if (const char* env = getenv("ESC_COUNT_BIGNH")) {
+        long long v = atoll(env);
+        if (v >= 16) E->cs.big_nh = v;
+    }
+    if (const char* env = getenv("ESC_COUNT_M1PCT")) {
+        long long v = atoll(env);
+        if (v >= 1) E->cs.m1_pct = v;
+    }
     if (const char* env = getenv("ESC_COUNT_RMIN")) {
         long long v = atoll(env);
         if (v >= 1) E->cs.r_min = v;

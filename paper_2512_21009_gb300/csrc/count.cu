@@ -62,7 +62,6 @@ constexpr int NH_S = 4096;           // shared-memory N(h) table slots
 constexpr int LCH = 32;              // changed hyperedges per chunk of a centre work item
 constexpr int kSuper = 8;            // chunks of one g1 served by one build of N(g1)
 constexpr int kWin = 64;             // |h & g1| values served from the histogram window
-constexpr int kBigNH = 512;          // N(h) with more entries also gets a hash table in the lists
 constexpr int kIC = 32;              // |h & g1| up to which h & g1 is listed for the triple sizes
 constexpr int kHistSmem = 1024;      // |h| up to which the open-at-h histograms live in shared memory
 
@@ -262,17 +261,18 @@ __device__ __forceinline__ void load_tables(Tables& t, int nt) {
 
 // Classify the triad (a, b, c) with sizes ka, kb, kc, pairwise intersections
 // xab, xbc, xac and triple intersection t into the warp's histogram.
-__device__ __forceinline__ void classify(const Tables& tb, uint32_t* hist, uint32_t fam, int64_t delta, int32_t ia,
-                                         int32_t ib, int32_t ic, int ka, int kb, int kc, int xab, int xbc, int xac,
-                                         int t, int64_t ta, int64_t tbb, int64_t tc, Accum& acc) {
+// Class bins of the triad (a, b, c) with sizes ka, kb, kc, pairwise
+// intersections xab, xbc, xac and triple intersection t: bh the hyperedge
+// class, bt the temporal class (or -1: family not kept, outside the window).
+__device__ __forceinline__ void classify_bins(const Tables& tb, uint32_t fam, int64_t delta, int32_t ia, int32_t ib,
+                                              int32_t ic, int ka, int kb, int kc, int xab, int xbc, int xac, int t,
+                                              int64_t ta, int64_t tbb, int64_t tc, int& bh, int& bt, Accum& acc) {
     int ra = ka - xab - xac + t, rb = kb - xab - xbc + t, rc = kc - xbc - xac + t;
     int m = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xab - t > 0) << 3) | ((xbc - t > 0) << 4) |
             ((xac - t > 0) << 5) | ((t > 0) << 6);
     ++acc.n_tri;
-    if (fam & kFamH) {
-        int c = tb.cls30[m];
-        if (c >= 0) atomicAdd(&hist[c], 1u);
-    }
+    bh = (fam & kFamH) ? tb.cls30[m] : -1;
+    bt = -1;
     if (fam & kFamT) {
         // order the labels 0 (a), 1 (b), 2 (c) by (timestamp, ID)
         int64_t T[3] = {ta, tbb, tc};
@@ -283,10 +283,7 @@ __device__ __forceinline__ void classify(const Tables& tb, uint32_t* hist, uint3
         if (ESC_BEFORE(o2, o1)) { tmp = o1; o1 = o2; o2 = tmp; }
         if (ESC_BEFORE(o1, o0)) { tmp = o0; o0 = o1; o1 = tmp; }
 #undef ESC_BEFORE
-        if (T[o2] - T[o0] <= delta) {
-            int c = tb.cls96[tb.perm[perm_index(o0, o1)][m]];
-            if (c >= 0) atomicAdd(&hist[kHistT + c], 1u);
-        }
+        if (T[o2] - T[o0] <= delta) bt = tb.cls96[tb.perm[perm_index(o0, o1)][m]];
     }
 }
 
@@ -356,7 +353,7 @@ __device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t lo, int64_t n, int32_t* sizes,
-                          int64_t max_u) {
+                          int64_t max_u, int64_t big_nh) {
     int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     int lane = lane_id();
     if (i >= n) return;
@@ -376,11 +373,10 @@ __global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t 
             set_error(sc, kErrUnsupported, -4, h, u);
             u = 0;
         }
-        // list of up to u entries, plus a hash table for a large N(h)
         // list of up to u entries; a large N(h) also gets its hash table
         // (2u rounded up to a power of two slots) and a one-hash membership
         // filter of 8 bits per slot (a quarter of the slots, as words)
-        const long long t = u > kBigNH ? (long long)pow2_at_least(2 * u) : 0;
+        const long long t = u > big_nh ? (long long)pow2_at_least(2 * u) : 0;
         sizes[i] = int32_t(u + t + t / 4);
     }
 }
@@ -549,7 +545,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             }
             __syncthreads();
         }
-        const bool big = uh > kBigNH;
+        const bool big = uh > cs.big_nh;
         uint32_t* const filt = reinterpret_cast<uint32_t*>(cs.nh_g + base + uh + cap);
         if (big)
             for (uint32_t t = tid; t < cap / 4; t += NT_NH) filt[t] = 0;
@@ -1103,12 +1099,15 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                     int run = 0;
                     for (int l = 0; l < nh; ++l) {
                         s.hpre[l] = run;
+                        // a visit of N(g1) (mode 1: shared-memory list, one filter
+                        // load) costs less than a visit of N(h) (mode 0: list from
+                        // global memory, a hash probe); m1_pct weighs the two
                         int mode = 0, work = s.hnn[l];
                         if (!want_t && s.htcap[l] > 0) {
                             if (s.hr[l] >= 0 && k1 < min(s.hnn[l], n1)) {
                                 mode = 2;
                                 work = k1;
-                            } else if (s.hnn[l] > n1) {
+                            } else if (int64_t(n1) * 100 < int64_t(s.hnn[l]) * cs.m1_pct) {
                                 mode = 1;
                                 work = n1;
                             }
@@ -1132,8 +1131,12 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 const int wtot = s.hpre[nh];
                 if (tid == 0) acc.w[2] += (unsigned long long)wtot;
                 // a closed pair {g1, g2} for the item's l-th h
+                // a closed pair {g1, g2} for the item's l-th h; its bins go to
+                // bh / bt / bn (class, temporal class, open-at-h class taken
+                // back) for one warp-aggregated update, or, when direct, to
+                // the histograms at once
                 auto closed = [&](int l, int32_t h, int32_t g2, int sl, int xh2, int32_t vf2, int k2, bool chg2,
-                                  int& skey, bool direct) {
+                                  int64_t ts2, int& skey, int& bh, int& bt, int& bn, bool direct) {
                     const int kh = s.hk[l], xh1 = s.hx[l];
                     const int x12 = int(T1.vals[sl]);
                     if (want_open && !direct) atomicOr(&mark[sl], 1u << l);
@@ -1148,9 +1151,15 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                         const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
                                                   kh, s.hI[l], s.hIn[l], acc.w[4]);
                         if (want_open)
-                            classify(s.tb, hist, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l], ts1,
-                                     want_t ? S.h_ts[g2] : 0, acc);
-                        if (agg) atomicAdd(&s.hneg[wid][s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)]], 1u);
+                            classify_bins(s.tb, fam, delta, h, g1, g2, kh, k1, k2, xh1, x12, xh2, t, s.hts[l], ts1, ts2,
+                                          bh, bt, acc);
+                        if (agg) bn = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
+                        if (direct) {
+                            if (bh >= 0) atomicAdd(&hist[bh], 1u);
+                            if (bt >= 0) atomicAdd(&hist[kHistT + bt], 1u);
+                            if (bn >= 0) atomicAdd(&s.hneg[wid][bn], 1u);
+                            bh = bt = bn = -1;
+                        }
                         if (fam & kFamV)
                             acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
                                       2ull * t;
@@ -1158,7 +1167,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 };
                 for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
                     const int idx = idx0 + tid;
-                    int skey = -1;
+                    int skey = -1, bh = -1, bt = -1, bn = -1;
                     // the h of a work index is the last l with hpre[l] <= idx:
                     // one lane searches for the warp's first index, the others
                     // step forward from there (a warp spans few h)
@@ -1197,9 +1206,9 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                                 const int ps = probe_list_table(cs.nh_g + s.htoff[l], uint32_t(s.htcap[l] - 1), f);
                                 if (ps < 0) continue;
                                 const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
-                                int unused;
+                                int unused, dh = -1, dt = -1, dn = -1;
                                 closed(l, h, f, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), S.h_card[f],
-                                       bit_test(A.chg, f), unused, true);
+                                       bit_test(A.chg, f), want_t ? S.h_ts[f] : 0, unused, dh, dt, dn, true);
                             }
                         } else if (mode == 1) {
                             const int sl = T1.list[q];
@@ -1217,7 +1226,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                                 const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
                                 const int32_t meta = lk[q];
                                 closed(l, h, g2, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), meta & 0x7fffffff,
-                                       meta < 0, skey, false);
+                                       meta < 0, want_t ? lts[q] : 0, skey, bh, bt, bn, false);
                             }
                         } else {
                             const int32_t g2 = cs.nh_g[s.hnb[l] + q];
@@ -1229,19 +1238,25 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                                     const int k2 = int((xv2 >> 16) & 0x7fffu);
                                     const bool chg2 = ((xv2 >> 31) & 1u) != 0;
                                     const int32_t vf2 = int32_t(uint32_t(xv2 >> 32));
+                                    const int64_t ts2 = want_t ? cs.nh_ts[s.hnb[l] + q] : 0;
                                     if (sl >= 0) {
-                                        closed(l, h, g2, sl, xh2, vf2, k2, chg2, skey, false);
+                                        closed(l, h, g2, sl, xh2, vf2, k2, chg2, ts2, skey, bh, bt, bn, false);
                                     } else if (g2 > g1 && !(g2 < h && chg2)) {
                                         // open pair centred at h, enumerated (temporal family kept)
                                         ++acc.n_meta;
-                                        classify(s.tb, hist, fam, delta, h, g1, g2, s.hk[l], k1, k2, s.hx[l], 0, xh2,
-                                                 0, s.hts[l], ts1, want_t ? cs.nh_ts[s.hnb[l] + q] : 0, acc);
+                                        classify_bins(s.tb, fam, delta, h, g1, g2, s.hk[l], k1, k2, s.hx[l], 0, xh2, 0,
+                                                      s.hts[l], ts1, ts2, bh, bt, acc);
                                     }
                                 }
                             }
                         }
                     }
-                    if (agg) warp_count(&s.sub[0][0], skey);
+                    if (agg && __any_sync(0xffffffffu, skey >= 0)) warp_count(&s.sub[0][0], skey);
+                    // one shared-memory atomic per distinct bin of the warp
+                    // (most iterations of the hyperedge family classify nothing)
+                    if (__any_sync(0xffffffffu, bh >= 0)) warp_count(hist, bh);
+                    if (__any_sync(0xffffffffu, bt >= 0)) warp_count(hist + kHistT, bt);
+                    if (agg && __any_sync(0xffffffffu, bn >= 0)) warp_count(s.hneg[wid], bn);
                 }
                 __syncthreads();
                 if (agg) {
@@ -1677,7 +1692,7 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
         const int64_t b = a + cs.cap < hi ? a + cs.cap : hi;
         const int64_t n = b - a;
         // sizes of N(h) and the prefix that places every list
-        k_nh_size<<<blocks_for(n * 32, 256), 256, 0, st>>>(S, sc, changed, a, n, cs.sizes, max_u);
+        k_nh_size<<<blocks_for(n * 32, 256), 256, 0, st>>>(S, sc, changed, a, n, cs.sizes, max_u, cs.big_nh);
         const unsigned gb = blocks_for(n, kScanBlock);
         k_scan_sums<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, n, nullptr, cs.block_sums);
         k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gb, nullptr);

@@ -71,6 +71,8 @@ struct CountScratch {
     int64_t r_cap = 0;
     int64_t* r_off = nullptr;        // [cap] start of h's index in the pool, -1: none
     int64_t r_min = 4096;            // sum of member degrees from which h gets the lists
+    int64_t big_nh = 512;            // sum of member degrees above which N(h) gets a table and a filter
+    int64_t m1_pct = 100;            // visit N(g1) instead of N(h) when |N(g1)| * 100 < |N(h)| * m1_pct
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 4 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     int c_per_sm = 4;                // centre blocks per SM the overflow tables were sized for
