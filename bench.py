@@ -486,11 +486,13 @@ def run_batched(args):
     t_plain = time.perf_counter() - t0
     # batched: one call for every graph
     l0 = E.esc_group_launch_count(groups[1])
+    E.esc_group_set_profiling(groups[1], True)
     barrier(dist, dev)
     t0 = time.perf_counter()
     E.esc_group_apply(groups[1], batches)
     t_batched = time.perf_counter() - t0
     launches_batched = E.esc_group_launch_count(groups[1]) - l0
+    bst = E.esc_group_last_stats(groups[1])
     same = True
     for i in range(len(streams)):
         for tt in (0, 1, 2):
@@ -519,6 +521,10 @@ def run_batched(args):
                     "launches": int(launches_batched)},
         "batched_over_plain": t_plain / t_batched,
         "counts_identical": n_diff == 0,
+        "batched_call": {"count_ms": bst["ms_count_del"] + bst["ms_count_ins"], "triads": bst["triads"],
+                         "counter_work": dict(zip(["centre_items", "n_g1_build_entries", "pair_pass_visits",
+                                                   "closed_pairs", "slow_t_steps", "aggregate_visits"],
+                                                  bst["work"]))},
     }))
 
 

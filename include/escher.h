@@ -368,7 +368,7 @@ esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int6
 
 /* ------------------------------------------------------------------------
  * Autotuning.  The counter's launch shape (centre blocks per SM x threads:
- * 0: 1 x 512, 1: 2 x 256, 2: 2 x 512, 3: 4 x 256) and, without the temporal
+ * 0: 1 x 512, 1: 2 x 256, 2: 2 x 512, 3: 3 x 256) and, without the temporal
  * family, whether large neighbourhoods get restricted incidence lists, are
  * timed on the graph's own data: the triads holding a sample of live
  * hyperedges (ids: that graph's IDs, host or device memory) are counted and

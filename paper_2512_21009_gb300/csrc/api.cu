@@ -299,7 +299,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     sh.n_cta_nh = E->sm_count * 2;
     sh.n_cta_c = E->sm_count;
     sh.with_ts = (shared.families & kFamT) != 0;
-    sh.c_per_sm = 4;
+    sh.c_per_sm = 3;
     // restricted-list pool of a count run (int32 entries, below 2^31): none
     // unless asked for -- building the lists costs more than the probes they
     // save on the measured workloads

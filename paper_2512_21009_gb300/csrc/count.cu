@@ -849,6 +849,12 @@ struct SmemC {
     int hIn[LCH];
 };
 
+// three blocks of the default centre shape fit one SM's shared memory
+// (233,472 bytes, 1,024 of them reserved per block) and leave the rest to L1,
+// which the gathers of the pair pass use: four blocks (with |h & g1| listed
+// up to 16) were 8% slower on the 1M-vertex workload
+static_assert(sizeof(SmemC<256, 2048>) + 1024 <= 233472 / 3, "three 256-thread centre blocks per SM");
+
 // t = |h & g1 & g2| from the smallest shared vertices (see the file comment);
 // when both |h & g1| and |h & g2| exceed 1, the listed h & g1 (hI, nI
 // entries) is tested against g2, else every member of h.
@@ -1168,23 +1174,13 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                 for (int idx0 = 0; idx0 < wtot; idx0 += NT_C) {
                     const int idx = idx0 + tid;
                     int skey = -1, bh = -1, bt = -1, bn = -1;
-                    // the h of a work index is the last l with hpre[l] <= idx:
-                    // one lane searches for the warp's first index, the others
-                    // step forward from there (a warp spans few h)
-                    const int iw = idx0 + (tid & ~31);
-                    int lw = 0;
-                    if (lane == 0 && iw < wtot) {
-                        int hi_l = nh - 1;
-                        while (lw < hi_l) {
-                            const int mid = (lw + hi_l + 1) >> 1;
-                            if (s.hpre[mid] <= iw) lw = mid;
+                    if (idx < wtot) {
+                        int l = 0, hi_l = nh - 1;  // the h of this work index: last l with hpre[l] <= idx
+                        while (l < hi_l) {
+                            const int mid = (l + hi_l + 1) >> 1;
+                            if (s.hpre[mid] <= idx) l = mid;
                             else hi_l = mid - 1;
                         }
-                    }
-                    lw = __shfl_sync(0xffffffffu, lw, 0);
-                    if (idx < wtot) {
-                        int l = lw;
-                        while (l + 1 < nh && s.hpre[l + 1] <= idx) ++l;
                         const int q = idx - s.hpre[l];
                         const int32_t h = s.hh[l];
                         const int mode = s.hfrom[l];
@@ -1658,11 +1654,11 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
     const bool timed = cs.cev && cs.n_cev && *cs.n_cev < cs.max_cev;
     if (timed) cudaEventRecord(cs.cev[2 * *cs.n_cev], st);
-    // four blocks per SM need the tables sized for them
-    switch (cs.center_small == 3 && cs.c_per_sm < 4 ? 1 : cs.center_small) {
+    // three blocks per SM need the tables sized for them
+    switch (cs.center_small == 3 && cs.c_per_sm < 3 ? 1 : cs.center_small) {
         case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;
         case 2: k_center<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemC<512, 4096>), st>>>(A); break;
-        case 3: k_center<256, 2048, 4><<<cs.n_cta_c * 4, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;
+        case 3: k_center<256, 2048, 3><<<cs.n_cta_c * 3, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;
         default: k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A); break;
     }
     if (timed) cudaEventRecord(cs.cev[2 * (*cs.n_cev)++ + 1], st);
@@ -1684,7 +1680,7 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
                              int(sizeof(SmemC<256, 4096>)));
         cudaFuncSetAttribute(k_center<512, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(sizeof(SmemC<512, 4096>)));
-        cudaFuncSetAttribute(k_center<256, 2048, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(sizeof(SmemC<256, 2048>)));
         attr_done = true;
     }

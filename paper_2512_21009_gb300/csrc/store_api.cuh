@@ -74,7 +74,7 @@ struct CountScratch {
     int64_t big_nh = 512;            // sum of member degrees above which N(h) gets a table and a filter
     int64_t m1_pct = 100;            // visit N(g1) instead of N(h) when |N(g1)| * 100 < |N(h)| * m1_pct
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
-    int center_small = 3;            // centre blocks per SM x threads: 3: 4 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
+    int center_small = 3;            // centre blocks per SM x threads: 3: 3 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     int c_per_sm = 4;                // centre blocks per SM the overflow tables were sized for
     int64_t* h_total = nullptr;      // pinned host word for the list total
     // profiling: events around each centre-kernel launch of a call
@@ -91,7 +91,7 @@ struct CountShape {
     int n_cta_nh, n_cta_c;
     int64_t r_cap;      // int32 entries of the restricted-list pool (0: none)
     bool with_ts;       // keep the neighbours' timestamps in the lists (temporal family)
-    int c_per_sm;       // centre blocks per SM the overflow tables are sized for (2 or 4)
+    int c_per_sm;       // centre blocks per SM the overflow tables are sized for (2 or 3)
 };
 
 // Largest neighbour-entry count sum(deg) of a changed hyperedge the counter
