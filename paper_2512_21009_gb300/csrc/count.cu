@@ -82,6 +82,11 @@ __device__ __forceinline__ uint32_t filter_bit(int32_t k, uint32_t tcap) {
     return fmix32(uint32_t(k) ^ 0x27d4eb2fu) & (8u * tcap - 1u);
 }
 
+// bit of key k in a shared-memory filter of N(g1) of w words (w a power of two)
+__device__ __forceinline__ uint32_t bloom_bit(int32_t k, int w) {
+    return fmix32(uint32_t(k) ^ 0x5bd1e995u) & (uint32_t(w) * 32u - 1u);
+}
+
 __device__ __forceinline__ int part_of(int32_t k, int P) {
     return int((fmix32(uint32_t(k) ^ 0x9e3779b9u) >> 8) % uint32_t(P));
 }
@@ -847,6 +852,10 @@ struct SmemC {
     uint32_t xc[LCH][2];
     int32_t hI[LCH][kIC];      // h & g1 when 2 <= |h & g1| <= kIC
     int hIn[LCH];
+    // one-hash filter of an N(g1) whose table is in global memory (words; a
+    // power of two, smaller where the block's own table is larger)
+    static constexpr int BLOOM_W = T1_S >= 4096 ? 2048 : 4096;
+    uint32_t bloom[BLOOM_W];
 };
 
 // three blocks of the default centre shape fit one SM's shared memory
@@ -945,6 +954,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
     int32_t* g_list = cs.oc_list + blockIdx.x * (gs / 2);
     int32_t* g_lk = cs.oc_lk + blockIdx.x * (gs / 2);
     int64_t* g_lts = cs.oc_lts + blockIdx.x * (gs / 2);
+    int32_t* g_lkey = cs.oc_lkey + blockIdx.x * (gs / 2);
     uint32_t* hist = s.hist[wid];
     Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0};
     const int64_t n_items = A.sc->items[A.side];
@@ -990,6 +1000,10 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
         uint32_t* mark;
         int32_t* lk;
         int64_t* lts;
+        // an N(g1) too large for the block's shared table lives in global
+        // memory; then its keys are also kept in list order (lkey) and a
+        // shared-memory filter answers most "is g2 in N(g1)" questions
+        bool gbl = false;
         int P = 1;
         const uint32_t t1_cap = pow2_at_least(2 * u1);
         if (t1_cap <= min(A.c_smem_cap, uint32_t(T1_S))) {  // the block's table holds T1_S slots
@@ -1002,10 +1016,13 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
             mark = g_mark;
             lk = g_lk;
             lts = g_lts;
+            gbl = true;
             if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
             else P = int((4 * u1 + gs - 1) / gs);
         }
         for (int p = 0; p < P; ++p) {
+            if (gbl)
+                for (int i = tid; i < s.BLOOM_W; i += NT_C) s.bloom[i] = 0;
             // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p)
             for (int m0 = 0; m0 < k1; m0 += NT_C) {
                 const int n = min(NT_C, k1 - m0);
@@ -1034,6 +1051,11 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                     const int kf = S.h_card[f];
                     const bool changed_f = bit_test(A.chg, f);
                     lk[q] = kf | (changed_f ? int32_t(0x80000000u) : 0);
+                    if (gbl) {
+                        g_lkey[q] = f;
+                        const uint32_t bb = bloom_bit(f, s.BLOOM_W);
+                        atomicOr(&s.bloom[bb >> 5], 1u << (bb & 31));
+                    }
                     if (want_t) lts[q] = S.h_ts[f];
                     if (agg) {
                         const int x = int(T1.vals[sl]);
@@ -1207,8 +1229,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                                        bit_test(A.chg, f), want_t ? S.h_ts[f] : 0, unused, dh, dt, dn, true);
                             }
                         } else if (mode == 1) {
-                            const int sl = T1.list[q];
-                            const int32_t g2 = T1.keys[sl];
+                            const int32_t g2 = gbl ? g_lkey[q] : T1.keys[T1.list[q]];
                             // most g2 are not in N(h): the filter answers them
                             // with one load; the rest probe the table
                             const uint32_t tcap = uint32_t(s.htcap[l]);
@@ -1219,6 +1240,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                                                ? probe_list_table(cs.nh_g + s.htoff[l], tcap - 1, g2)
                                                : -1;
                             if (ps >= 0) {
+                                const int sl = T1.list[q];
                                 const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
                                 const int32_t meta = lk[q];
                                 closed(l, h, g2, sl, int(xv2 & kXMask), int32_t(uint32_t(xv2 >> 32)), meta & 0x7fffffff,
@@ -1227,7 +1249,13 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                         } else {
                             const int32_t g2 = cs.nh_g[s.hnb[l] + q];
                             if (P == 1 || part_of(g2, P) == p) {
-                                const int sl = tab_find(T1, g2);
+                                int sl = -1;
+                                if (gbl) {
+                                    const uint32_t bb = bloom_bit(g2, s.BLOOM_W);
+                                    if ((s.bloom[bb >> 5] >> (bb & 31)) & 1u) sl = tab_find(T1, g2);
+                                } else {
+                                    sl = tab_find(T1, g2);
+                                }
                                 if (sl >= 0 || (!agg && want_open)) {
                                     const uint64_t xv2 = cs.nh_xv[s.hnb[l] + q];
                                     const int xh2 = int(xv2 & kXMask);
@@ -1536,7 +1564,7 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 2 * al(sizeof(int32_t) * sh.cap) + al(sizeof(int64_t) * (sh.cap + 1));
     const int64_t rn = sh.n_cta_nh, rc = int64_t(sh.c_per_sm) * sh.n_cta_c;
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
-    b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 2 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
+    b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 3 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
     return b + 4096;
 }
@@ -1598,6 +1626,7 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->oc_list = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_lk = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_lts = static_cast<int64_t*>(take(sizeof(int64_t) * rc * (sh.gs_c / 2)));
+    cs->oc_lkey = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->h_total = pinned_word;
     cudaError_t e;
     if ((e = cudaMemsetAsync(cs->lcnt, 0, sizeof(int32_t) * sh.e_cap, st))) return e;

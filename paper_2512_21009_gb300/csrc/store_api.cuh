@@ -64,6 +64,7 @@ struct CountScratch {
     int32_t* oc_list = nullptr;
     int32_t* oc_lk = nullptr;
     int64_t* oc_lts = nullptr;
+    int32_t* oc_lkey = nullptr;      // keys of a global N(g1) in list order
     // restricted incidence lists of a large N(h): for each vertex u of the
     // graph, the neighbours f of h that hold u (a dense index over the
     // graph's vertices, then the lists)
