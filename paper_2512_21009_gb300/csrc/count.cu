@@ -14,17 +14,25 @@
 //   (ii) {h, g1, f},  g1 in N(h), f in N(g1) outside N(h), f != h
 //                                              -- open with centre g1.
 // Both are enumerated from the pair (h, g1).  The work is organised by g1
-// (centre-major): one block builds N(g1) once, in shared memory, with
-// x = |g1 & f| and the size, timestamp and changed flag of every f, and
-// then serves every changed h that has g1 as a candidate neighbour:
-//   1. k_nh_build   per changed h: N(h) with x_hg and the smallest shared
-//                   vertex, written as a list; the incident-vertex types 1
-//                   and 2; candidate pairs (g1, h) counted per g1;
-//   2. scans and k_scatter invert the pairs into lists L(g1);
-//   3. k_center     per (g1, part of L(g1)): N(g1) in shared memory; for each
-//                   h of the part, (i) by probing N(g1) with every g2 in N(h)
-//                   (which also marks N(h) inside N(g1)), then (ii) by one
-//                   pass over the unmarked entries of N(g1).
+// (centre-major): one block builds N(g1) once, with x = |g1 & f| and the
+// size, changed flag (and timestamp) of every f, and then serves the changed
+// h that have g1 as a candidate neighbour:
+//   1. k_nh_build   per changed h (largest first): N(h) with x_hg and the
+//                   smallest shared vertex, written as a list that also
+//                   carries |g|, whether g changed and its timestamp; a large
+//                   N(h) also as its hash table and a membership filter; the
+//                   incident-vertex types 1 and 2; candidate pairs (g1, h)
+//                   counted per g1; without the temporal family the open
+//                   triads centred at h, in aggregate;
+//   2. scans and k_scatter invert the pairs into lists L(g1), ordered by |g1|;
+//   3. k_center     per (g1, up to 8 chunks of 32 of L(g1)): N(g1) in shared
+//                   memory (or a global table with a shared filter); for
+//                   each h, (i) the pairs {g1, g2}: N(h) probing N(g1), or
+//                   N(g1) probing N(h)'s filter and table, whichever is
+//                   smaller (marking N(h) inside N(g1)); then (ii) the open
+//                   triads centred at g1: in aggregate from totals over
+//                   N(g1) minus the marked entries, or, with the temporal
+//                   family, counted per h by time position and bucket.
 // t = |h & g1 & g2| for a closed triple comes from the smallest shared
 // vertices: if |h & g1| = 1 it is [that vertex is in g2], and symmetrically;
 // otherwise the members of h are tested against g1 and g2.
