@@ -752,6 +752,8 @@ def run_serving(args):
     _load_group(E, grp, streams, max_bh, max_bi)
     torch.cuda.synchronize()
     t_load = time.time() - t0
+    if not args.no_graph_launch:
+        E.esc_group_set_graph_launch(grp, True)  # each call replays one captured CUDA graph
     models = [_IdModel(st.initial.n) for st in streams]
     nvs = [st.n_vertices for st in streams]
     t_clock = time.monotonic_ns() // 1000 - 3600 * 10 ** 6   # timestamps after every initial one
@@ -799,7 +801,8 @@ def run_serving(args):
                                 "Zipf(2.0) in [2,256]); Poisson arrivals, uniform graph, sizes log-uniform "
                                 "[10, 1e4], 1:1 insert/delete; hyperedge + temporal families"),
                    "offered_per_s": args.rate, "seconds_per_run": args.duration, "queue_updates": max_pending,
-                   "load_s": round(t_load, 1), "hyperedges": int(sum(st.initial.n for st in streams))},
+                   "load_s": round(t_load, 1), "hyperedges": int(sum(st.initial.n for st in streams)),
+                   "graph_launch": not args.no_graph_launch},
         "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
         "runs": runs,
         "continuous_over_one_per_call": cont["updates_per_s"] / max(runs["one_per_call"]["overload"]["updates_per_s"], 1e-9),
@@ -835,6 +838,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--no-graph-launch", action="store_true", help="serving: launch kernel by kernel")
     ap.add_argument("--ref-updates-per-step", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -367,6 +367,22 @@ esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int6
                                     int64_t delta, uint64_t* out_counts, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Graph launch.  With it on, every call of the graph (or group) replays one
+ * CUDA graph holding the whole device work of a call -- ingest, both counts,
+ * store update, fold -- captured at the first call: its kernels read the
+ * call's sizes on the device and plan the count runs there, so the same graph
+ * serves calls of any size within the configured limits.  A call whose
+ * neighbour lists do not fit one count run per side (the arena holds 512
+ * entries per batch hyperedge) is detected inside the graph before anything
+ * changes and is run again without the graph.  Results
+ * are identical either way; what changes is the host's launch work per call.
+ * A graph created on the legacy default stream moves to a stream of its own
+ * (calls still return only when done).  Errors: INVALID_ARG, CUDA.
+ * ------------------------------------------------------------------------ */
+esc_status esc_set_graph_launch(esc_graph* g, int32_t on);
+esc_status esc_group_set_graph_launch(esc_group* grp, int32_t on);
+
+/* ------------------------------------------------------------------------
  * Autotuning.  The counter's launch shape (centre blocks per SM x threads:
  * 0: 1 x 512, 1: 2 x 256, 2: 2 x 512, 3: 3 x 256) and, without the temporal
  * family, whether large neighbourhoods get restricted incidence lists, are

@@ -63,6 +63,8 @@ struct Engine {
     uint64_t* h_counts = nullptr;      // pinned [kCStride]
     int32_t* h_ids = nullptr;          // pinned [max_ins]
     int64_t* h_word = nullptr;         // pinned word read back by the counter
+    int64_t* h_dims = nullptr;         // pinned [3]: batches, inserts, deletes of the call
+    int64_t* d_dims = nullptr;         // device copy
     // device staging for host-pointer inputs
     int64_t* st_off = nullptr;
     int32_t* st_mem = nullptr;
@@ -79,6 +81,12 @@ struct Engine {
     size_t hs_lo[4] = {};  // first element of hs[k] not yet copied in this call
     bool profiling = false;
     cudaEvent_t cev[32] = {};          // centre-kernel launch events (profiling)
+    // calls as one replayed CUDA graph (a fixed launch sequence whose kernels
+    // read the call's sizes on the device)
+    bool graph_mode = false;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t own_st = nullptr;     // capture needs a stream other than the legacy one
+    int64_t graph_kernels = 0, graph_count_kernels = 0;
     int n_cev = 0;
     // sizing pass: alloc() only adds up the bytes it would take
     bool dry = false;
@@ -114,12 +122,15 @@ struct Engine {
         if (h_counts) cudaFreeHost(h_counts);
         if (h_ids) cudaFreeHost(h_ids);
         if (h_word) cudaFreeHost(h_word);
+        if (h_dims) cudaFreeHost(h_dims);
         for (auto& h : hs)
             if (h.p) cudaFreeHost(h.p);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
         for (auto& e : cev)
             if (e) cudaEventDestroy(e);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (own_st) cudaStreamDestroy(own_st);
     }
 
     esc_status fail(esc_status s, const std::string& m) {
@@ -149,6 +160,25 @@ static esc_status check_cfg(const esc_config* c, bool per_graph_only) {
     if (c->families == 0 || (c->families & ~7u)) return ESC_ERR_INVALID_ARG;
     if (c->delta < 0) return ESC_ERR_INVALID_ARG;
     return ESC_OK;
+}
+
+// Graph mode: calls replay one captured launch sequence.  Capture needs a
+// stream other than the legacy default one, so an engine created on that
+// stream gets its own (every call still synchronises before it returns).
+static cudaError_t set_graph_mode(Engine* E, bool on) {
+    if (E->gexec) {
+        cudaGraphExecDestroy(E->gexec);
+        E->gexec = nullptr;
+    }
+    E->graph_mode = on;
+    if (on && !E->st) {
+        if (!E->own_st) {
+            cudaError_t e = cudaStreamCreate(&E->own_st);
+            if (e != cudaSuccess) return e;
+        }
+        E->st = E->own_st;
+    }
+    return cudaSuccess;
 }
 
 static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, const esc_config* per,
@@ -261,6 +291,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     ESC_CU(E->alloc(&C.del_g, E->max_ins), "alloc");
     ESC_CU(E->alloc(&C.touched, V), "alloc");
     ESC_CU(E->alloc(&E->d_sc, 1), "alloc");
+    ESC_CU(E->alloc(&E->d_dims, 3), "alloc");
     C.sc = E->d_sc;
     C.batches = E->d_batches;
     ESC_CU(E->alloc(&E->st_off, E->max_ins + G + 1), "alloc");
@@ -273,6 +304,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
         ESC_CU(cudaMallocHost(&E->h_sc, sizeof(Scalars)), "pinned");
         ESC_CU(cudaMallocHost(&E->h_counts, sizeof(uint64_t) * kCStride), "pinned");
         ESC_CU(cudaMallocHost(&E->h_ids, sizeof(int32_t) * E->max_ins), "pinned");
+        ESC_CU(cudaMallocHost(&E->h_dims, sizeof(int64_t) * 3), "pinned");
     }
     // counter scratch: neighbour lists for a run of changed hyperedges (runs
     // are split when the lists would not fit), per-ID inversion arrays, and
@@ -322,6 +354,8 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     // and partitioned paths run on small inputs; lower the neighbourhood size
     // from which restricted lists are built
     if (const char* env = getenv("ESC_CENTER_SMALL")) E->cs.center_small = atoi(env);
+    if (const char* env = getenv("ESC_CALL_GRAPH"))
+        if (atoi(env) != 0) ESC_CU(set_graph_mode(E, true), "graph mode");
     if (const char* env = getenv("ESC_COUNT_BIGNH")) {
         long long v = atoll(env);
         if (v >= 16) E->cs.big_nh = v;
@@ -441,6 +475,48 @@ static esc_status stage(Engine* E, const T* src, size_t n, T* dst_area, int k, s
     return ESC_OK;
 }
 
+constexpr int kFixedRuns = 1;  // count runs per side in the captured sequence (the arena holds a batch)
+
+// The device work of one call, in order: ingest, count on the old graph,
+// delete, insert, count on the new graph, fold.  fixed: the sequence does not
+// depend on the call's sizes (every kernel reads them on the device; count
+// runs planned on the device), so it can be captured once into a CUDA graph.
+static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStream_t st, LaunchCounter& lc,
+                                   bool prof = false) {
+    const Store& S = E->S;
+    cudaError_t e;
+    if ((e = store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc))) return e;
+    if (fixed) {
+        // the inserted side's runs must fit the sequence before anything changes
+        if ((e = count_precheck_fixed(S, C, E->cs, E->max_u, kFixedRuns, st, lc))) return e;
+        if ((e = store_latch(C, st, lc))) return e;
+    }
+    if (prof) cudaEventRecord(E->ev[1], st);
+    if (fixed)
+        e = count_launch_fixed(S, C.sc, C.del, C.del_g, S.delb, C.dims + 2, 0, S.dcounts, E->cs, E->max_u,
+                               kFixedRuns, st, lc);
+    else
+        e = count_launch(S, C.sc, C.del, C.del_g, S.delb, 0, C.n_del, 0, S.dcounts, E->cs, E->max_u, st, lc);
+    if (e) return e;
+    if (fixed) {
+        // a failed count (the retry status) must leave the store unchanged
+        if ((e = store_latch(C, st, lc))) return e;
+    }
+    if (prof) cudaEventRecord(E->ev[2], st);
+    if ((e = store_delete(S, C, E->sm_count, st, lc))) return e;
+    if ((e = store_insert(S, C, E->sm_count, st, lc))) return e;
+    if (prof) cudaEventRecord(E->ev[3], st);
+    uint64_t* dins = S.dcounts + int64_t(S.n_graphs) * kCStride;
+    if (fixed)
+        e = count_launch_fixed(S, C.sc, C.ids, C.ins_g, S.insb, C.dims + 1, 1, dins, E->cs, E->max_u, kFixedRuns,
+                               st, lc);
+    else
+        e = count_launch(S, C.sc, C.ids, C.ins_g, S.insb, 0, C.n_ins, 1, dins, E->cs, E->max_u, st, lc);
+    if (e) return e;
+    if (prof) cudaEventRecord(E->ev[4], st);
+    return store_finish(S, C, E->sm_count, st, lc);
+}
+
 static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     if (n == 0) return ESC_OK;
     if (n < 0 || n > E->G || !bs) return E->fail(ESC_ERR_INVALID_ARG, "bad batch list");
@@ -516,44 +592,73 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     ESC_CU(cudaMemcpyAsync(E->d_batches, E->h_batches, sizeof(BatchIn) * n, cudaMemcpyHostToDevice, st), "copy");
     ESC_CU(cudaMemcpyAsync(E->d_bins_lo, bins, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st), "copy");
     ESC_CU(cudaMemcpyAsync(E->d_bdel_lo, bdel, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st), "copy");
-    ESC_CU(cudaMemsetAsync(E->d_sc, 0, sizeof(Scalars), st), "memset");
+    E->h_dims[0] = n;
+    E->h_dims[1] = tot_ins;
+    E->h_dims[2] = tot_del;
     Call C = E->C;
     C.n_batches = n;
     C.n_ins = tot_ins;
     C.n_del = tot_del;
-    const Store& S = E->S;
+    C.dims = E->d_dims;
     LaunchCounter lc;
     const bool prof = E->profiling;
-    E->cs.cev = prof ? E->cev : nullptr;
-    E->n_cev = 0;
-    if (prof) cudaEventRecord(E->ev[0], st);
-    ESC_CU(store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc), "ingest");
-    if (prof) cudaEventRecord(E->ev[1], st);
-    ESC_CU(count_launch(S, C.sc, C.del, C.del_g, S.delb, 0, tot_del, 0, S.dcounts, E->cs, E->max_u, st, lc),
-           "count (deleted side)");
-    if (prof) cudaEventRecord(E->ev[2], st);
-    ESC_CU(store_delete(S, C, st, lc), "store delete");
-    ESC_CU(store_insert(S, C, E->sm_count, st, lc), "store insert");
-    if (prof) cudaEventRecord(E->ev[3], st);
-    ESC_CU(count_launch(S, C.sc, C.ids, C.ins_g, S.insb, 0, tot_ins, 1,
-                        S.dcounts + int64_t(S.n_graphs) * kCStride, E->cs, E->max_u, st, lc),
-           "count (inserted side)");
-    if (prof) cudaEventRecord(E->ev[4], st);
-    ESC_CU(store_finish(S, C, E->sm_count, st, lc), "finish");
-    if (prof) cudaEventRecord(E->ev[5], st);
-    ESC_CU(cudaMemcpyAsync(E->h_sc, E->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "status");
-    if (tot_ins > 0)
-        ESC_CU(cudaMemcpyAsync(E->h_ids, C.out_local, sizeof(int32_t) * tot_ins, cudaMemcpyDeviceToHost, st), "ids");
-    ESC_CU(cudaStreamSynchronize(st), "sync");
+    // graph mode: one replay of the fixed launch sequence; a call whose lists
+    // need more count runs than the sequence holds fails inside it with the
+    // retry status (changing nothing) and runs again with host-planned runs
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const bool fixed = E->graph_mode && attempt == 0;
+        ESC_CU(cudaMemsetAsync(E->d_sc, 0, sizeof(Scalars), st), "memset");
+        ESC_CU(cudaMemcpyAsync(E->d_dims, E->h_dims, sizeof(int64_t) * 3, cudaMemcpyHostToDevice, st), "copy");
+        C.fixed = fixed;
+        C.grid_batches = fixed ? E->G : n;
+        C.grid_ins = fixed ? E->max_ins : tot_ins;
+        C.grid_del = fixed ? E->max_ins : tot_del;
+        E->cs.cev = prof && !fixed ? E->cev : nullptr;
+        E->n_cev = 0;
+        if (prof) cudaEventRecord(E->ev[0], st);
+        if (fixed) {
+            if (!E->gexec) {
+                // capture once; every later call replays the same graph
+                LaunchCounter lg;
+                cudaGraph_t graph = nullptr;
+                store_prepare();
+                count_prepare();
+                ESC_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "capture");
+                cudaError_t e = launch_sequence(E, C, true, st, lg);
+                cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&E->gexec, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) return E->cuda_fail(e, "graph capture");
+                E->graph_kernels = lg.total;
+                E->graph_count_kernels = lg.count;
+            }
+            ESC_CU(cudaGraphLaunch(E->gexec, st), "graph launch");
+            lc.total += E->graph_kernels;
+            lc.count += E->graph_count_kernels;
+        } else {
+            ESC_CU(launch_sequence(E, C, false, st, lc, prof), "launch");
+        }
+        if (prof) cudaEventRecord(E->ev[5], st);
+        ESC_CU(cudaMemcpyAsync(E->h_sc, E->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "status");
+        if (tot_ins > 0)
+            ESC_CU(cudaMemcpyAsync(E->h_ids, C.out_local, sizeof(int32_t) * tot_ins, cudaMemcpyDeviceToHost, st),
+                   "ids");
+        ESC_CU(cudaStreamSynchronize(st), "sync");
+        if (E->h_sc->status != kErrRetry) break;
+    }
     E->lc.total += lc.total;
     E->lc.count += lc.count;
     if (prof) {
         esc_batch_stats& L = E->last;
         cudaEventElapsedTime(&L.ms_total, E->ev[0], E->ev[5]);
-        cudaEventElapsedTime(&L.ms_ingest, E->ev[0], E->ev[1]);
-        cudaEventElapsedTime(&L.ms_count_del, E->ev[1], E->ev[2]);
-        cudaEventElapsedTime(&L.ms_store, E->ev[2], E->ev[3]);
-        cudaEventElapsedTime(&L.ms_count_ins, E->ev[3], E->ev[4]);
+        L.ms_ingest = L.ms_count_del = L.ms_store = L.ms_count_ins = 0.f;
+        if (!E->graph_mode || E->h_sc->status == 0) {
+            cudaEventElapsedTime(&L.ms_ingest, E->ev[0], E->ev[1]);
+            cudaEventElapsedTime(&L.ms_count_del, E->ev[1], E->ev[2]);
+            cudaEventElapsedTime(&L.ms_store, E->ev[2], E->ev[3]);
+            cudaEventElapsedTime(&L.ms_count_ins, E->ev[3], E->ev[4]);
+        }
         L.ms_center = 0.f;
         for (int k = 0; k < E->n_cev; ++k) {
             float ms = 0.f;
@@ -745,6 +850,10 @@ static esc_status autotune(Engine* E, int64_t n, const int32_t* ids, int32_t rep
         if (r == 0) cs.r_cap = cap_now;
     }
     cs.center_small = best_shape;
+    if (E->gexec) {  // a captured sequence holds the old shape
+        cudaGraphExecDestroy(E->gexec);
+        E->gexec = nullptr;
+    }
     if (best_r == 1) {
         if (extra) E->allocs.push_back(extra);  // kept for the engine's life
     } else {
@@ -846,6 +955,12 @@ esc_status esc_group_autotune(esc_group* grp, int32_t graph, int64_t n_ids, cons
     const int64_t base = grp->e->ebase[graph];
     for (auto& h : glob) h = int32_t(h + base);
     return esc::autotune(grp->e, n_ids, glob.data(), reps, out);
+}
+
+esc_status esc_group_set_graph_launch(esc_group* grp, int32_t on) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    cudaError_t e = esc::set_graph_mode(grp->e, on != 0);
+    return e == cudaSuccess ? ESC_OK : grp->e->cuda_fail(e, "graph mode");
 }
 
 esc_status esc_group_destroy(esc_group* grp) {
@@ -977,6 +1092,12 @@ esc_status esc_local_triads(esc_graph* g, int64_t n_ids, const int32_t* ids, uin
 esc_status esc_autotune(esc_graph* g, int64_t n_ids, const int32_t* ids, int32_t reps, esc_tune_result* out) {
     if (!g) return ESC_ERR_INVALID_ARG;
     return esc::autotune(g->e, n_ids, ids, reps, out);
+}
+
+esc_status esc_set_graph_launch(esc_graph* g, int32_t on) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    cudaError_t e = esc::set_graph_mode(g->e, on != 0);
+    return e == cudaSuccess ? ESC_OK : g->e->cuda_fail(e, "graph mode");
 }
 
 esc_status esc_destroy(esc_graph* g) {

@@ -311,7 +311,19 @@ struct CountArgs {
     uint64_t* dc;               // [G][kCStride]
     CountScratch cs;
     uint32_t nh_smem_cap, c_smem_cap;
+    bool dev;                   // the run's range comes from the device (planned by k_run_plan)
 };
+
+// The changed hyperedges of one count run, [lo, lo + n) of the side, and the
+// neighbour-list position their lists start at.
+struct RunRange {
+    int64_t lo, n, base;
+};
+
+__device__ __forceinline__ RunRange run_of(const CountArgs& A) {
+    if (A.dev) return RunRange{A.sc->run_lo[A.side], A.sc->run_n[A.side], A.sc->run_base[A.side]};
+    return RunRange{0, A.n, 0};
+}
 
 template <int NT>
 __device__ void flush(const CountArgs& A, unsigned long long* acc_bins, uint32_t (*hist)[128], int nw, int g,
@@ -365,14 +377,15 @@ __device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
 // 1. sizes and N(h)
 // ---------------------------------------------------------------------------
 
-__global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t lo, int64_t n, int32_t* sizes,
-                          int64_t max_u, int64_t big_nh) {
-    int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = lane_id();
-    if (i >= n) return;
+__global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t lo, int64_t n_host,
+                          const int32_t* n_dev, int32_t* sizes, int64_t max_u, int64_t big_nh) {
+    const int64_t n = n_dev ? *n_dev : n_host;
+    const int lane = lane_id();
+    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += (int64_t(gridDim.x) * blockDim.x) >> 5) {
     if (sc->gate) {  // the call failed earlier: the changed list may hold invalid IDs
         if (lane == 0) sizes[i] = 0;
-        return;
+        continue;
     }
     int32_t h = changed[lo + i];
     int k = S.h_card[h];
@@ -391,6 +404,7 @@ __global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t 
         // filter of 8 bits per slot (a quarter of the slots, as words)
         const long long t = u > big_nh ? (long long)pow2_at_least(2 * u) : 0;
         sizes[i] = int32_t(u + t + t / 4);
+    }
     }
 }
 
@@ -513,6 +527,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
     // without the temporal family k_center may meet N(g1) and a large N(h)
     // through restricted lists
     const bool use_r = !(fam & kFamT) && cs.r_cap > 0;
+    const RunRange R = run_of(A);
     uint32_t* ghx = cs.onh_hist + int64_t(blockIdx.x) * 2 * (kMaxCard + 1);
     __syncthreads();
     const int64_t gs = cs.gs_nh;
@@ -525,8 +540,8 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         __syncthreads();
         if (tid == 0) s.item = (long long)atomicAdd(&A.sc->qnh[A.side], 1ull);
         __syncthreads();
-        if (s.item >= A.n) break;
-        const int64_t i = cs.order[s.item];
+        if (s.item >= R.n) break;
+        const int64_t i = cs.order[s.item];  // index in the side
         const int32_t h = A.changed[A.lo + i];
         const int g = A.changed_g ? A.changed_g[A.lo + i] : 0;
         if (g != cur_g) {
@@ -540,7 +555,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         uh = block_sum<NT_NH>(uh, s.red);
         Tab NH;
         const uint32_t cap = pow2_at_least(2 * uh);
-        const int64_t base = cs.nh_off[i];
+        const int64_t base = cs.nh_off[i] - R.base;
         // a neighbourhood too large for the block's tables is built in place,
         // in the table part of its own list region (see k_nh_size)
         const bool huge = cap > A.nh_smem_cap && (int64_t)cap > gs;
@@ -719,17 +734,22 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
 constexpr int32_t kBigFirst = 4096;  // neighbour-region entries from which h goes first
 constexpr int kOrderBuckets = 16;    // log2 buckets of |g1| for the centre items
 
-__global__ void k_order_flags(const int32_t* sizes, int64_t n, int32_t* flag) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < n) flag[i] = sizes[i] >= kBigFirst ? 1 : 0;
+__global__ void k_order_flags(CountArgs A) {
+    const RunRange R = run_of(A);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < R.n; i += int64_t(gridDim.x) * blockDim.x)
+        A.cs.oflag[i] = A.cs.sizes[R.lo + i] >= kBigFirst ? 1 : 0;
 }
 
-// stable partition: the flagged indices in order, then the others in order
-__global__ void k_order_place(const int32_t* flag, const int64_t* pre, int64_t n, int32_t* order) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t nb = pre[n];
-    order[flag[i] ? pre[i] : nb + (i - pre[i])] = int32_t(i);
+// stable partition of the run: the flagged hyperedges in order, then the
+// others in order (as indices in the side)
+__global__ void k_order_place(CountArgs A) {
+    const RunRange R = run_of(A);
+    const int32_t* flag = A.cs.oflag;
+    const int64_t* pre = A.cs.opre;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < R.n; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t nb = pre[R.n];
+        A.cs.order[flag[i] ? pre[i] : nb + (i - pre[i])] = int32_t(R.lo + i);
+    }
 }
 
 __device__ __forceinline__ int g1_bucket(int k1) { return min(kOrderBuckets - 1, 31 - __clz(max(k1, 1))); }
@@ -795,18 +815,22 @@ __global__ void k_set_loffg(CountArgs A) {
 
 __global__ void k_scatter(CountArgs A) {
     const CountScratch& cs = A.cs;
-    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
-    if (i >= A.n || A.sc->gate) return;
-    const int32_t h = A.changed[A.lo + i];
-    const int64_t base = cs.nh_off[i];
-    const int nn = cs.nh_n[i];
-    for (int q = lane; q < nn; q += 32) {
-        const int32_t gg = cs.nh_g[base + q];
-        if (gg < h && bit_test(A.chg, gg)) continue;
-        const int64_t pos = cs.loffg[gg] + atomicAdd(&cs.lfill[gg], 1);
-        cs.l_i[pos] = int32_t(i);
-        cs.l_xv[pos] = cs.nh_xv[base + q];
+    if (A.sc->gate) return;
+    const RunRange R = run_of(A);
+    for (int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < R.n;
+         w += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+        const int64_t i = R.lo + w;  // index in the side
+        const int32_t h = A.changed[A.lo + i];
+        const int64_t base = cs.nh_off[i] - R.base;
+        const int nn = cs.nh_n[i];
+        for (int q = lane; q < nn; q += 32) {
+            const int32_t gg = cs.nh_g[base + q];
+            if (gg < h && bit_test(A.chg, gg)) continue;
+            const int64_t pos = cs.loffg[gg] + atomicAdd(&cs.lfill[gg], 1);
+            cs.l_i[pos] = int32_t(i);
+            cs.l_xv[pos] = cs.nh_xv[base + q];
+        }
     }
 }
 
@@ -933,6 +957,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
     // centred at h by k_nh_build, those centred at g1 here from totals
     const bool agg = want_open && !want_t;
     const CountScratch& cs = A.cs;
+    const RunRange R = run_of(A);
     const int32_t* v2h = S.vp.arena;
     const int32_t* h2v = S.hp.arena;
     load_tables(s.tb, NT_C);
@@ -1103,7 +1128,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                     s.hli[tid] = li;
                     s.hts[tid] = S.h_ts[h];
                     s.hmem[tid] = h2v + S.h_off[h];
-                    s.hnb[tid] = cs.nh_off[li];
+                    s.hnb[tid] = cs.nh_off[li] - R.base;
                     s.hnn[tid] = cs.nh_n[li];
                     s.htcap[tid] = cs.nh_tcap[li];
                     s.htoff[tid] = cs.nh_toff[li];
@@ -1659,21 +1684,40 @@ cudaError_t upload_tables(cudaStream_t st) {
     return cudaMemcpyToSymbolAsync(c_tables, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
 }
 
+void count_prepare() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_nh_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemNH)));
+    cudaFuncSetAttribute(k_center<512, 8192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemC<512, 8192>)));
+    cudaFuncSetAttribute(k_center<256, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemC<256, 4096>)));
+    cudaFuncSetAttribute(k_center<512, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemC<512, 4096>)));
+    cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemC<256, 2048>)));
+    done = true;
+}
+
+// One count run: the changed hyperedges [lo, lo + n) (host-planned), or the
+// range k_run_plan left on the device (dev).
 static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
-                             const uint32_t* chg_bits, int64_t lo, int64_t n, int side, uint64_t* dcounts_side,
-                             const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
+                             const uint32_t* chg_bits, int64_t lo, int64_t n, bool dev, int side,
+                             uint64_t* dcounts_side, const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
     CountArgs A{S, sc, changed, changed_g, chg_bits, lo, n, side, dcounts_side, cs,
                 uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
-                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small == 0 ? 8192 : 4096))};
+                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small == 0 ? 8192 : 4096)), dev};
     const unsigned gd = blocks_for(cs.e_cap, kScanBlock);
     const unsigned ge = capped(blocks_for(cs.e_cap, 256));
-    const unsigned gn = blocks_for(n, kScanBlock);
+    const int64_t nmax = dev ? cs.cap : n;  // what the grids are made for
+    const unsigned gn = blocks_for(nmax, kScanBlock);
+    const int32_t* n_run = dev ? &sc->run_n32[side] : nullptr;
     k_run_begin<<<1, 1, 0, st>>>(sc, side);
-    k_order_flags<<<blocks_for(n, 256), 256, 0, st>>>(cs.sizes, n, cs.oflag);
-    k_scan_sums<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, nullptr, cs.block_sums);
-    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gn, nullptr);
-    k_scan_apply<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, nullptr, cs.block_sums, cs.opre);
-    k_order_place<<<blocks_for(n, 256), 256, 0, st>>>(cs.oflag, cs.opre, n, cs.order);
+    k_order_flags<<<capped(blocks_for(nmax, 256)), 256, 0, st>>>(A);
+    k_scan_sums<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, n_run, cs.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gn, n_run);
+    k_scan_apply<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, n_run, cs.block_sums, cs.opre);
+    k_order_place<<<capped(blocks_for(nmax, 256)), 256, 0, st>>>(A);
     k_nh_build<<<cs.n_cta_nh, NT_NH, sizeof(SmemNH), st>>>(A);
     cudaMemsetAsync(cs.block_sums, 0, sizeof(int64_t) * kOrderBuckets, st);
     k_dsort_count<<<ge, 256, 0, st>>>(A);
@@ -1688,7 +1732,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, 0, &sc->n_d[side]);
     k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
     k_set_loffg<<<ge, 256, 0, st>>>(A);
-    k_scatter<<<blocks_for(n * 32, 256), 256, 0, st>>>(A);
+    k_scatter<<<capped(blocks_for(nmax * 32, 256)), 256, 0, st>>>(A);
     const bool timed = cs.cev && cs.n_cev && *cs.n_cev < cs.max_cev;
     if (timed) cudaEventRecord(cs.cev[2 * *cs.n_cev], st);
     // three blocks per SM need the tables sized for them
@@ -1708,24 +1752,13 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
 cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                          const uint32_t* chg_bits, int64_t lo, int64_t hi, int side, uint64_t* dcounts_side,
                          const CountScratch& cs, int64_t max_u, cudaStream_t st, LaunchCounter& lc) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_nh_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemNH)));
-        cudaFuncSetAttribute(k_center<512, 8192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(SmemC<512, 8192>)));
-        cudaFuncSetAttribute(k_center<256, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(SmemC<256, 4096>)));
-        cudaFuncSetAttribute(k_center<512, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(SmemC<512, 4096>)));
-        cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(sizeof(SmemC<256, 2048>)));
-        attr_done = true;
-    }
+    count_prepare();
     for (int64_t a = lo; a < hi; a += cs.cap) {
         const int64_t b = a + cs.cap < hi ? a + cs.cap : hi;
         const int64_t n = b - a;
         // sizes of N(h) and the prefix that places every list
-        k_nh_size<<<blocks_for(n * 32, 256), 256, 0, st>>>(S, sc, changed, a, n, cs.sizes, max_u, cs.big_nh);
+        k_nh_size<<<blocks_for(n * 32, 256), 256, 0, st>>>(S, sc, changed, a, n, nullptr, cs.sizes, max_u,
+                                                           cs.big_nh);
         const unsigned gb = blocks_for(n, kScanBlock);
         k_scan_sums<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, n, nullptr, cs.block_sums);
         k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gb, nullptr);
@@ -1735,7 +1768,8 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
         if (*cs.h_total <= cs.list_cap) {
-            if ((e = count_run(S, sc, changed, changed_g, chg_bits, a, n, side, dcounts_side, cs, st, lc))) return e;
+            if ((e = count_run(S, sc, changed, changed_g, chg_bits, a, n, false, side, dcounts_side, cs, st, lc)))
+                return e;
             continue;
         }
         // the lists do not fit: split [a, b) by the prefix of the sizes
@@ -1753,6 +1787,130 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
         }
     }
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// count runs planned on the device: a fixed launch sequence (capturable in a
+// CUDA graph) for a side whose size the kernels read from n_side
+// ---------------------------------------------------------------------------
+
+__global__ void k_side_n(Scalars* sc, int side, const int64_t* n_side) {
+    sc->n_side[side] = int32_t(*n_side);
+    sc->run_lo[side] = 0;
+    sc->run_n[side] = 0;
+}
+
+// Run r of a side: from the end of run r - 1, the longest range of changed
+// hyperedges whose lists fit the arena.
+__global__ void k_run_plan(Scalars* sc, int side, const int64_t* nh_off, int64_t list_cap) {
+    const int64_t n = sc->n_side[side];
+    const int64_t lo = sc->run_lo[side] + sc->run_n[side];
+    int64_t hi = lo;
+    if (lo < n && !sc->gate) {
+        const int64_t lim = nh_off[lo] + list_cap;
+        int64_t a = lo, b = n;  // the last index whose prefix stays within lim
+        while (a < b) {
+            const int64_t mid = (a + b + 1) >> 1;
+            if (nh_off[mid] <= lim) a = mid;
+            else b = mid - 1;
+        }
+        hi = a;
+        if (hi == lo) set_error(sc, kErrUnsupported, -9, lo, nh_off[lo + 1] - nh_off[lo]);
+    }
+    sc->run_lo[side] = lo;
+    sc->run_n[side] = hi - lo;
+    sc->run_n32[side] = int32_t(hi - lo);
+    sc->run_base[side] = lo < n ? nh_off[lo] : 0;
+}
+
+__global__ void k_run_check(Scalars* sc, int side) {
+    if (!sc->gate && sc->run_lo[side] + sc->run_n[side] < sc->n_side[side])
+        set_error(sc, kErrRetry, -10, side, sc->run_lo[side] + sc->run_n[side]);
+}
+
+// Before the store changes: the neighbour-list sizes the inserted side will
+// have (the sum of the members' new degrees, as k_nh_size will find after the
+// insert) and whether the fixed sequence's runs hold them; if not, the call
+// takes the retry status now, while nothing has changed.
+__global__ void k_pre_sizes(Store S, Call C, int32_t* sizes, int64_t max_u, int64_t big_nh) {
+    const int64_t n = C.dims[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) C.sc->n_side[1] = int32_t(n);
+    if (C.sc->gate) return;
+    const int lane = lane_id();
+    for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < n;
+         j += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+        const int64_t p0 = C.ins_off[j];
+        const int k = C.card[j];
+        long long u = 0;
+        for (int t = lane; t < k; t += 32) {
+            const int32_t v = C.sorted[p0 + t];
+            u += S.v_deg[v] - S.v_ndel[v] + S.v_nins[v];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (lane == 0) {
+            if (u > max_u) u = 0;  // the ingest check reports it
+            const long long t = u > big_nh ? (long long)pow2_at_least(2 * u) : 0;
+            sizes[j] = int32_t(u + t + t / 4);
+        }
+    }
+}
+
+__global__ void k_pre_plan(Scalars* sc, const int64_t* pre, int64_t list_cap, int runs) {
+    if (sc->gate) return;
+    const int64_t n = sc->n_side[1];
+    int64_t lo = 0;
+    for (int r = 0; r < runs && lo < n; ++r) {
+        const int64_t lim = pre[lo] + list_cap;
+        int64_t a = lo, b = n;
+        while (a < b) {
+            const int64_t mid = (a + b + 1) >> 1;
+            if (pre[mid] <= lim) a = mid;
+            else b = mid - 1;
+        }
+        if (a == lo) return;  // one list alone exceeds the arena: the count reports it
+        lo = a;
+    }
+    if (lo < n) set_error(sc, kErrRetry, -11, 1, lo);
+}
+
+cudaError_t count_precheck_fixed(const Store& S, const Call& C, const CountScratch& cs, int64_t max_u, int runs,
+                                 cudaStream_t st, LaunchCounter& lc) {
+    const int32_t* n1 = &C.sc->n_side[1];
+    k_pre_sizes<<<capped(blocks_for(cs.cap * 32, 256)), 256, 0, st>>>(S, C, cs.oflag, max_u, cs.big_nh);
+    const unsigned gb = blocks_for(cs.cap, kScanBlock);
+    k_scan_sums<int32_t><<<gb, kScanNT, 0, st>>>(cs.oflag, 0, n1, cs.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gb, n1);
+    k_scan_apply<int32_t><<<gb, kScanNT, 0, st>>>(cs.oflag, 0, n1, cs.block_sums, cs.opre);
+    k_pre_plan<<<1, 1, 0, st>>>(C.sc, cs.opre, cs.list_cap, runs);
+    lc.total += 5;
+    return cudaGetLastError();
+}
+
+cudaError_t count_launch_fixed(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
+                               const uint32_t* chg_bits, const int64_t* n_side, int side, uint64_t* dcounts_side,
+                               const CountScratch& cs, int64_t max_u, int runs, cudaStream_t st,
+                               LaunchCounter& lc) {
+    count_prepare();
+    const int32_t* nd = &sc->n_side[side];
+    k_side_n<<<1, 1, 0, st>>>(sc, side, n_side);
+    k_nh_size<<<capped(blocks_for(cs.cap * 32, 256)), 256, 0, st>>>(S, sc, changed, 0, 0, nd, cs.sizes, max_u,
+                                                                    cs.big_nh);
+    const unsigned gb = blocks_for(cs.cap, kScanBlock);
+    k_scan_sums<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, 0, nd, cs.block_sums);
+    k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gb, nd);
+    k_scan_apply<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, 0, nd, cs.block_sums, cs.nh_off);
+    lc.total += 5;
+    cudaError_t e;
+    for (int r = 0; r < runs; ++r) {
+        k_run_plan<<<1, 1, 0, st>>>(sc, side, cs.nh_off, cs.list_cap);
+        ++lc.total;
+        if ((e = count_run(S, sc, changed, changed_g, chg_bits, 0, 0, true, side, dcounts_side, cs, st, lc)))
+            return e;
+    }
+    k_run_check<<<1, 1, 0, st>>>(sc, side);
+    ++lc.total;
+    return cudaGetLastError();
 }
 
 }  // namespace esc

@@ -37,6 +37,10 @@ constexpr uint32_t kFamH = 1u, kFamV = 2u, kFamT = 4u;
 // status codes, identical to esc_status
 constexpr int kOk = 0, kErrInvalid = 1, kErrNotFound = 2, kErrNoMem = 3, kErrUnsupported = 4,
               kErrTimeout = 5, kErrCuda = 6;
+// internal: the neighbour lists of a side needed more count runs than a
+// fixed launch sequence holds; nothing changed and the call is run again
+// with runs planned on the host (never returned to a caller)
+constexpr int kErrRetry = 9;
 
 __host__ __device__ inline int slab_class(int64_t n) {
     int c = 0;
@@ -73,6 +77,11 @@ struct Scalars {
     int64_t items[2];     // centre work items
     int32_t n_d[2];       // distinct candidate neighbours g1 of one count run
     unsigned long long r_used[2];  // int32 entries of the restricted-list pool taken in this run
+    // count runs planned on the device (per side): the changed hyperedges
+    // [run_lo, run_lo + run_n) of the side's n_side, their lists starting at
+    // neighbour-list position run_base
+    int64_t run_lo[2], run_n[2], run_base[2];
+    int32_t n_side[2], run_n32[2];
     unsigned long long stats[16]; // v2h, h2v, meta reads, triads, algorithmic entries, then counter work
 };
 
@@ -127,7 +136,12 @@ struct Call {
     int32_t n_batches;
     const BatchIn* batches;  // device [n_batches]
     int64_t* nnz_lo;         // device [n_batches+1]: member offsets of each batch
-    int64_t n_ins, n_del;    // totals
+    int64_t n_ins, n_del;    // totals (host copies, for launch decisions)
+    const int64_t* dims;     // device [3]: n_batches, n_ins, n_del (what the kernels read)
+    // sizes the launch grids are made for: the call's own, or, for a launch
+    // sequence that serves calls of any size (a CUDA graph), the limits
+    int64_t grid_batches, grid_ins, grid_del;
+    bool fixed;              // launch every kernel even when its part of the call is empty
     int64_t max_nnz;         // staging capacity
     int64_t* ins_off;        // [n_ins+1]
     int32_t* raw;            // [max_nnz] members, global vertex IDs

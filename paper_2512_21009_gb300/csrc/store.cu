@@ -16,6 +16,8 @@
 // The first error found latches a "gate" word; every later kernel that would
 // change the store reads the gate first and does nothing when it is set, so a
 // failed call leaves the store unchanged.
+#include <algorithm>
+
 #include "escher_internal.cuh"
 #include "store_api.cuh"
 
@@ -42,6 +44,19 @@ __device__ __forceinline__ void pool_clamp(const SlabPool& P) {
         if (P.top[c] < 0) P.top[c] = 0;
 }
 
+// Sizes of the call, read on the device (so one launch sequence serves calls
+// of any size, e.g. replayed from a CUDA graph).
+__device__ __forceinline__ int nbat(const Call& C) { return int(C.dims[0]); }
+__device__ __forceinline__ int64_t nins(const Call& C) { return C.dims[1]; }
+__device__ __forceinline__ int64_t ndel(const Call& C) { return C.dims[2]; }
+
+// Grid-stride ranges: one thread, or one warp, per element.
+#define ESC_FOR_THREADS(i, n) \
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < (n); i += int64_t(gridDim.x) * blockDim.x)
+#define ESC_FOR_WARPS(i, n)                                                            \
+    for (int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < (n); \
+         i += (int64_t(gridDim.x) * blockDim.x) >> 5)
+
 __device__ __forceinline__ void touch(const Store& S, const Call& C, int32_t v) {
     if (atomicExch(&S.v_touch[v], 1) == 0) {
         int t = atomicAdd(&C.sc->n_touched, 1);
@@ -60,10 +75,11 @@ __global__ void k_plan(Call C) {
     __shared__ long long carry_s;
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < C.n_batches; b0 += 1024) {
+    const int nb = nbat(C);
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
         int b = b0 + threadIdx.x;
         long long nnz = 0;
-        if (b < C.n_batches) {
+        if (b < nb) {
             const BatchIn& B = C.batches[b];
             if (B.n_ins > 0) {
                 if (B.off[0] != 0) set_error(C.sc, kErrInvalid, b, 0, B.off[0]);
@@ -74,13 +90,13 @@ __global__ void k_plan(Call C) {
         // members of one call stay below 2^31
         int tot;
         int pre = block_exclusive_scan<1024>(int(nnz > 0x7fffffff ? 0x7fffffff : nnz), &tot, warp_tmp);
-        if (b < C.n_batches) C.nnz_lo[b] = carry_s + pre;
+        if (b < nb) C.nnz_lo[b] = carry_s + pre;
         __syncthreads();
         if (threadIdx.x == 0) carry_s += tot;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        C.nnz_lo[C.n_batches] = carry_s;
+        C.nnz_lo[nb] = carry_s;
         C.sc->nnz = carry_s;
         if (carry_s > C.max_nnz) set_error(C.sc, kErrNoMem, -1, carry_s, C.max_nnz);
     }
@@ -93,9 +109,11 @@ __device__ __forceinline__ int batch_of(const int64_t* lo, int nb, int64_t j) {
 // Inserts and deletes: offsets, timestamps, graph of each element; delete
 // IDs translated to global IDs.
 __global__ void k_gather(Store S, Call C, const int64_t* b_ins_lo, const int64_t* b_del_lo) {
-    int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j < C.n_ins) {
-        int b = batch_of(b_ins_lo, C.n_batches, j);
+    const int64_t ni = nins(C), nd = ndel(C);
+    const int nb = nbat(C);
+    ESC_FOR_THREADS(j, ni + nd) {
+    if (j < ni) {
+        int b = batch_of(b_ins_lo, nb, j);
         const BatchIn& B = C.batches[b];
         int64_t i = j - b_ins_lo[b];
         int64_t o0 = B.off[i], o1 = B.off[i + 1];
@@ -103,12 +121,12 @@ __global__ void k_gather(Store S, Call C, const int64_t* b_ins_lo, const int64_t
         if (n <= 0) set_error(C.sc, n < 0 ? kErrInvalid : kErrInvalid, b, i, n);
         else if (n > kMaxCard) set_error(C.sc, kErrUnsupported, b, i, n);
         C.ins_off[j] = C.nnz_lo[b] + o0;
-        if (j == C.n_ins - 1) C.ins_off[C.n_ins] = C.nnz_lo[b] + o1;
+        if (j == ni - 1) C.ins_off[ni] = C.nnz_lo[b] + o1;
         C.ts[j] = B.ts ? B.ts[i] : 0;
         C.ins_g[j] = B.graph;
-    } else if (j < C.n_ins + C.n_del) {
-        int64_t d = j - C.n_ins;
-        int b = batch_of(b_del_lo, C.n_batches, d);
+    } else {
+        int64_t d = j - ni;
+        int b = batch_of(b_del_lo, nb, d);
         const BatchIn& B = C.batches[b];
         int64_t i = d - b_del_lo[b];
         int32_t h = B.del[i];
@@ -121,6 +139,7 @@ __global__ void k_gather(Store S, Call C, const int64_t* b_ins_lo, const int64_t
         }
         C.del_g[d] = g;
     }
+    }
 }
 
 // Members, translated to global vertex IDs and range-checked.
@@ -129,7 +148,7 @@ __global__ void k_gather_mem(Store S, Call C) {
     if (n > C.max_nnz) n = C.max_nnz;
     for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
          p += int64_t(gridDim.x) * blockDim.x) {
-        int b = batch_of(C.nnz_lo, C.n_batches, p);
+        int b = batch_of(C.nnz_lo, nbat(C), p);
         const BatchIn& B = C.batches[b];
         int32_t v = B.mem[p - C.nnz_lo[b]];
         int g = B.graph;
@@ -151,14 +170,13 @@ __global__ void k_latch(Scalars* sc, int first) {
 // differs from its left neighbour.  Longer lists go to the block sorter.
 __global__ void k_sort_small(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = lane_id();
-    if (j >= C.n_ins) return;
+    const int lane = lane_id();
+    ESC_FOR_WARPS(j, nins(C)) {
     int64_t p0 = C.ins_off[j];
     int n = int(C.ins_off[j + 1] - p0);
     if (n > 32) {
         if (lane == 0) C.big[atomicAdd(&C.sc->n_big, 1)] = int32_t(j);
-        return;
+        continue;
     }
     int32_t x = lane < n ? C.raw[p0 + lane] : 0x7fffffff;
 #pragma unroll
@@ -179,6 +197,7 @@ __global__ void k_sort_small(Store S, Call C) {
         int k = __popc(bal);
         C.card[j] = k;
         atomicAdd(&C.sc->need_h[slab_class(k)], 1);
+    }
     }
 }
 
@@ -236,28 +255,27 @@ __global__ void __launch_bounds__(kSortNT) k_sort_big(Store S, Call C) {
 // Deletes: live and distinct; mark them; count the slab classes they free.
 __global__ void k_del_check(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (d >= C.n_del) return;
-    int32_t h = C.del[d];
-    if (!bit_test(S.live, h)) {
-        set_error(C.sc, kErrNotFound, -1, d, h - S.ebase[C.del_g[d]]);
-        return;
+    ESC_FOR_THREADS(d, ndel(C)) {
+        int32_t h = C.del[d];
+        if (!bit_test(S.live, h)) {
+            set_error(C.sc, kErrNotFound, -1, d, h - S.ebase[C.del_g[d]]);
+            continue;
+        }
+        uint32_t old = atomicOr(&S.delb[h >> 5], 1u << (h & 31));
+        if (old & (1u << (h & 31))) {
+            set_error(C.sc, kErrInvalid, -1, d, h - S.ebase[C.del_g[d]]);
+            continue;
+        }
+        atomicAdd(&C.sc->freed_h[slab_class(S.h_card[h])], 1);
     }
-    uint32_t old = atomicOr(&S.delb[h >> 5], 1u << (h & 31));
-    if (old & (1u << (h & 31))) {
-        set_error(C.sc, kErrInvalid, -1, d, h - S.ebase[C.del_g[d]]);
-        return;
-    }
-    atomicAdd(&C.sc->freed_h[slab_class(S.h_card[h])], 1);
 }
 
 // Per-vertex delete counts from the deleted hyperedges' member lists, and the
 // largest neighbour-entry count sum(deg) of a deleted hyperedge.
 __global__ void k_touch_del(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t d = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = lane_id();
-    if (d >= C.n_del) return;
+    const int lane = lane_id();
+    ESC_FOR_WARPS(d, ndel(C)) {
     int32_t h = C.del[d];
     int k = bit_test(S.live, h) ? S.h_card[h] : 0;
     const int32_t* m = S.hp.arena + S.h_off[h];
@@ -271,21 +289,22 @@ __global__ void k_touch_del(Store S, Call C) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
     if (lane == 0) atomicMax(&C.sc->max_u, int(u > 0x7fffffff ? 0x7fffffff : u));
+    }
 }
 
 // Per-vertex insert counts; every inserted member gets its place in the run
 // of IDs appended to its vertex's v2h list.
 __global__ void k_touch_ins(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = lane_id();
-    if (j >= C.n_ins) return;
-    int64_t p0 = C.ins_off[j];
-    int k = C.card[j];
-    for (int t = lane; t < k; t += 32) {
-        int32_t v = C.sorted[p0 + t];
-        C.slot[p0 + t] = atomicAdd(&S.v_nins[v], 1);
-        touch(S, C, v);
+    const int lane = lane_id();
+    ESC_FOR_WARPS(j, nins(C)) {
+        int64_t p0 = C.ins_off[j];
+        int k = C.card[j];
+        for (int t = lane; t < k; t += 32) {
+            int32_t v = C.sorted[p0 + t];
+            C.slot[p0 + t] = atomicAdd(&S.v_nins[v], 1);
+            touch(S, C, v);
+        }
     }
 }
 
@@ -309,9 +328,8 @@ __global__ void k_vplan(Store S, Call C) {
 // Largest neighbour-entry count of an inserted hyperedge on the new graph.
 __global__ void k_ins_u(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = lane_id();
-    if (j >= C.n_ins) return;
+    const int lane = lane_id();
+    ESC_FOR_WARPS(j, nins(C)) {
     int64_t p0 = C.ins_off[j];
     int k = C.card[j];
     long long u = 0;
@@ -322,6 +340,7 @@ __global__ void k_ins_u(Store S, Call C) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
     if (lane == 0) atomicMax(&C.sc->max_u, int(u > 0x7fffffff ? 0x7fffffff : u));
+    }
 }
 
 // Capacities: slab arenas (exact demand per class after reuse of free
@@ -341,7 +360,7 @@ __global__ void k_check(Store S, Call C, int64_t max_u) {
         if (short_by > 0) bump += short_by * slab_size(c);
     }
     if (*S.vp.tail + bump > S.vp.cap) set_error(sc, kErrNoMem, -3, *S.vp.tail + bump, S.vp.cap);
-    for (int b = 0; b < C.n_batches; ++b) {
+    for (int b = 0; b < nbat(C); ++b) {
         const BatchIn& B = C.batches[b];
         int g = B.graph;
         long long freeids = S.hw[g] - S.n_live[g] + B.n_del;
@@ -357,13 +376,13 @@ __global__ void k_check(Store S, Call C, int64_t max_u) {
 
 __global__ void k_hdel(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t d = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (d >= C.n_del) return;
-    int32_t h = C.del[d];
-    pool_free(S.hp, slab_class(S.h_card[h]), S.h_off[h]);
-    atomicAnd(&S.live[h >> 5], ~(1u << (h & 31)));
-    S.h_card[h] = 0;
-    atomicAdd(reinterpret_cast<unsigned long long*>(&S.n_live[C.del_g[d]]), ~0ull);
+    ESC_FOR_THREADS(d, ndel(C)) {
+        int32_t h = C.del[d];
+        pool_free(S.hp, slab_class(S.h_card[h]), S.h_off[h]);
+        atomicAnd(&S.live[h >> 5], ~(1u << (h & 31)));
+        S.h_card[h] = 0;
+        atomicAdd(reinterpret_cast<unsigned long long*>(&S.n_live[C.del_g[d]]), ~0ull);
+    }
 }
 
 // ID rule: the j-th insert of a graph takes the j-th smallest free ID below
@@ -374,9 +393,10 @@ __global__ void __launch_bounds__(kSelNT) k_select(Store S, Call C) {
     __shared__ int warp_tmp[32];
     __shared__ long long carry_s;
     if (C.sc->gate) return;
-    const BatchIn& B = C.batches[blockIdx.x];
+    for (int bi = blockIdx.x; bi < nbat(C); bi += gridDim.x) {
+    const BatchIn& B = C.batches[bi];
     int64_t n = B.n_ins;
-    if (n == 0) return;
+    if (n == 0) continue;
     int g = B.graph;
     int64_t eb = S.ebase[g], hwg = S.hw[g];
     int64_t nwords = (hwg + 31) >> 5;
@@ -407,20 +427,22 @@ __global__ void __launch_bounds__(kSelNT) k_select(Store S, Call C) {
     int64_t F = carry_s < n ? carry_s : n;
     for (int64_t r = F + threadIdx.x; r < n; r += kSelNT) C.ids[B.ins_lo + r] = int32_t(eb + hwg + (r - F));
     if (threadIdx.x == 0) S.hw[g] = hwg + (n - F);
+    __syncthreads();
+    }
 }
 
 __global__ void k_hins(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (j >= C.n_ins) return;
-    int32_t id = C.ids[j];
-    int k = C.card[j];
-    S.h_off[id] = pool_alloc(S.hp, slab_class(k));
-    S.h_card[id] = k;
-    S.h_ts[id] = C.ts[j];
-    atomicOr(&S.live[id >> 5], 1u << (id & 31));
-    atomicOr(&S.insb[id >> 5], 1u << (id & 31));
-    atomicAdd(reinterpret_cast<unsigned long long*>(&S.n_live[C.ins_g[j]]), 1ull);
+    ESC_FOR_THREADS(j, nins(C)) {
+        int32_t id = C.ids[j];
+        int k = C.card[j];
+        S.h_off[id] = pool_alloc(S.hp, slab_class(k));
+        S.h_card[id] = k;
+        S.h_ts[id] = C.ts[j];
+        atomicOr(&S.live[id >> 5], 1u << (id & 31));
+        atomicOr(&S.insb[id >> 5], 1u << (id & 31));
+        atomicAdd(reinterpret_cast<unsigned long long*>(&S.n_live[C.ins_g[j]]), 1ull);
+    }
 }
 
 __global__ void k_valloc(Store S, Call C) {
@@ -481,17 +503,17 @@ __global__ void k_vfilter(Store S, Call C) {
 // ID to the v2h list of each member.
 __global__ void k_ins_write(Store S, Call C) {
     if (C.sc->gate) return;
-    int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = lane_id();
-    if (j >= C.n_ins) return;
-    int32_t id = C.ids[j];
-    int64_t p0 = C.ins_off[j];
-    int64_t hoff = S.h_off[id];
-    int k = C.card[j];
-    for (int t = lane; t < k; t += 32) {
-        int32_t v = C.sorted[p0 + t];
-        S.hp.arena[hoff + t] = v;
-        S.vp.arena[S.v_off[v] + S.v_base[v] + C.slot[p0 + t]] = id;
+    const int lane = lane_id();
+    ESC_FOR_WARPS(j, nins(C)) {
+        int32_t id = C.ids[j];
+        int64_t p0 = C.ins_off[j];
+        int64_t hoff = S.h_off[id];
+        int k = C.card[j];
+        for (int t = lane; t < k; t += 32) {
+            int32_t v = C.sorted[p0 + t];
+            S.hp.arena[hoff + t] = v;
+            S.vp.arena[S.v_off[v] + S.v_base[v] + C.slot[p0 + t]] = id;
+        }
     }
 }
 
@@ -510,16 +532,17 @@ __global__ void k_vfree(Store S, Call C) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_fold_counts(Store S, Call C) {
-    const BatchIn& B = C.batches[blockIdx.x];
-    int g = B.graph;
-    uint64_t* cur = S.counts + int64_t(g) * kCStride;
-    uint64_t* dd = S.dcounts + int64_t(g) * kCStride;
-    uint64_t* di = S.dcounts + (int64_t(S.n_graphs) + g) * kCStride;
-    bool ok = C.sc->gate == 0;
-    for (int k = threadIdx.x; k < kCStride; k += blockDim.x) {
-        if (ok) cur[k] += di[k] - dd[k];
-        dd[k] = 0;
-        di[k] = 0;
+    const bool ok = C.sc->gate == 0;
+    for (int bi = blockIdx.x; bi < nbat(C); bi += gridDim.x) {
+        const int g = C.batches[bi].graph;
+        uint64_t* cur = S.counts + int64_t(g) * kCStride;
+        uint64_t* dd = S.dcounts + int64_t(g) * kCStride;
+        uint64_t* di = S.dcounts + (int64_t(S.n_graphs) + g) * kCStride;
+        for (int k = threadIdx.x; k < kCStride; k += blockDim.x) {
+            if (ok) cur[k] += di[k] - dd[k];
+            dd[k] = 0;
+            di[k] = 0;
+        }
     }
 }
 
@@ -529,7 +552,7 @@ __global__ void k_cleanup(Store S, Call C) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     int64_t stride = int64_t(gridDim.x) * blockDim.x;
     if (ran) {
-        for (int64_t d = i; d < C.n_del; d += stride) {
+        for (int64_t d = i; d < ndel(C); d += stride) {
             int32_t h = C.del[d];
             if (h >= 0) atomicAnd(&S.delb[h >> 5], ~(1u << (h & 31)));
         }
@@ -542,7 +565,7 @@ __global__ void k_cleanup(Store S, Call C) {
         }
     }
     if (ok) {
-        for (int64_t j = i; j < C.n_ins; j += stride) {
+        for (int64_t j = i; j < nins(C); j += stride) {
             int32_t id = C.ids[j];
             atomicAnd(&S.insb[id >> 5], ~(1u << (id & 31)));
             C.out_local[j] = int32_t(id - S.ebase[C.ins_g[j]]);
@@ -567,54 +590,70 @@ inline unsigned grid_for(int64_t n, int nt) {
         if (e_ != cudaSuccess) return e_;   \
     } while (0)
 
+// grids: one thread or one warp per element, at most 16 blocks per SM (the
+// kernels stride over what is left)
+static unsigned g_thr(int64_t n, int sm) { return std::min<unsigned>(grid_for(n, kBlk), unsigned(sm) * 16u); }
+static unsigned g_warp(int64_t n, int sm) { return std::min<unsigned>(grid_for(n * 32, kBlk), unsigned(sm) * 16u); }
+
+void store_prepare() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxCard * sizeof(int32_t)));
+    done = true;
+}
+
 cudaError_t store_ingest(const Store& S, const Call& C, const int64_t* b_ins_lo, const int64_t* b_del_lo,
                          int64_t max_u, int sm_count, cudaStream_t st, LaunchCounter& lc) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(kMaxCard * sizeof(int32_t)));
-        attr_done = true;
-    }
+    store_prepare();
+    const int64_t gi = C.grid_ins, gd = C.grid_del;
+    const bool any_i = C.fixed || gi > 0, any_d = C.fixed || gd > 0;
     ESC_LAUNCH(lc, k_plan<<<1, 1024, 0, st>>>(C));
-    if (C.n_ins + C.n_del > 0)
-        ESC_LAUNCH(lc, k_gather<<<grid_for(C.n_ins + C.n_del, kBlk), kBlk, 0, st>>>(S, C, b_ins_lo, b_del_lo));
-    if (C.n_ins > 0) ESC_LAUNCH(lc, k_gather_mem<<<sm_count * 8, kBlk, 0, st>>>(S, C));
+    if (any_i || any_d)
+        ESC_LAUNCH(lc, k_gather<<<g_thr(gi + gd, sm_count), kBlk, 0, st>>>(S, C, b_ins_lo, b_del_lo));
+    if (any_i) ESC_LAUNCH(lc, k_gather_mem<<<sm_count * 8, kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_latch<<<1, 1, 0, st>>>(C.sc, 1));
-    if (C.n_ins > 0) {
-        ESC_LAUNCH(lc, k_sort_small<<<grid_for(C.n_ins * 32, kBlk), kBlk, 0, st>>>(S, C));
+    if (any_i) {
+        ESC_LAUNCH(lc, k_sort_small<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));
         ESC_LAUNCH(lc, k_sort_big<<<sm_count * 2, kSortNT, kMaxCard * sizeof(int32_t), st>>>(S, C));
     }
-    if (C.n_del > 0) {
-        ESC_LAUNCH(lc, k_del_check<<<grid_for(C.n_del, kBlk), kBlk, 0, st>>>(S, C));
-        ESC_LAUNCH(lc, k_touch_del<<<grid_for(C.n_del * 32, kBlk), kBlk, 0, st>>>(S, C));
+    if (any_d) {
+        ESC_LAUNCH(lc, k_del_check<<<g_thr(gd, sm_count), kBlk, 0, st>>>(S, C));
+        ESC_LAUNCH(lc, k_touch_del<<<g_warp(gd, sm_count), kBlk, 0, st>>>(S, C));
     }
-    if (C.n_ins > 0) ESC_LAUNCH(lc, k_touch_ins<<<grid_for(C.n_ins * 32, kBlk), kBlk, 0, st>>>(S, C));
+    if (any_i) ESC_LAUNCH(lc, k_touch_ins<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_vplan<<<sm_count * 4, kBlk, 0, st>>>(S, C));
-    if (C.n_ins > 0) ESC_LAUNCH(lc, k_ins_u<<<grid_for(C.n_ins * 32, kBlk), kBlk, 0, st>>>(S, C));
+    if (any_i) ESC_LAUNCH(lc, k_ins_u<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_check<<<1, 32, 0, st>>>(S, C, max_u));
     ESC_LAUNCH(lc, k_latch<<<1, 1, 0, st>>>(C.sc, 0));
     return cudaSuccess;
 }
 
-cudaError_t store_delete(const Store& S, const Call& C, cudaStream_t st, LaunchCounter& lc) {
-    if (C.n_del > 0) ESC_LAUNCH(lc, k_hdel<<<grid_for(C.n_del, kBlk), kBlk, 0, st>>>(S, C));
+cudaError_t store_delete(const Store& S, const Call& C, int sm_count, cudaStream_t st, LaunchCounter& lc) {
+    if (C.fixed || C.grid_del > 0) ESC_LAUNCH(lc, k_hdel<<<g_thr(C.grid_del, sm_count), kBlk, 0, st>>>(S, C));
     return cudaSuccess;
 }
 
 cudaError_t store_insert(const Store& S, const Call& C, int sm_count, cudaStream_t st, LaunchCounter& lc) {
-    if (C.n_ins > 0) {
-        ESC_LAUNCH(lc, k_select<<<C.n_batches, kSelNT, 0, st>>>(S, C));
-        ESC_LAUNCH(lc, k_hins<<<grid_for(C.n_ins, kBlk), kBlk, 0, st>>>(S, C));
+    const int64_t gi = C.grid_ins;
+    const bool any_i = C.fixed || gi > 0;
+    if (any_i) {
+        ESC_LAUNCH(lc, k_select<<<unsigned(std::max<int64_t>(C.grid_batches, 1)), kSelNT, 0, st>>>(S, C));
+        ESC_LAUNCH(lc, k_hins<<<g_thr(gi, sm_count), kBlk, 0, st>>>(S, C));
     }
     ESC_LAUNCH(lc, k_valloc<<<sm_count, kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_vfilter<<<sm_count * 8, kBlk, 0, st>>>(S, C));
-    if (C.n_ins > 0) ESC_LAUNCH(lc, k_ins_write<<<grid_for(C.n_ins * 32, kBlk), kBlk, 0, st>>>(S, C));
+    if (any_i) ESC_LAUNCH(lc, k_ins_write<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_vfree<<<sm_count, kBlk, 0, st>>>(S, C));
     return cudaSuccess;
 }
 
+cudaError_t store_latch(const Call& C, cudaStream_t st, LaunchCounter& lc) {
+    ESC_LAUNCH(lc, k_latch<<<1, 1, 0, st>>>(C.sc, 0));
+    return cudaSuccess;
+}
+
 cudaError_t store_finish(const Store& S, const Call& C, int sm_count, cudaStream_t st, LaunchCounter& lc) {
-    ESC_LAUNCH(lc, k_fold_counts<<<C.n_batches, 160, 0, st>>>(S, C));
+    ESC_LAUNCH(lc, k_fold_counts<<<unsigned(std::max<int64_t>(C.grid_batches, 1)), 160, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_cleanup<<<sm_count * 4, kBlk, 0, st>>>(S, C));
     return cudaSuccess;
 }

@@ -14,9 +14,14 @@ struct LaunchCounter {
 // store.cu
 cudaError_t store_ingest(const Store& S, const Call& C, const int64_t* b_ins_lo, const int64_t* b_del_lo,
                          int64_t max_u, int sm_count, cudaStream_t st, LaunchCounter& lc);
-cudaError_t store_delete(const Store& S, const Call& C, cudaStream_t st, LaunchCounter& lc);
+cudaError_t store_delete(const Store& S, const Call& C, int sm_count, cudaStream_t st, LaunchCounter& lc);
 cudaError_t store_insert(const Store& S, const Call& C, int sm_count, cudaStream_t st, LaunchCounter& lc);
 cudaError_t store_finish(const Store& S, const Call& C, int sm_count, cudaStream_t st, LaunchCounter& lc);
+// kernel attributes, set once before any launch (and before a capture)
+void store_prepare();
+void count_prepare();
+// latch the status into the gate (later kernels then change nothing)
+cudaError_t store_latch(const Call& C, cudaStream_t st, LaunchCounter& lc);
 
 // count.cu
 struct CountScratch {
@@ -119,5 +124,18 @@ cudaError_t upload_tables(cudaStream_t st);
 cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                          const uint32_t* chg_bits, int64_t lo, int64_t hi, int side, uint64_t* dcounts_side,
                          const CountScratch& cs, int64_t max_u, cudaStream_t st, LaunchCounter& lc);
+
+// For the fixed sequence, before the store changes: the retry status if the
+// inserted side will need more than `runs` count runs.
+cudaError_t count_precheck_fixed(const Store& S, const Call& C, const CountScratch& cs, int64_t max_u, int runs,
+                                 cudaStream_t st, LaunchCounter& lc);
+
+// The same as a fixed launch sequence (every kernel reads the side's size
+// n_side and its run ranges on the device, so the sequence can be captured
+// once and replayed): `runs` count runs per side; if the lists need more, the
+// call fails with the internal retry status and changes nothing.
+cudaError_t count_launch_fixed(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
+                               const uint32_t* chg_bits, const int64_t* n_side, int side, uint64_t* dcounts_side,
+                               const CountScratch& cs, int64_t max_u, int runs, cudaStream_t st, LaunchCounter& lc);
 
 }  // namespace esc

@@ -37,6 +37,7 @@ EXPORTED = [
     "esc_group_last_error", "esc_group_set_profiling", "esc_group_last_stats", "esc_group_launch_count",
     "esc_group_bytes", "esc_server_create", "esc_server_submit", "esc_server_wait", "esc_server_drain",
     "esc_server_triads", "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
+    "esc_set_graph_launch", "esc_group_set_graph_launch",
     "esc_version", "esc_count_static_noalloc",
 ]
 
@@ -130,6 +131,8 @@ def load(path: str = LIB_PATH):
     L.esc_server_get_stats.argtypes = [vp, C.POINTER(esc_server_stats)]
     L.esc_server_destroy.argtypes = [vp]
     L.esc_autotune.argtypes = [vp, i64, vp, i32, C.POINTER(esc_tune_result)]
+    L.esc_set_graph_launch.argtypes = [vp, i32]
+    L.esc_group_set_graph_launch.argtypes = [vp, i32]
     L.esc_group_autotune.argtypes = [vp, i32, i64, vp, i32, C.POINTER(esc_tune_result)]
     L.esc_version.restype = C.c_char_p
     L.esc_count_static_noalloc.argtypes = [i32, i64, vp, vp, vp, u32, i64, vp, vp]
@@ -139,7 +142,8 @@ def load(path: str = LIB_PATH):
                  "esc_group_create", "esc_group_apply", "esc_group_triads", "esc_group_destroy",
                  "esc_group_set_profiling", "esc_group_last_stats", "esc_group_bytes", "esc_server_create",
                  "esc_server_submit", "esc_server_wait", "esc_server_drain", "esc_server_triads",
-                 "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune"):
+                 "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
+                 "esc_set_graph_launch", "esc_group_set_graph_launch"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -363,6 +367,16 @@ def esc_autotune(h: int, ids, reps: int = 2) -> dict:
     return _tune_dict(r)
 
 
+def esc_set_graph_launch(h: int, on: bool = True) -> None:
+    L = load()
+    _check(L.esc_set_graph_launch(h, 1 if on else 0), L.esc_last_error, h)
+
+
+def esc_group_set_graph_launch(grp: int, on: bool = True) -> None:
+    L = load()
+    _check(L.esc_group_set_graph_launch(grp, 1 if on else 0), L.esc_group_last_error, grp)
+
+
 def esc_group_autotune(grp: int, graph: int, ids, reps: int = 2) -> dict:
     L = load()
     p, keep = _ptr(ids, np.int32)
@@ -533,6 +547,9 @@ class Graph:
 
     def autotune(self, ids, reps: int = 2) -> dict:
         return esc_autotune(self.h, ids, reps)
+
+    def set_graph_launch(self, on: bool = True) -> None:
+        esc_set_graph_launch(self.h, on)
 
     def close(self) -> None:
         if self.h:
