@@ -426,6 +426,73 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# horizontal updates: vertex sets of live hyperedges change in place
+# ---------------------------------------------------------------------------
+
+def run_horizontal(args):
+    """The 1M-vertex uniform workload; each step changes the vertex sets of
+    --batch / 2 distinct live hyperedges (about 30% of each one's members
+    dropped, 0-3 uniform vertices added), which keep their IDs (Sec. III-B's
+    incident-vertex insertions and deletions).  Hyperedge + vertex families."""
+    import torch
+    from paper_2512_21009_gb300 import escher as E
+    torch.cuda.set_device(0)
+    s = gen.large(seed=args.seed, membership="uniform", scale=args.scale, n_batches=1, batch_updates=2)
+    init = s.initial
+    n_up = max(1, args.batch // 2)
+    steps = args.warmup + args.steps
+    g = E.Graph(s.n_vertices, init.offsets, init.members, init.timestamps,
+                capacity_hyperedges=init.n + 64, capacity_incidences=int(init.nnz * 1.6) + 4096,
+                max_batch_hyperedges=max(2 * n_up, min(init.n, 100_000)),
+                max_batch_incidences=max(4 * n_up * 16, 1 << 22), families=3)
+    rng = np.random.default_rng(args.seed + 5)
+    off0, mem0 = init.offsets, init.members
+    cur = [mem0[off0[i]:off0[i + 1]] for i in range(init.n)]   # client copy of the vertex sets
+    batches = []
+    for k in range(steps):
+        ids = np.sort(rng.choice(init.n, size=min(n_up, init.n), replace=False)).astype(np.int32)
+        sets = []
+        for h in ids:
+            c = cur[h]
+            keep = c[rng.random(c.size) < 0.7]
+            new = np.unique(np.concatenate([keep, rng.integers(0, s.n_vertices, size=int(rng.integers(0, 4)))]))
+            if new.size == 0:
+                new = c[:1]
+            cur[h] = new.astype(np.int32)
+            sets.append(cur[h])
+        off = np.zeros(len(sets) + 1, np.int64)
+        off[1:] = np.cumsum([x.size for x in sets])
+        batches.append((torch.from_numpy(ids).cuda(), torch.from_numpy(off).cuda(),
+                        torch.from_numpy(np.concatenate(sets).astype(np.int32)).cuda()))
+    g.set_profiling(True)
+    for k in range(args.warmup):
+        E.esc_update_members(g.h, *batches[k])
+    torch.cuda.synchronize()
+    lat, cnt_ms = [], []
+    t0 = time.perf_counter()
+    for k in range(args.warmup, steps):
+        t1 = time.perf_counter()
+        E.esc_update_members(g.h, *batches[k])
+        lat.append((time.perf_counter() - t1) * 1e3)
+        st = g.stats()
+        cnt_ms.append(st["ms_count_del"] + st["ms_count_ins"])
+    el = time.perf_counter() - t0
+    g.close()
+    print(json.dumps({
+        "metric": METRIC, "value": n_up * args.steps / el, "unit": "hyperedge updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts",
+        "data": "synthetic",
+        "config": {"workload": (f"horizontal updates on the uniform large graph ({s.n_vertices:,} vertices, "
+                                f"{init.n:,} hyperedges): {n_up:,} distinct hyperedges per batch get a new vertex "
+                                "set (~30% of members dropped, 0-3 vertices added), IDs kept"),
+                   "families": "hyperedge (30) + incident-vertex (3)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "count_ms_per_step": sum(cnt_ms) / len(cnt_ms),
+    }))
+
+
+# ---------------------------------------------------------------------------
 # batched form: many hypergraphs, one call vs one call per graph
 # ---------------------------------------------------------------------------
 
@@ -827,7 +894,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_uniform",
-                    choices=["large_uniform", "tiny", "batched", "temporal", "serving"])
+                    choices=["large_uniform", "tiny", "batched", "temporal", "serving", "horizontal"])
     ap.add_argument("--graphs", type=int, default=None)
     ap.add_argument("--rate", type=float, default=5e4, help="serving: offered requests/s")
     ap.add_argument("--duration", type=float, default=8.0, help="serving: seconds per run")
@@ -851,6 +918,8 @@ def main():
         run_temporal(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "horizontal":
+        run_horizontal(args)
     else:
         run_ours(args)
 

@@ -140,6 +140,18 @@ esc_status esc_apply_batch(esc_graph* g, int64_t n_ins, const int64_t* ins_offse
                            const int32_t* ins_members, const int64_t* ins_timestamps,
                            int64_t n_del, const int32_t* del_ids, int32_t* out_ins_ids);
 
+/* Horizontal update (Sec. III-B: incident vertices inserted into and deleted
+ * from live hyperedges): live hyperedge ids[j] gets the vertex set
+ * members[offsets[j] .. offsets[j+1]) (offsets int64[n+1], offsets[0] == 0;
+ * repeated members collapse) and keeps its ID and timestamp.  All counts are
+ * refreshed: every triad holding an updated hyperedge leaves its old class
+ * and enters its new one.  ids: int32[n], distinct; pointers host or device.
+ * Errors: INVALID_ARG (repeated ID, malformed sets), NOT_FOUND (an ID not
+ * live), OUT_OF_MEMORY / UNSUPPORTED as esc_apply_batch; a failed call
+ * changes nothing. */
+esc_status esc_update_members(esc_graph* g, int64_t n, const int32_t* ids, const int64_t* offsets,
+                              const int32_t* members);
+
 /* Copy the current counts of one family into out (uint64[n_out]; n_out must be
  * at least 30, 3 or 96).  window is the temporal window and must equal the
  * configured delta for ESC_TRIAD_TEMPORAL; it is ignored otherwise.
@@ -260,6 +272,10 @@ esc_status esc_group_bytes(const esc_config* shared_cfg, int32_t n_graphs, const
  * when every store and count is updated.  Errors as esc_apply_batch; the
  * failing batch is named by esc_group_last_error. */
 esc_status esc_group_apply(esc_group* grp, int32_t n, const esc_batch* batches);
+
+/* esc_update_members for graph `graph` of the group (that graph's IDs). */
+esc_status esc_group_update_members(esc_group* grp, int32_t graph, int64_t n, const int32_t* ids,
+                                    const int64_t* offsets, const int32_t* members);
 
 esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window,
                             uint64_t* out, int32_t n_out);

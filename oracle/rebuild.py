@@ -14,6 +14,9 @@ Semantics followed (paper Section III-B, "Operations on ESCHER"):
   hyperedge, including IDs deleted earlier in the same batch.  Once those run
   out, new IDs are handed out in increasing order from the high-water mark.
   Initial hyperedges therefore get IDs 0..n-1 in input order.
+* Horizontal updates (Section III-B: incident vertices inserted into or
+  deleted from live hyperedges): a live hyperedge gets a new vertex set and
+  keeps its ID and its timestamp.
 """
 from __future__ import annotations
 
@@ -92,6 +95,29 @@ class OracleHypergraph:
                 self.ts.append(int(ins_ts[j]))
             out[j] = hid
         return out
+
+    def update_members(self, ids, offsets, members) -> None:
+        """Give each live hyperedge ids[j] the vertex set members[offsets[j]:
+        offsets[j+1]] (repeats collapse); IDs and timestamps are kept."""
+        ids = np.asarray(ids, dtype=np.int64)
+        offsets = np.asarray(offsets, dtype=np.int64)
+        members = np.asarray(members, dtype=np.int64)
+        if offsets.shape[0] != ids.size + 1 or (ids.size and offsets[0] != 0) or np.any(np.diff(offsets) < 0):
+            raise ValueError("bad offsets")
+        if np.unique(ids).size != ids.size:
+            raise ValueError("duplicate hyperedge")
+        new_sets = []
+        for j, hid in enumerate(ids):
+            if self.edge(int(hid)) is None:
+                raise ValueError(f"update of non-live hyperedge {int(hid)}")
+            s = np.unique(members[offsets[j]:offsets[j + 1]])
+            if s.size == 0:
+                raise ValueError("empty hyperedge")
+            if s[0] < 0 or s[-1] >= self.n_vertices:
+                raise ValueError("vertex out of range")
+            new_sets.append(s.astype(np.int32))
+        for hid, s in zip(ids, new_sets):
+            self.members[int(hid)] = s
 
     # ------------------------------------------------------------------ views
     def csr(self):

@@ -70,6 +70,7 @@ struct Engine {
     int32_t* st_mem = nullptr;
     int64_t* st_ts = nullptr;
     int32_t* st_del = nullptr;
+    int32_t* st_pin = nullptr;
     CountScratch cs{};
     int64_t max_u = 0;
     // pinned host copies of host-pointer inputs, grown on demand, so that a
@@ -77,8 +78,8 @@ struct Engine {
     struct Pinned {
         void* p = nullptr;
         size_t bytes = 0;
-    } hs[4];
-    size_t hs_lo[4] = {};  // first element of hs[k] not yet copied in this call
+    } hs[5];
+    size_t hs_lo[5] = {};  // first element of hs[k] not yet copied in this call
     bool profiling = false;
     cudaEvent_t cev[32] = {};          // centre-kernel launch events (profiling)
     // calls as one replayed CUDA graph (a fixed launch sequence whose kernels
@@ -298,6 +299,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     ESC_CU(E->alloc(&E->st_mem, E->max_nnz), "alloc");
     ESC_CU(E->alloc(&E->st_ts, E->max_ins), "alloc");
     ESC_CU(E->alloc(&E->st_del, E->max_ins), "alloc");
+    ESC_CU(E->alloc(&E->st_pin, E->max_ins), "alloc");
     if (!dry) {
         ESC_CU(cudaMallocHost(&E->h_batches, sizeof(BatchIn) * G), "pinned");
         ESC_CU(cudaMallocHost(&E->h_lo, sizeof(int64_t) * 2 * (G + 1)), "pinned");
@@ -517,7 +519,8 @@ static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStr
     return store_finish(S, C, E->sm_count, st, lc);
 }
 
-static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
+// pins: per batch, the IDs its inserts keep (a horizontal update), or null
+static esc_status run_call(Engine* E, int n, const esc_batch* bs, const int32_t* const* pins = nullptr) {
     if (n == 0) return ESC_OK;
     if (n < 0 || n > E->G || !bs) return E->fail(ESC_ERR_INVALID_ARG, "bad batch list");
     std::vector<char> seen(E->G, 0);
@@ -529,7 +532,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
         if (x.n_ins < 0 || x.n_del < 0) return E->fail(ESC_ERR_INVALID_ARG, "negative count");
         if (x.n_ins > 0 && (!x.ins_offsets || !x.ins_members))
             return E->fail(ESC_ERR_INVALID_ARG, "missing insert arrays");
-        if (x.n_ins > 0 && (E->shared.families & kFamT) && !x.ins_timestamps)
+        if (x.n_ins > 0 && (E->shared.families & kFamT) && !x.ins_timestamps && !(pins && pins[b]))
             return E->fail(ESC_ERR_INVALID_ARG, "timestamps required by the temporal family");
         if (x.n_del > 0 && !x.del_ids) return E->fail(ESC_ERR_INVALID_ARG, "missing delete IDs");
         tot_ins += x.n_ins;
@@ -539,7 +542,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
         return E->fail(ESC_ERR_OUT_OF_MEMORY, "batch larger than max_batch_hyperedges");
     cudaStream_t st = E->st;
     // stage host inputs
-    size_t u_off = 0, u_mem = 0, u_ts = 0, u_del = 0;
+    size_t u_off = 0, u_mem = 0, u_ts = 0, u_del = 0, u_pin = 0;
     for (auto& lo : E->hs_lo) lo = 0;
     int64_t* bins = E->h_lo;
     int64_t* bdel = E->h_lo + (E->G + 1);
@@ -559,6 +562,10 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
         B.mem = nullptr;
         B.ts = nullptr;
         B.del = nullptr;
+        B.pin = nullptr;
+        if (x.n_ins > 0 && pins && pins[b])
+            if ((s = stage(E, pins[b], size_t(x.n_ins), E->st_pin, 4, u_pin, size_t(E->max_ins), &B.pin)) != ESC_OK)
+                return s;
         if (x.n_ins > 0) {
             bool off_dev = is_device_ptr(x.ins_offsets);
             if ((s = stage(E, x.ins_offsets, size_t(x.n_ins + 1), E->st_off, 0, u_off,
@@ -586,7 +593,8 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
     {
         esc_status s;
         if ((s = flush_staged(E, E->st_off, 0, u_off)) != ESC_OK || (s = flush_staged(E, E->st_mem, 1, u_mem)) != ESC_OK ||
-            (s = flush_staged(E, E->st_ts, 2, u_ts)) != ESC_OK || (s = flush_staged(E, E->st_del, 3, u_del)) != ESC_OK)
+            (s = flush_staged(E, E->st_ts, 2, u_ts)) != ESC_OK || (s = flush_staged(E, E->st_del, 3, u_del)) != ESC_OK ||
+            (s = flush_staged(E, E->st_pin, 4, u_pin)) != ESC_OK)
             return s;
     }
     ESC_CU(cudaMemcpyAsync(E->d_batches, E->h_batches, sizeof(BatchIn) * n, cudaMemcpyHostToDevice, st), "copy");
@@ -690,6 +698,38 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs) {
             memcpy(x.out_ins_ids, src, sizeof(int32_t) * x.n_ins);
     }
     return ESC_OK;
+}
+
+// Horizontal update (incident vertices inserted into / deleted from live
+// hyperedges): each hyperedge ids[j] of graph g gets a new vertex set and
+// keeps its ID and timestamp.  As a call: the old hyperedges are deleted and
+// the new sets inserted with their IDs kept, so both counts of Alg. 3 see the
+// change (triads holding an updated hyperedge leave their old class and
+// join their new one).
+static esc_status update_members(Engine* E, int32_t g, int64_t n, const int32_t* ids, const int64_t* offsets,
+                                 const int32_t* members) {
+    if (g < 0 || g >= E->G || n < 0 || (n > 0 && (!ids || !offsets || !members)))
+        return E->fail(ESC_ERR_INVALID_ARG, "bad update");
+    if (n == 0) return ESC_OK;
+    std::vector<int32_t> pin(static_cast<size_t>(n));
+    if (is_device_ptr(ids))
+        ESC_CU(cudaMemcpy(pin.data(), ids, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "ids");
+    else
+        memcpy(pin.data(), ids, sizeof(int32_t) * n);
+    std::vector<int32_t> del(pin);
+    std::sort(del.begin(), del.end());
+    for (size_t i = 1; i < del.size(); ++i)
+        if (del[i] == del[i - 1]) return E->fail(ESC_ERR_INVALID_ARG, "hyperedge " + std::to_string(del[i]) + " repeated");
+    esc_batch b{};
+    b.graph = g;
+    b.n_ins = n;
+    b.ins_offsets = offsets;
+    b.ins_members = members;
+    b.ins_timestamps = nullptr;
+    b.n_del = n;
+    b.del_ids = del.data();
+    const int32_t* pins[1] = {pin.data()};
+    return run_call(E, 1, &b, pins);
 }
 
 static esc_status read_counts(Engine* E, int32_t g, esc_triad_type type, int64_t window, uint64_t* out,
@@ -941,6 +981,12 @@ esc_status esc_group_apply(esc_group* grp, int32_t n, const esc_batch* batches) 
     return esc::run_call(grp->e, n, batches);
 }
 
+esc_status esc_group_update_members(esc_group* grp, int32_t graph, int64_t n, const int32_t* ids,
+                                    const int64_t* offsets, const int32_t* members) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::update_members(grp->e, graph, n, ids, offsets, members);
+}
+
 esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window, uint64_t* out,
                             int32_t n_out) {
     if (!grp) return ESC_ERR_INVALID_ARG;
@@ -1076,6 +1122,12 @@ esc_status esc_apply_batch(esc_graph* g, int64_t n_ins, const int64_t* ins_offse
     b.del_ids = del_ids;
     b.out_ins_ids = out_ins_ids;
     return esc::run_call(g->e, 1, &b);
+}
+
+esc_status esc_update_members(esc_graph* g, int64_t n, const int32_t* ids, const int64_t* offsets,
+                              const int32_t* members) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    return esc::update_members(g->e, 0, n, ids, offsets, members);
 }
 
 esc_status esc_triads(esc_graph* g, esc_triad_type type, int64_t window, uint64_t* out, int32_t n_out) {

@@ -129,6 +129,7 @@ struct BatchIn {
     const int32_t* mem;
     const int64_t* ts;
     const int32_t* del;
+    const int32_t* pin;      // [n_ins] IDs the inserts keep (a horizontal update), or null: the ID rule
     int64_t ins_lo, del_lo;  // position in the concatenated arrays
 };
 

@@ -124,6 +124,19 @@ __global__ void k_gather(Store S, Call C, const int64_t* b_ins_lo, const int64_t
         if (j == ni - 1) C.ins_off[ni] = C.nnz_lo[b] + o1;
         C.ts[j] = B.ts ? B.ts[i] : 0;
         C.ins_g[j] = B.graph;
+        if (B.pin) {
+            // a horizontal update: the hyperedge keeps its ID and, unless
+            // given one, its timestamp (read before anything changes)
+            const int32_t p = B.pin[i];
+            if (p < 0 || p >= S.ecap[B.graph]) {
+                set_error(C.sc, kErrNotFound, b, i, p);
+                C.ids[j] = -1;
+            } else {
+                const int64_t id = S.ebase[B.graph] + p;
+                C.ids[j] = int32_t(id);
+                if (!B.ts) C.ts[j] = S.h_ts[id];
+            }
+        }
     } else {
         int64_t d = j - ni;
         int b = batch_of(b_del_lo, nb, d);
@@ -362,6 +375,7 @@ __global__ void k_check(Store S, Call C, int64_t max_u) {
     if (*S.vp.tail + bump > S.vp.cap) set_error(sc, kErrNoMem, -3, *S.vp.tail + bump, S.vp.cap);
     for (int b = 0; b < nbat(C); ++b) {
         const BatchIn& B = C.batches[b];
+        if (B.pin) continue;  // kept IDs need no free ones
         int g = B.graph;
         long long freeids = S.hw[g] - S.n_live[g] + B.n_del;
         long long extra = B.n_ins - freeids;
@@ -396,7 +410,7 @@ __global__ void __launch_bounds__(kSelNT) k_select(Store S, Call C) {
     for (int bi = blockIdx.x; bi < nbat(C); bi += gridDim.x) {
     const BatchIn& B = C.batches[bi];
     int64_t n = B.n_ins;
-    if (n == 0) continue;
+    if (n == 0 || B.pin) continue;  // kept IDs were set by k_gather
     int g = B.graph;
     int64_t eb = S.ebase[g], hwg = S.hw[g];
     int64_t nwords = (hwg + 31) >> 5;

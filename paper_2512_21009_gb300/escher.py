@@ -37,7 +37,7 @@ EXPORTED = [
     "esc_group_last_error", "esc_group_set_profiling", "esc_group_last_stats", "esc_group_launch_count",
     "esc_group_bytes", "esc_server_create", "esc_server_submit", "esc_server_wait", "esc_server_drain",
     "esc_server_triads", "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
-    "esc_set_graph_launch", "esc_group_set_graph_launch",
+    "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members", "esc_group_update_members",
     "esc_version", "esc_count_static_noalloc",
 ]
 
@@ -132,6 +132,8 @@ def load(path: str = LIB_PATH):
     L.esc_server_destroy.argtypes = [vp]
     L.esc_autotune.argtypes = [vp, i64, vp, i32, C.POINTER(esc_tune_result)]
     L.esc_set_graph_launch.argtypes = [vp, i32]
+    L.esc_update_members.argtypes = [vp, i64, vp, vp, vp]
+    L.esc_group_update_members.argtypes = [vp, i32, i64, vp, vp, vp]
     L.esc_group_set_graph_launch.argtypes = [vp, i32]
     L.esc_group_autotune.argtypes = [vp, i32, i64, vp, i32, C.POINTER(esc_tune_result)]
     L.esc_version.restype = C.c_char_p
@@ -143,7 +145,8 @@ def load(path: str = LIB_PATH):
                  "esc_group_set_profiling", "esc_group_last_stats", "esc_group_bytes", "esc_server_create",
                  "esc_server_submit", "esc_server_wait", "esc_server_drain", "esc_server_triads",
                  "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
-                 "esc_set_graph_launch", "esc_group_set_graph_launch"):
+                 "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members",
+                 "esc_group_update_members"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -367,6 +370,24 @@ def esc_autotune(h: int, ids, reps: int = 2) -> dict:
     return _tune_dict(r)
 
 
+def esc_update_members(h: int, ids, offsets, members) -> None:
+    """Horizontal update: live hyperedge ids[j] gets the vertex set
+    members[offsets[j]:offsets[j+1]] and keeps its ID and timestamp."""
+    L = load()
+    pi, ki = _ptr(ids, np.int32)
+    po, ko = _ptr(offsets, np.int64)
+    pm, km = _ptr(members, np.int32)
+    _check(L.esc_update_members(h, len(ids), pi, po, pm), L.esc_last_error, h)
+
+
+def esc_group_update_members(grp: int, graph: int, ids, offsets, members) -> None:
+    L = load()
+    pi, ki = _ptr(ids, np.int32)
+    po, ko = _ptr(offsets, np.int64)
+    pm, km = _ptr(members, np.int32)
+    _check(L.esc_group_update_members(grp, int(graph), len(ids), pi, po, pm), L.esc_group_last_error, grp)
+
+
 def esc_set_graph_launch(h: int, on: bool = True) -> None:
     L = load()
     _check(L.esc_set_graph_launch(h, 1 if on else 0), L.esc_last_error, h)
@@ -550,6 +571,9 @@ class Graph:
 
     def set_graph_launch(self, on: bool = True) -> None:
         esc_set_graph_launch(self.h, on)
+
+    def update_members(self, ids, offsets, members) -> None:
+        esc_update_members(self.h, ids, offsets, members)
 
     def close(self) -> None:
         if self.h:

@@ -1,0 +1,44 @@
+"""Host-side logic that needs no GPU: the serving client's copy of the ID
+rule (bench.py) against the oracle's, and the seeded serving generators."""
+import numpy as np
+
+import gen
+from oracle import OracleHypergraph
+
+
+def test_client_id_model_follows_the_id_rule():
+    import bench
+    rng = np.random.default_rng(1)
+    nv, n0 = 50, 40
+    off = np.arange(0, 2 * n0 + 1, 2, dtype=np.int64)
+    mem = np.concatenate([np.sort(rng.choice(nv, 2, replace=False)) for _ in range(n0)]).astype(np.int32)
+    og = OracleHypergraph(nv, off, mem, np.zeros(n0, np.int64))
+    m = bench._IdModel(n0)
+    for step in range(300):
+        nd, ni = int(rng.integers(0, 8)), int(rng.integers(0, 10))
+        idx, d = m.pick(rng, nd)
+        edges = [np.sort(rng.choice(nv, 3, replace=False)) for _ in range(ni)]
+        io = np.zeros(ni + 1, np.int64)
+        io[1:] = np.cumsum([3] * ni)
+        im = np.concatenate(edges).astype(np.int32) if ni else np.zeros(0, np.int32)
+        want = og.apply_batch(io, im, np.zeros(ni, np.int64), np.sort(d).astype(np.int64))
+        got = m.commit(idx, d, ni)
+        assert np.array_equal(got, want), step
+        assert sorted(m.live[:m.n].tolist()) == og.live_ids().tolist()
+
+
+def test_serving_generators_are_seeded_and_shaped():
+    a = gen.resident_graphs(seed=5, n_graphs=6, e_hi=5e3)
+    b = gen.resident_graphs(seed=5, n_graphs=6, e_hi=5e3)
+    for x, y in zip(a.graphs, b.graphs):
+        assert np.array_equal(x.initial.members, y.initial.members)
+        e0 = x.initial.n
+        assert 1000 <= e0 <= 5000 and x.n_vertices == max(256, e0 // 2)
+        k = np.diff(x.initial.offsets)
+        assert k.min() >= 2 and k.max() <= 256
+        assert x.initial.members.max() < x.n_vertices
+    off, u = gen.insert_pool(6, 1000)
+    assert len(off) == 1001 and off[-1] == len(u)
+    assert u.dtype == np.float32 and 0.0 <= u.min() and u.max() < 1.0
+    t, g, s = gen.serving_arrivals(7, 10, 500, 100.0)
+    assert np.all(np.diff(t) > 0) and g.max() < 10 and s.min() >= 10 and s.max() <= 10000

@@ -437,3 +437,25 @@ def test_generator_is_deterministic_and_well_formed():
     # truncated Zipf(2): P(k=2) = 2^-2 / sum_{k=2}^{1000} k^-2
     p2 = 0.25 / sum(k ** -2.0 for k in range(2, 1001))
     assert abs((z == 2).mean() - p2) < 0.01
+
+
+def test_horizontal_update_counts_as_delete_and_insert():
+    """A horizontal update keeps the ID and timestamp; its static counts are
+    those of deleting the hyperedge and inserting the new set as a new one
+    (the classes do not depend on labels), and updating back restores the
+    counts exactly."""
+    s = gen.random_small(91, 40, 30, 2, 5)
+    init = s.initial
+    a = OracleHypergraph(s.n_vertices, init.offsets, init.members, init.timestamps)
+    b = OracleHypergraph(s.n_vertices, init.offsets, init.members, init.timestamps)
+    before = O.counts(a, 3, 0)
+    old = a.edge(4).copy()
+    new = np.array([0, 1, 2, 39], np.int32)
+    a.update_members(np.array([4]), np.array([0, 4]), new)
+    assert np.array_equal(a.edge(4), new) and a.ts[4] == init.timestamps[4]
+    b.apply_batch(np.array([0, 4]), new, np.array([init.timestamps[4]]), np.array([4]))
+    ca, cb = O.counts(a, 3, 0), O.counts(b, 3, 0)
+    assert np.array_equal(ca["hyperedge"], cb["hyperedge"]) and np.array_equal(ca["vertex"], cb["vertex"])
+    a.update_members(np.array([4]), np.array([0, old.size]), old)
+    back = O.counts(a, 3, 0)
+    assert np.array_equal(back["hyperedge"], before["hyperedge"]) and np.array_equal(back["vertex"], before["vertex"])
