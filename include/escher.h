@@ -152,6 +152,31 @@ esc_status esc_apply_batch(esc_graph* g, int64_t n_ins, const int64_t* ins_offse
 esc_status esc_update_members(esc_graph* g, int64_t n, const int32_t* ids, const int64_t* offsets,
                               const int32_t* members);
 
+/* Insert hyperedges under IDs the caller gives, e.g. to rebuild a graph from
+ * esc_export's output: hyperedge j, with vertex set members[offsets[j] ..
+ * offsets[j+1]) and timestamp timestamps[j], takes ID ids[j].  ids: int32[n],
+ * distinct, each in [0, capacity_hyperedges) and not live.  timestamps:
+ * int64[n], required when the temporal family is kept, else NULL means 0.
+ * The new hyperedges' triads are counted as for esc_apply_batch's inserts
+ * (Algorithm 3, inserted side).  Later inserts keep the ID rule over the IDs
+ * left free (free IDs below the largest used one, smallest first, then fresh
+ * ones), so IDs depend only on which IDs are live.  Pointers host or device.
+ * Errors: INVALID_ARG (repeated or live ID, malformed sets, missing
+ * timestamps), NOT_FOUND (an ID outside the range), OUT_OF_MEMORY and
+ * UNSUPPORTED as esc_apply_batch; a failed call changes nothing. */
+esc_status esc_insert_with_ids(esc_graph* g, int64_t n, const int32_t* ids, const int64_t* offsets,
+                               const int32_t* members, const int64_t* timestamps);
+
+/* Create a graph that holds a checkpointed state: esc_create with cfg and no
+ * hyperedges, then the n_he hyperedges inserted under their IDs (the ids,
+ * timestamps, offsets and members arrays of esc_export), in batches of at
+ * most max_batch_hyperedges hyperedges and max_batch_incidences members.
+ * The result has the exported graph's store, counts and future ID
+ * assignment.  Errors as esc_create and esc_insert_with_ids; on failure
+ * nothing is allocated, *out is NULL and esc_last_error(NULL) says why. */
+esc_status esc_restore(const esc_config* cfg, int64_t n_he, const int32_t* ids, const int64_t* offsets,
+                       const int32_t* members, const int64_t* timestamps, void* cuda_stream, esc_graph** out);
+
 /* Copy the current counts of one family into out (uint64[n_out]; n_out must be
  * at least 30, 3 or 96).  window is the temporal window and must equal the
  * configured delta for ESC_TRIAD_TEMPORAL; it is ignored otherwise.
@@ -276,6 +301,17 @@ esc_status esc_group_apply(esc_group* grp, int32_t n, const esc_batch* batches);
 /* esc_update_members for graph `graph` of the group (that graph's IDs). */
 esc_status esc_group_update_members(esc_group* grp, int32_t graph, int64_t n, const int32_t* ids,
                                     const int64_t* offsets, const int32_t* members);
+
+/* esc_insert_with_ids for graph `graph` of the group (that graph's IDs); one
+ * call, so n and the members must fit the group's batch limits. */
+esc_status esc_group_insert_with_ids(esc_group* grp, int32_t graph, int64_t n, const int32_t* ids,
+                                     const int64_t* offsets, const int32_t* members, const int64_t* timestamps);
+
+/* esc_export_sizes / esc_export for graph `graph` of the group, in that
+ * graph's own hyperedge and vertex IDs. */
+esc_status esc_group_export_sizes(esc_group* grp, int32_t graph, int64_t* n_live, int64_t* n_incidences);
+esc_status esc_group_export(esc_group* grp, int32_t graph, int32_t* ids, int64_t* timestamps, int64_t* offsets,
+                            int32_t* members, int64_t* v_offsets, int32_t* v_members);
 
 esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window,
                             uint64_t* out, int32_t n_out);

@@ -389,10 +389,12 @@ static std::string describe(const Scalars& s) {
     switch (s.status) {
         case kErrInvalid:
             if (b >= 0) snprintf(buf, sizeof buf, "batch %d: invalid input at element %d (value %d)", b, i, v);
+            else if (b == -5) snprintf(buf, sizeof buf, "insert with ID %d, which holds a live hyperedge", v);
             else snprintf(buf, sizeof buf, "duplicate delete of hyperedge %d", v);
             break;
         case kErrNotFound:
-            snprintf(buf, sizeof buf, "delete of hyperedge %d, which is not live", v);
+            if (b == -6) snprintf(buf, sizeof buf, "ID %d is outside the graph's hyperedge ID range", v);
+            else snprintf(buf, sizeof buf, "delete of hyperedge %d, which is not live", v);
             break;
         case kErrNoMem:
             if (b == -1) snprintf(buf, sizeof buf, "inserted members (%d) exceed max_batch_incidences (%d)", i, v);
@@ -608,6 +610,7 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs, const int32_t*
     C.n_ins = tot_ins;
     C.n_del = tot_del;
     C.dims = E->d_dims;
+    C.pinned = pins != nullptr;
     LaunchCounter lc;
     const bool prof = E->profiling;
     // graph mode: one replay of the fixed launch sequence; a call whose lists
@@ -700,6 +703,21 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs, const int32_t*
     return ESC_OK;
 }
 
+// Copy n int32 IDs (host or device) to the host and check they are distinct.
+static esc_status host_ids(Engine* E, int64_t n, const int32_t* ids, std::vector<int32_t>& out) {
+    out.resize(static_cast<size_t>(n));
+    if (is_device_ptr(ids))
+        ESC_CU(cudaMemcpy(out.data(), ids, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "ids");
+    else
+        memcpy(out.data(), ids, sizeof(int32_t) * n);
+    std::vector<int32_t> sorted(out);
+    std::sort(sorted.begin(), sorted.end());
+    for (size_t i = 1; i < sorted.size(); ++i)
+        if (sorted[i] == sorted[i - 1])
+            return E->fail(ESC_ERR_INVALID_ARG, "hyperedge ID " + std::to_string(sorted[i]) + " repeated");
+    return ESC_OK;
+}
+
 // Horizontal update (incident vertices inserted into / deleted from live
 // hyperedges): each hyperedge ids[j] of graph g gets a new vertex set and
 // keeps its ID and timestamp.  As a call: the old hyperedges are deleted and
@@ -711,15 +729,11 @@ static esc_status update_members(Engine* E, int32_t g, int64_t n, const int32_t*
     if (g < 0 || g >= E->G || n < 0 || (n > 0 && (!ids || !offsets || !members)))
         return E->fail(ESC_ERR_INVALID_ARG, "bad update");
     if (n == 0) return ESC_OK;
-    std::vector<int32_t> pin(static_cast<size_t>(n));
-    if (is_device_ptr(ids))
-        ESC_CU(cudaMemcpy(pin.data(), ids, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "ids");
-    else
-        memcpy(pin.data(), ids, sizeof(int32_t) * n);
+    std::vector<int32_t> pin;
+    esc_status s = host_ids(E, n, ids, pin);
+    if (s != ESC_OK) return s;
     std::vector<int32_t> del(pin);
     std::sort(del.begin(), del.end());
-    for (size_t i = 1; i < del.size(); ++i)
-        if (del[i] == del[i - 1]) return E->fail(ESC_ERR_INVALID_ARG, "hyperedge " + std::to_string(del[i]) + " repeated");
     esc_batch b{};
     b.graph = g;
     b.n_ins = n;
@@ -730,6 +744,129 @@ static esc_status update_members(Engine* E, int32_t g, int64_t n, const int32_t*
     b.del_ids = del.data();
     const int32_t* pins[1] = {pin.data()};
     return run_call(E, 1, &b, pins);
+}
+
+// Inserts whose IDs the caller gives (a restored checkpoint; with pin null,
+// the ID rule picks them as for any insert): hyperedge j
+// takes ID pin[j] (which must be free) and its triads are counted like any
+// insert's (the inserted side of Alg. 3).  The graph's high-water mark rises
+// to cover the IDs, so later inserts follow the ID rule as if the hyperedges
+// had been inserted one by one: free IDs below the mark first, smallest
+// first, then fresh ones.  One call per chunk of at most max_ins hyperedges
+// and max_nnz members; with chunked set, a failed chunk leaves the earlier
+// ones in place (callers that need all-or-nothing pass chunked = false).
+static esc_status insert_pinned(Engine* E, int32_t g, int64_t n, const int32_t* pin, const int64_t* offsets,
+                                const int32_t* members, const int64_t* timestamps, bool chunked) {
+    if (n == 0) return ESC_OK;
+    std::vector<int64_t> hoff(size_t(n) + 1);
+    if (is_device_ptr(offsets))
+        ESC_CU(cudaMemcpy(hoff.data(), offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost), "offsets");
+    else
+        memcpy(hoff.data(), offsets, sizeof(int64_t) * (n + 1));
+    if (hoff[0] != 0) return E->fail(ESC_ERR_INVALID_ARG, "offsets must start at 0");
+    std::vector<int64_t> zero_ts;
+    if (!timestamps) {
+        if (E->shared.families & kFamT) return E->fail(ESC_ERR_INVALID_ARG, "timestamps required by the temporal family");
+        zero_ts.assign(static_cast<size_t>(n), 0);
+        timestamps = zero_ts.data();
+    }
+    std::vector<int64_t> rebased;
+    int64_t i0 = 0;
+    while (i0 < n) {
+        int64_t i1 = n;
+        if (chunked) {
+            i1 = i0;
+            while (i1 < n && i1 - i0 < E->max_ins && hoff[i1 + 1] - hoff[i0] <= E->max_nnz) ++i1;
+            if (i1 == i0) return E->fail(ESC_ERR_OUT_OF_MEMORY, "a hyperedge is larger than max_batch_incidences");
+        }
+        rebased.resize(size_t(i1 - i0) + 1);
+        for (int64_t i = i0; i <= i1; ++i) rebased[i - i0] = hoff[i] - hoff[i0];
+        esc_batch b{};
+        b.graph = g;
+        b.n_ins = i1 - i0;
+        b.ins_offsets = rebased.data();
+        b.ins_members = members + hoff[i0];
+        b.ins_timestamps = timestamps + i0;
+        const int32_t* pins[1] = {pin ? pin + i0 : nullptr};
+        esc_status s = run_call(E, 1, &b, pin ? pins : nullptr);
+        if (s != ESC_OK) return s;
+        i0 = i1;
+    }
+    return ESC_OK;
+}
+
+static esc_status insert_with_ids(Engine* E, int32_t g, int64_t n, const int32_t* ids, const int64_t* offsets,
+                                  const int32_t* members, const int64_t* timestamps) {
+    if (g < 0 || g >= E->G || n < 0 || (n > 0 && (!ids || !offsets || !members)))
+        return E->fail(ESC_ERR_INVALID_ARG, "bad insert");
+    if (n == 0) return ESC_OK;
+    std::vector<int32_t> pin;
+    esc_status s = host_ids(E, n, ids, pin);
+    if (s != ESC_OK) return s;
+    return insert_pinned(E, g, n, pin.data(), offsets, members, timestamps, false);
+}
+
+// Graph g's live hyperedges and vertex lists, in the graph's own IDs.
+static esc_status export_graph(Engine* E, int32_t g, int64_t* n_live, int64_t* n_incidences, int32_t* ids,
+                               int64_t* timestamps, int64_t* offsets, int32_t* members, int64_t* v_offsets,
+                               int32_t* v_members) {
+    if (g < 0 || g >= E->G) return E->fail(ESC_ERR_INVALID_ARG, "bad graph");
+    ESC_CU(cudaStreamSynchronize(E->st), "sync");
+    const Store& S = E->S;
+    const int64_t eb = E->ebase[g], vb = E->vbase[g];
+    const size_t ne = size_t(E->ecap[g]), nvt = size_t(E->nv[g]);  // ebase and ecap are multiples of 32
+    std::vector<int32_t> card(ne);
+    std::vector<uint32_t> live(ne / 32);
+    ESC_CU(cudaMemcpy(card.data(), S.h_card + eb, ne * 4, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(live.data(), S.live + eb / 32, live.size() * 4, cudaMemcpyDeviceToHost), "export");
+    if (n_live || n_incidences) {
+        int64_t nl = 0, ni = 0;
+        for (size_t i = 0; i < ne; ++i)
+            if (live[i >> 5] >> (i & 31) & 1) {
+                ++nl;
+                ni += card[i];
+            }
+        if (n_live) *n_live = nl;
+        if (n_incidences) *n_incidences = ni;
+    }
+    if (!ids && !timestamps && !offsets && !members && !v_offsets && !v_members) return ESC_OK;
+    std::vector<int32_t> vdeg(nvt);
+    std::vector<int64_t> hoff(ne), hts(ne), voff(nvt);
+    int64_t htail = 0, vtail = 0;
+    ESC_CU(cudaMemcpy(hoff.data(), S.h_off + eb, ne * 8, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(hts.data(), S.h_ts + eb, ne * 8, cudaMemcpyDeviceToHost), "export");
+    if (nvt) {
+        ESC_CU(cudaMemcpy(vdeg.data(), S.v_deg + vb, nvt * 4, cudaMemcpyDeviceToHost), "export");
+        ESC_CU(cudaMemcpy(voff.data(), S.v_off + vb, nvt * 8, cudaMemcpyDeviceToHost), "export");
+    }
+    ESC_CU(cudaMemcpy(&htail, S.hp.tail, 8, cudaMemcpyDeviceToHost), "export");
+    ESC_CU(cudaMemcpy(&vtail, S.vp.tail, 8, cudaMemcpyDeviceToHost), "export");
+    std::vector<int32_t> harena(static_cast<size_t>(htail)), varena(static_cast<size_t>(vtail));
+    if (htail) ESC_CU(cudaMemcpy(harena.data(), S.hp.arena, size_t(htail) * 4, cudaMemcpyDeviceToHost), "export");
+    if (vtail) ESC_CU(cudaMemcpy(varena.data(), S.vp.arena, size_t(vtail) * 4, cudaMemcpyDeviceToHost), "export");
+    int64_t k = 0, p = 0;
+    if (offsets) offsets[0] = 0;
+    for (size_t i = 0; i < ne; ++i) {
+        if (!(live[i >> 5] >> (i & 31) & 1)) continue;
+        if (ids) ids[k] = int32_t(i);
+        if (timestamps) timestamps[k] = hts[i];
+        for (int j = 0; j < card[i]; ++j, ++p)
+            if (members) members[p] = int32_t(harena[size_t(hoff[i]) + j] - vb);
+        ++k;
+        if (offsets) offsets[k] = p;
+    }
+    int64_t q = 0;
+    if (v_offsets) v_offsets[0] = 0;
+    for (size_t v = 0; v < nvt; ++v) {
+        std::vector<int32_t> l(varena.begin() + voff[v], varena.begin() + voff[v] + vdeg[v]);
+        std::sort(l.begin(), l.end());
+        if (v_members)
+            for (int32_t x : l) v_members[q++] = int32_t(x - eb);
+        else
+            q += int64_t(l.size());
+        if (v_offsets) v_offsets[v + 1] = q;
+    }
+    return ESC_OK;
 }
 
 static esc_status read_counts(Engine* E, int32_t g, esc_triad_type type, int64_t window, uint64_t* out,
@@ -987,6 +1124,25 @@ esc_status esc_group_update_members(esc_group* grp, int32_t graph, int64_t n, co
     return esc::update_members(grp->e, graph, n, ids, offsets, members);
 }
 
+esc_status esc_group_insert_with_ids(esc_group* grp, int32_t graph, int64_t n, const int32_t* ids,
+                                     const int64_t* offsets, const int32_t* members, const int64_t* timestamps) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::insert_with_ids(grp->e, graph, n, ids, offsets, members, timestamps);
+}
+
+esc_status esc_group_export_sizes(esc_group* grp, int32_t graph, int64_t* n_live, int64_t* n_incidences) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::export_graph(grp->e, graph, n_live, n_incidences, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr);
+}
+
+esc_status esc_group_export(esc_group* grp, int32_t graph, int32_t* ids, int64_t* timestamps, int64_t* offsets,
+                            int32_t* members, int64_t* v_offsets, int32_t* v_members) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::export_graph(grp->e, graph, nullptr, nullptr, ids, timestamps, offsets, members, v_offsets,
+                             v_members);
+}
+
 esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window, uint64_t* out,
                             int32_t n_out) {
     if (!grp) return ESC_ERR_INVALID_ARG;
@@ -1062,46 +1218,11 @@ esc_status esc_create(const esc_config* cfg, int64_t n_he, const int64_t* offset
     if (n_he > 0) {
         // initial hyperedges enter as insert batches, in order, so they get
         // IDs 0..n_he-1 and their triads are counted by the same kernels
-        std::vector<int64_t> hoff(size_t(n_he) + 1);
-        if (esc::is_device_ptr(offsets)) {
-            cudaMemcpy(hoff.data(), offsets, sizeof(int64_t) * (n_he + 1), cudaMemcpyDeviceToHost);
-        } else {
-            memcpy(hoff.data(), offsets, sizeof(int64_t) * (n_he + 1));
-        }
-        if (hoff[0] != 0) {
-            esc::t_create_error = "offsets must start at 0";
+        s = esc::insert_pinned(E, 0, n_he, nullptr, offsets, members, timestamps, true);
+        if (s != ESC_OK) {
+            esc::t_create_error = E->err;
             esc_destroy(g);
-            return ESC_ERR_INVALID_ARG;
-        }
-        const bool mem_dev = esc::is_device_ptr(members);
-        const bool ts_dev = timestamps && esc::is_device_ptr(timestamps);
-        int64_t i0 = 0;
-        std::vector<int64_t> rebased;
-        while (i0 < n_he) {
-            int64_t i1 = i0;
-            while (i1 < n_he && i1 - i0 < E->max_ins && hoff[i1 + 1] - hoff[i0] <= E->max_nnz) ++i1;
-            if (i1 == i0) {
-                esc::t_create_error = "a hyperedge is larger than max_batch_incidences";
-                esc_destroy(g);
-                return ESC_ERR_OUT_OF_MEMORY;
-            }
-            rebased.resize(size_t(i1 - i0) + 1);
-            for (int64_t i = i0; i <= i1; ++i) rebased[i - i0] = hoff[i] - hoff[i0];
-            esc_batch b{};
-            b.graph = 0;
-            b.n_ins = i1 - i0;
-            b.ins_offsets = rebased.data();
-            b.ins_members = members + hoff[i0];
-            b.ins_timestamps = timestamps ? timestamps + i0 : nullptr;
-            (void)mem_dev;
-            (void)ts_dev;
-            s = esc::run_call(E, 1, &b);
-            if (s != ESC_OK) {
-                esc::t_create_error = E->err;
-                esc_destroy(g);
-                return s;
-            }
-            i0 = i1;
+            return s;
         }
     }
     *out = g;
@@ -1177,66 +1298,43 @@ int64_t esc_launch_count(const esc_graph* g) { return g ? g->e->lc.total : 0; }
 
 esc_status esc_export_sizes(esc_graph* g, int64_t* n_live, int64_t* n_incidences) {
     if (!g) return ESC_ERR_INVALID_ARG;
-    Engine* E = g->e;
-    std::vector<int32_t> card(size_t(E->S.e_total));
-    std::vector<uint32_t> live(size_t(E->S.e_total / 32));
-    ESC_CU(cudaMemcpy(card.data(), E->S.h_card, card.size() * 4, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(live.data(), E->S.live, live.size() * 4, cudaMemcpyDeviceToHost), "export");
-    int64_t nl = 0, ni = 0;
-    for (size_t i = 0; i < card.size(); ++i)
-        if (live[i >> 5] >> (i & 31) & 1) {
-            ++nl;
-            ni += card[i];
-        }
-    if (n_live) *n_live = nl;
-    if (n_incidences) *n_incidences = ni;
-    return ESC_OK;
+    return esc::export_graph(g->e, 0, n_live, n_incidences, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 esc_status esc_export(esc_graph* g, int32_t* ids, int64_t* timestamps, int64_t* offsets, int32_t* members,
                       int64_t* v_offsets, int32_t* v_members) {
     if (!g) return ESC_ERR_INVALID_ARG;
-    Engine* E = g->e;
-    ESC_CU(cudaStreamSynchronize(E->st), "sync");
-    const esc::Store& S = E->S;
-    const size_t ne = size_t(S.e_total), nvt = size_t(S.nv_total);
-    std::vector<int32_t> card(ne), vdeg(nvt);
-    std::vector<uint32_t> live(ne / 32);
-    std::vector<int64_t> hoff(ne), hts(ne), voff(nvt);
-    int64_t htail = 0, vtail = 0;
-    ESC_CU(cudaMemcpy(card.data(), S.h_card, ne * 4, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(live.data(), S.live, live.size() * 4, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(hoff.data(), S.h_off, ne * 8, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(hts.data(), S.h_ts, ne * 8, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(vdeg.data(), S.v_deg, nvt * 4, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(voff.data(), S.v_off, nvt * 8, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(&htail, S.hp.tail, 8, cudaMemcpyDeviceToHost), "export");
-    ESC_CU(cudaMemcpy(&vtail, S.vp.tail, 8, cudaMemcpyDeviceToHost), "export");
-    std::vector<int32_t> harena(static_cast<size_t>(htail)), varena(static_cast<size_t>(vtail));
-    if (htail) ESC_CU(cudaMemcpy(harena.data(), S.hp.arena, size_t(htail) * 4, cudaMemcpyDeviceToHost), "export");
-    if (vtail) ESC_CU(cudaMemcpy(varena.data(), S.vp.arena, size_t(vtail) * 4, cudaMemcpyDeviceToHost), "export");
-    int64_t k = 0, p = 0;
-    if (offsets) offsets[0] = 0;
-    for (size_t i = 0; i < ne; ++i) {
-        if (!(live[i >> 5] >> (i & 31) & 1)) continue;
-        if (ids) ids[k] = int32_t(i);
-        if (timestamps) timestamps[k] = hts[i];
-        for (int j = 0; j < card[i]; ++j, ++p)
-            if (members) members[p] = harena[size_t(hoff[i]) + j];
-        ++k;
-        if (offsets) offsets[k] = p;
+    return esc::export_graph(g->e, 0, nullptr, nullptr, ids, timestamps, offsets, members, v_offsets, v_members);
+}
+
+esc_status esc_insert_with_ids(esc_graph* g, int64_t n, const int32_t* ids, const int64_t* offsets,
+                               const int32_t* members, const int64_t* timestamps) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    return esc::insert_with_ids(g->e, 0, n, ids, offsets, members, timestamps);
+}
+
+esc_status esc_restore(const esc_config* cfg, int64_t n_he, const int32_t* ids, const int64_t* offsets,
+                       const int32_t* members, const int64_t* timestamps, void* cuda_stream, esc_graph** out) {
+    if (!out) return ESC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_he < 0 || (n_he > 0 && (!ids || !offsets || !members))) {
+        esc::t_create_error = "invalid checkpoint";
+        return ESC_ERR_INVALID_ARG;
     }
-    int64_t q = 0;
-    if (v_offsets) v_offsets[0] = 0;
-    for (size_t v = 0; v < nvt; ++v) {
-        std::vector<int32_t> l(varena.begin() + voff[v], varena.begin() + voff[v] + vdeg[v]);
-        std::sort(l.begin(), l.end());
-        if (v_members)
-            for (int32_t x : l) v_members[q++] = x;
-        else
-            q += int64_t(l.size());
-        if (v_offsets) v_offsets[v + 1] = q;
+    esc_graph* g = nullptr;
+    esc_status s = esc_create(cfg, 0, nullptr, nullptr, nullptr, cuda_stream, &g);
+    if (s != ESC_OK) return s;
+    std::vector<int32_t> pin;
+    if (n_he > 0) {
+        s = esc::host_ids(g->e, n_he, ids, pin);
+        if (s == ESC_OK) s = esc::insert_pinned(g->e, 0, n_he, pin.data(), offsets, members, timestamps, true);
     }
+    if (s != ESC_OK) {
+        esc::t_create_error = g->e->err;
+        esc_destroy(g);
+        return s;
+    }
+    *out = g;
     return ESC_OK;
 }
 

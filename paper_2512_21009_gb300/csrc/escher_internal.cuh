@@ -143,6 +143,7 @@ struct Call {
     // sequence that serves calls of any size (a CUDA graph), the limits
     int64_t grid_batches, grid_ins, grid_del;
     bool fixed;              // launch every kernel even when its part of the call is empty
+    bool pinned;             // some batch gives the IDs of its inserts
     int64_t max_nnz;         // staging capacity
     int64_t* ins_off;        // [n_ins+1]
     int32_t* raw;            // [max_nnz] members, global vertex IDs

@@ -129,7 +129,7 @@ __global__ void k_gather(Store S, Call C, const int64_t* b_ins_lo, const int64_t
             // given one, its timestamp (read before anything changes)
             const int32_t p = B.pin[i];
             if (p < 0 || p >= S.ecap[B.graph]) {
-                set_error(C.sc, kErrNotFound, b, i, p);
+                set_error(C.sc, kErrNotFound, -6, i, p);
                 C.ids[j] = -1;
             } else {
                 const int64_t id = S.ebase[B.graph] + p;
@@ -283,6 +283,23 @@ __global__ void k_del_check(Store S, Call C) {
     }
 }
 
+// Inserts with given IDs: the ID must not hold a live hyperedge, unless the
+// same call deletes it (a horizontal update).
+__global__ void k_pin_check(Store S, Call C) {
+    if (C.sc->gate) return;
+    for (int bi = blockIdx.x; bi < nbat(C); bi += gridDim.x) {
+        const BatchIn& B = C.batches[bi];
+        if (!B.pin) continue;
+        const int64_t eb = S.ebase[B.graph];
+        for (int64_t i = threadIdx.x; i < B.n_ins; i += blockDim.x) {
+            const int32_t p = B.pin[i];
+            if (p < 0 || p >= S.ecap[B.graph]) continue;  // k_gather reports it
+            const int64_t id = eb + p;
+            if (bit_test(S.live, id) && !bit_test(S.delb, id)) set_error(C.sc, kErrInvalid, -5, i, p);
+        }
+    }
+}
+
 // Per-vertex delete counts from the deleted hyperedges' member lists, and the
 // largest neighbour-entry count sum(deg) of a deleted hyperedge.
 __global__ void k_touch_del(Store S, Call C) {
@@ -410,7 +427,23 @@ __global__ void __launch_bounds__(kSelNT) k_select(Store S, Call C) {
     for (int bi = blockIdx.x; bi < nbat(C); bi += gridDim.x) {
     const BatchIn& B = C.batches[bi];
     int64_t n = B.n_ins;
-    if (n == 0 || B.pin) continue;  // kept IDs were set by k_gather
+    if (n == 0) continue;
+    if (B.pin) {
+        // IDs given by the caller (set by k_gather): the high-water mark
+        // covers them, so later inserts never take one
+        int m = -1;
+        for (int64_t r = threadIdx.x; r < n; r += kSelNT) m = max(m, B.pin[r]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane_id() == 0) warp_tmp[warp_id()] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 0; w < kSelNT / 32; ++w) m = max(m, warp_tmp[w]);
+            if (int64_t(m) + 1 > S.hw[B.graph]) S.hw[B.graph] = int64_t(m) + 1;
+        }
+        __syncthreads();
+        continue;
+    }
     int g = B.graph;
     int64_t eb = S.ebase[g], hwg = S.hw[g];
     int64_t nwords = (hwg + 31) >> 5;
@@ -634,6 +667,7 @@ cudaError_t store_ingest(const Store& S, const Call& C, const int64_t* b_ins_lo,
         ESC_LAUNCH(lc, k_del_check<<<g_thr(gd, sm_count), kBlk, 0, st>>>(S, C));
         ESC_LAUNCH(lc, k_touch_del<<<g_warp(gd, sm_count), kBlk, 0, st>>>(S, C));
     }
+    if (C.fixed || C.pinned) ESC_LAUNCH(lc, k_pin_check<<<unsigned(std::max<int64_t>(C.grid_batches, 1)), kBlk, 0, st>>>(S, C));
     if (any_i) ESC_LAUNCH(lc, k_touch_ins<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_vplan<<<sm_count * 4, kBlk, 0, st>>>(S, C));
     if (any_i) ESC_LAUNCH(lc, k_ins_u<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));

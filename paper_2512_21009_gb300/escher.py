@@ -38,7 +38,8 @@ EXPORTED = [
     "esc_group_bytes", "esc_server_create", "esc_server_submit", "esc_server_wait", "esc_server_drain",
     "esc_server_triads", "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
     "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members", "esc_group_update_members",
-    "esc_version", "esc_count_static_noalloc",
+    "esc_version", "esc_count_static_noalloc", "esc_insert_with_ids", "esc_restore",
+    "esc_group_insert_with_ids", "esc_group_export_sizes", "esc_group_export",
 ]
 
 
@@ -136,6 +137,11 @@ def load(path: str = LIB_PATH):
     L.esc_group_update_members.argtypes = [vp, i32, i64, vp, vp, vp]
     L.esc_group_set_graph_launch.argtypes = [vp, i32]
     L.esc_group_autotune.argtypes = [vp, i32, i64, vp, i32, C.POINTER(esc_tune_result)]
+    L.esc_insert_with_ids.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.esc_restore.argtypes = [C.POINTER(esc_config), i64, vp, vp, vp, vp, vp, C.POINTER(vp)]
+    L.esc_group_insert_with_ids.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+    L.esc_group_export_sizes.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
+    L.esc_group_export.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
     L.esc_version.restype = C.c_char_p
     L.esc_count_static_noalloc.argtypes = [i32, i64, vp, vp, vp, u32, i64, vp, vp]
     L.esc_count_static_noalloc.restype = st
@@ -146,7 +152,8 @@ def load(path: str = LIB_PATH):
                  "esc_server_submit", "esc_server_wait", "esc_server_drain", "esc_server_triads",
                  "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
                  "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members",
-                 "esc_group_update_members"):
+                 "esc_group_update_members", "esc_insert_with_ids", "esc_restore", "esc_group_insert_with_ids",
+                 "esc_group_export_sizes", "esc_group_export"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -241,17 +248,63 @@ def esc_destroy(g: int) -> None:
         load().esc_destroy(g)
 
 
+def _export_arrays(n: int, m: int, n_vertices: int):
+    return (np.zeros(max(n, 1), np.int32), np.zeros(max(n, 1), np.int64), np.zeros(n + 1, np.int64),
+            np.zeros(max(m, 1), np.int32), np.zeros(n_vertices + 1, np.int64), np.zeros(max(m, 1), np.int32))
+
+
+def esc_group_export(grp: int, graph: int, n_vertices: int) -> dict:
+    """Graph ``graph`` of the group as esc_export gives it (its own IDs)."""
+    L = load()
+    nl, ni = C.c_int64(), C.c_int64()
+    _check(L.esc_group_export_sizes(grp, int(graph), C.byref(nl), C.byref(ni)), L.esc_group_last_error, grp)
+    n, m = nl.value, ni.value
+    ids, ts, off, mem, voff, vmem = _export_arrays(n, m, n_vertices)
+    rc = L.esc_group_export(grp, int(graph), ids.ctypes.data, ts.ctypes.data, off.ctypes.data, mem.ctypes.data,
+                            voff.ctypes.data, vmem.ctypes.data)
+    _check(rc, L.esc_group_last_error, grp)
+    return dict(ids=ids[:n], timestamps=ts[:n], offsets=off, members=mem[:m], v_offsets=voff,
+                v_members=vmem[:m])
+
+
+def esc_insert_with_ids(g: int, ids, offsets, members, timestamps=None) -> None:
+    """Insert hyperedge j under ID ids[j] (a free ID)."""
+    L = load()
+    pi, ki = _ptr(ids, np.int32)
+    po, ko = _ptr(offsets, np.int64)
+    pm, km = _ptr(members, np.int32)
+    pt, kt = _ptr(timestamps, np.int64)
+    _check(L.esc_insert_with_ids(g, len(ids), pi, po, pm, pt), L.esc_last_error, g)
+
+
+def esc_group_insert_with_ids(grp: int, graph: int, ids, offsets, members, timestamps=None) -> None:
+    L = load()
+    pi, ki = _ptr(ids, np.int32)
+    po, ko = _ptr(offsets, np.int64)
+    pm, km = _ptr(members, np.int32)
+    pt, kt = _ptr(timestamps, np.int64)
+    _check(L.esc_group_insert_with_ids(grp, int(graph), len(ids), pi, po, pm, pt), L.esc_group_last_error, grp)
+
+
+def esc_restore(cfg: esc_config, ids, offsets, members, timestamps=None, stream=None) -> int:
+    """A new graph holding the hyperedges of an export, under their IDs."""
+    L = load()
+    pi, ki = _ptr(ids, np.int32)
+    po, ko = _ptr(offsets, np.int64)
+    pm, km = _ptr(members, np.int32)
+    pt, kt = _ptr(timestamps, np.int64)
+    h = C.c_void_p()
+    rc = L.esc_restore(C.byref(cfg), len(ids), pi, po, pm, pt, _stream_ptr(stream), C.byref(h))
+    _check(rc, L.esc_last_error, None)
+    return h.value
+
+
 def esc_export(g: int, n_vertices: int) -> dict:
     L = load()
     nl, ni = C.c_int64(), C.c_int64()
     _check(L.esc_export_sizes(g, C.byref(nl), C.byref(ni)), L.esc_last_error, g)
     n, m = nl.value, ni.value
-    ids = np.zeros(max(n, 1), np.int32)
-    ts = np.zeros(max(n, 1), np.int64)
-    off = np.zeros(n + 1, np.int64)
-    mem = np.zeros(max(m, 1), np.int32)
-    voff = np.zeros(n_vertices + 1, np.int64)
-    vmem = np.zeros(max(m, 1), np.int32)
+    ids, ts, off, mem, voff, vmem = _export_arrays(n, m, n_vertices)
     rc = L.esc_export(g, ids.ctypes.data, ts.ctypes.data, off.ctypes.data, mem.ctypes.data,
                       voff.ctypes.data, vmem.ctypes.data)
     _check(rc, L.esc_last_error, g)
@@ -522,6 +575,25 @@ class Graph:
             offsets = np.zeros(1, np.int64)
             members = np.zeros(0, np.int32)
         self.h = esc_create(self.cfg, offsets, members, timestamps, stream)
+
+    @classmethod
+    def restore(cls, n_vertices: int, checkpoint: dict, *, capacity_hyperedges: int, capacity_incidences: int,
+                max_batch_hyperedges: int, max_batch_incidences: int, families: int, delta: int = 0,
+                stream=None) -> "Graph":
+        """A graph holding ``checkpoint`` (an ``export()`` result) under its IDs."""
+        self = cls.__new__(cls)
+        self.n_vertices = int(n_vertices)
+        self.families = families
+        self.delta = int(delta)
+        self.cfg = make_config(n_vertices, capacity_hyperedges, capacity_incidences, max_batch_hyperedges,
+                               max_batch_incidences, families, delta)
+        self.h = 0
+        self.h = esc_restore(self.cfg, checkpoint["ids"], checkpoint["offsets"], checkpoint["members"],
+                             checkpoint.get("timestamps"), stream)
+        return self
+
+    def insert_with_ids(self, ids, offsets, members, timestamps=None) -> None:
+        esc_insert_with_ids(self.h, ids, offsets, members, timestamps)
 
     def apply_batch(self, ins_offsets=None, ins_members=None, ins_timestamps=None, del_ids=None,
                     return_ids: bool = True) -> Optional[np.ndarray]:
