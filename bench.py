@@ -11,7 +11,8 @@ popularity one vertex sits in ~73% of the hyperedges and an exact recount of
 the triads around it is ~1e17 classifications per batch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload large_uniform|tiny] [--scale S]
+                  [--workload large_uniform|tiny|batched|temporal|serving|horizontal|sweep]
+                  [--sweep batch|delete|card|size|spread] [--scale S]
 
 Under torchrun (N > 1) every rank runs its own replica on its own GPU (weak
 scaling; the single-graph path has no exchange step).  Rank 0 prints one
@@ -493,6 +494,178 @@ def run_horizontal(args):
 
 
 # ---------------------------------------------------------------------------
+# sweeps: the same kernels over batch size, deletion share, inserted
+# cardinality, graph size and cardinality spread (one JSON line per point)
+# ---------------------------------------------------------------------------
+
+def _sweep_graph(E, nv, init, n_ids, n_inc, max_bh, max_bi, fam, dev):
+    import torch
+    todev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)  # noqa: E731
+    t0 = time.time()
+    g = E.Graph(nv, todev(init.offsets, np.int64), todev(init.members, np.int32), todev(init.timestamps, np.int64),
+                capacity_hyperedges=n_ids, capacity_incidences=n_inc, max_batch_hyperedges=max_bh,
+                max_batch_incidences=max_bi, families=fam, stream=torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    return g, time.time() - t0
+
+
+def _sweep_point(E, g, model, inserts, n_del, args, dev, rng):
+    """Apply ``warmup`` then ``steps`` batches (inserts[k] plus n_del deletes
+    of uniform live hyperedges, inputs resident on the device); device time
+    of the timed ones by CUDA events on the graph's stream."""
+    import torch
+    todev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)  # noqa: E731
+    prepared, expect = [], []
+    for csr in inserts:
+        idx, dels = model.pick(rng, n_del)
+        expect.append(model.commit(idx, dels, csr.n))
+        prepared.append((todev(csr.offsets, np.int64), todev(csr.members, np.int32),
+                         todev(csr.timestamps, np.int64), todev(np.sort(dels), np.int32)))
+    got = []
+
+    def step(b):
+        out = np.zeros(b[0].numel() - 1, np.int32)
+        E.esc_apply_batch(g.h, b[0], b[1], b[2], b[3], out)
+        got.append(out)
+
+    st = torch.cuda.current_stream(dev)
+    g.set_profiling(True)
+    for k in range(args.warmup):
+        step(prepared[k])
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    l0 = g.launch_count()
+    lat, cnt_ms, store_ms = [], [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for k in range(args.warmup, args.warmup + args.steps):
+        t1 = time.perf_counter()
+        step(prepared[k])
+        lat.append((time.perf_counter() - t1) * 1e3)
+        sts = g.stats()
+        cnt_ms.append(sts["ms_count_del"] + sts["ms_count_ins"])
+        store_ms.append(sts["ms_ingest"] + sts["ms_store"])
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    el = e0.elapsed_time(e1) / 1e3
+    for want, have in zip(expect, got):
+        if not np.array_equal(want, have):
+            raise SystemExit("bench: assigned IDs differ from the client's copy of the ID rule")
+    upd = sum(inserts[k].n + n_del for k in range(args.warmup, args.warmup + args.steps))
+    return {"value": upd / el, "ms_per_step": el * 1e3 / args.steps,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "stage_ms_per_step": {"count": sum(cnt_ms) / len(cnt_ms), "store_and_ingest": sum(store_ms) / len(store_ms)},
+            "gpu_launches": int(g.launch_count() - l0), "clocks": clk}
+
+
+def _sweep_line(args, r, workload, sweep, point, families, extra=None):
+    out = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32 ids / uint64 counts", "data": "synthetic",
+           "config": {"workload": workload, "sweep": sweep, "point": point, "families": families,
+                      "l2": "resident store larger than L2 (129 MB)"},
+           "latency_ms": r["latency_ms"], "stage_ms_per_step": r["stage_ms_per_step"],
+           "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    if extra:
+        out["config"].update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def run_sweep(args):
+    """Figs. 5a-c, 7 and 15 as synthetic sweeps.  batch: 50K/100K/200K
+    updates, half inserts; delete: 50K updates with 20-80% deletes; card:
+    50K inserts with cardinality Zipf(2.0) capped at 50/100/200; these three
+    share the uniform 1M-vertex graph of the default workload.  size: graphs
+    of 20M-55M hyperedges (times --size-scale), |V| = |E|/3, cardinality
+    Zipf(2.0) in [2, --size-kmax], 50K updates (with the cap at 10,000 one
+    point at 1M hyperedges takes minutes: the largest hyperedges meet ~4e5
+    neighbours each).  spread: a dyadic graph (1M
+    vertices, 4M two-member hyperedges), 50K updates whose inserted
+    cardinalities have mean 4 and standard deviation 0-16 (first point: plain
+    edges), incident-vertex family."""
+    import torch
+    from paper_2512_21009_gb300 import escher as E
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nb = args.warmup + args.steps
+    rng = np.random.default_rng(args.seed + 101)
+    fam_hv = "hyperedge (30) + incident-vertex (3)"
+    if args.sweep in ("batch", "delete", "card"):
+        s = gen.large(seed=args.seed, membership="uniform", scale=args.scale, n_batches=0)
+        init = s.initial
+        t_end = int(init.timestamps[-1])
+        if args.sweep == "batch":
+            pts = [(dict(batch=b, delete_pct=50), b - b // 2, b // 2, 1000) for b in (50_000, 100_000, 200_000)]
+        elif args.sweep == "delete":
+            pts = [(dict(batch=50_000, delete_pct=p), 50_000 - 500 * p, 500 * p, 1000) for p in (20, 40, 60, 80)]
+        else:
+            pts = [(dict(inserts=50_000, card_cap=c), 50_000, 0, c) for c in (50, 100, 200)]
+        ins = [gen.insert_batches(args.seed + 7 + i, s.n_vertices, nb, n_ins, kmax, ts_start=t_end)
+               for i, (_, n_ins, _, kmax) in enumerate(pts)]
+        n_ids = init.n + sum(c.n for L in ins for c in L) + 64
+        n_inc = int(1.6 * (init.nnz + sum(c.nnz for L in ins for c in L))) + (1 << 20)
+        max_bh = max(max(n_i + n_d for _, n_i, n_d, _ in pts), min(init.n, 100_000))
+        max_bi = max(max(c.nnz for L in ins for c in L), 4 * max_bh * 16)
+        g, t_create = _sweep_graph(E, s.n_vertices, init, n_ids, n_inc, max_bh, max_bi, 3, dev)
+        model = _IdModel(init.n)
+        desc = (f"large, uniform membership: {s.n_vertices:,} vertices, {init.n:,} initial hyperedges, "
+                "cardinality Zipf(2.0) in [2,1000]; inserts Zipf(2.0) in [2, cap], uniform members; deletes "
+                "uniform over live hyperedges")
+        for (point, n_ins, n_del, _), L in zip(pts, ins):
+            r = _sweep_point(E, g, model, L, n_del, args, dev, rng)
+            _sweep_line(args, r, desc, args.sweep, point, fam_hv, {"create_s": round(t_create, 2)})
+        g.close()
+    elif args.sweep == "size":
+        for i, m in enumerate((20, 30, 40, 55)):
+            if args.size_points and m not in args.size_points:
+                continue
+            n_e = max(64, int(round(m * 1e6 * args.size_scale)))
+            nv = max(10_000, n_e // 3)
+            init = gen.random_hypergraph(args.seed + 31 + i, nv, n_e, args.size_kmax)
+            L = gen.insert_batches(args.seed + 41 + i, nv, nb, 25_000, args.size_kmax,
+                                   ts_start=int(init.timestamps[-1]))
+            n_ids = init.n + 25_000 * nb + 64
+            n_inc = int(1.6 * (init.nnz + sum(c.nnz for c in L))) + (1 << 20)
+            max_bh = max(50_000, min(init.n, 100_000))
+            max_bi = max(max(c.nnz for c in L), 1 << 24)
+            g, t_create = _sweep_graph(E, nv, init, n_ids, n_inc, max_bh, max_bi, 3, dev)
+            r = _sweep_point(E, g, _IdModel(init.n), L, 25_000, args, dev, rng)
+            desc = (f"random hypergraph: {n_e:,} hyperedges ({m}M x {args.size_scale}), {nv:,} vertices (|E|/3), "
+                    f"cardinality Zipf(2.0) in [2,{args.size_kmax}], uniform members; batches of 25,000 inserts "
+                    "(same distribution) + 25,000 uniform deletes")
+            _sweep_line(args, r, desc, "size", dict(hyperedges=n_e, vertices=nv, incidences=int(init.nnz)), fam_hv,
+                        {"create_s": round(t_create, 2)})
+            g.close()
+            del g
+            torch.cuda.empty_cache()
+    else:  # spread
+        nv, n_e = int(round(1_000_000 * args.scale)), int(round(4_000_000 * args.scale))
+        init = gen.dyadic_graph(args.seed + 51, nv, n_e)
+        pts = [(2.0, 0.0)] + [(4.0, sd) for sd in (0.0, 1.0, 2.0, 4.0, 8.0, 16.0)]
+        ins = [gen.spread_inserts(args.seed + 61 + i, nv, nb, 25_000, mu, sd, ts_start=int(init.timestamps[-1]))
+               for i, (mu, sd) in enumerate(pts)]
+        n_ids = init.n + sum(c.n for L in ins for c in L) + 64
+        n_inc = int(1.6 * (init.nnz + sum(c.nnz for L in ins for c in L))) + (1 << 20)
+        max_bh = max(50_000, min(init.n, 100_000))
+        max_bi = max(max(c.nnz for L in ins for c in L), 1 << 22)
+        g, t_create = _sweep_graph(E, nv, init, n_ids, n_inc, max_bh, max_bi, 2, dev)
+        model = _IdModel(init.n)
+        desc = (f"dyadic graph: {nv:,} vertices, {n_e:,} two-member hyperedges (uniform distinct endpoints); "
+                "batches of 25,000 inserts with uniform members and 25,000 uniform deletes")
+        for (mu, sd), L in zip(pts, ins):
+            k = np.concatenate([np.diff(c.offsets) for c in L[args.warmup:]])
+            r = _sweep_point(E, g, model, L, 25_000, args, dev, rng)
+            _sweep_line(args, r, desc, "spread",
+                        dict(card_mean=round(float(k.mean()), 3), card_std=round(float(k.std()), 3),
+                             card_max=int(k.max())),
+                        "incident-vertex (3); on plain edges type 3 is the triangle count",
+                        {"create_s": round(t_create, 2)})
+        g.close()
+
+
+# ---------------------------------------------------------------------------
 # batched form: many hypergraphs, one call vs one call per graph
 # ---------------------------------------------------------------------------
 
@@ -894,7 +1067,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_uniform",
-                    choices=["large_uniform", "tiny", "batched", "temporal", "serving", "horizontal"])
+                    choices=["large_uniform", "tiny", "batched", "temporal", "serving", "horizontal", "sweep"])
+    ap.add_argument("--sweep", default="batch", choices=["batch", "delete", "card", "size", "spread"],
+                    help="sweep workload: which parameter varies")
+    ap.add_argument("--size-scale", type=float, default=0.05, help="size sweep: fraction of 20M-55M hyperedges")
+    ap.add_argument("--size-kmax", type=int, default=10_000, help="size sweep: cardinality cap")
+    ap.add_argument("--size-points", type=int, nargs="*", default=None,
+                    help="size sweep: which of 20 30 40 55 (million hyperedges before --size-scale) to run")
     ap.add_argument("--graphs", type=int, default=None)
     ap.add_argument("--rate", type=float, default=5e4, help="serving: offered requests/s")
     ap.add_argument("--duration", type=float, default=8.0, help="serving: seconds per run")
@@ -920,6 +1099,8 @@ def main():
         run_serving(args)
     elif args.workload == "horizontal":
         run_horizontal(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

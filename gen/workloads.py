@@ -38,7 +38,7 @@ __all__ = [
     "zipf_cardinalities", "uniform_cardinalities", "sample_members",
     "exp_gap_timestamps",
     "tiny", "large", "temporal", "batched", "resident_graphs", "insert_pool", "serving_arrivals",
-    "random_small",
+    "random_small", "random_hypergraph", "insert_batches", "dyadic_graph", "spread_cardinalities", "spread_inserts",
 ]
 
 
@@ -361,3 +361,83 @@ def serving_arrivals(seed: int, n_graphs: int, n_requests: int, rate_per_s: floa
     g = rng.integers(0, n_graphs, size=n_requests)
     s = np.floor(10 ** rng.uniform(math.log10(size_lo), math.log10(size_hi), size=n_requests)).astype(np.int64)
     return t, g, s
+
+
+def random_hypergraph(seed: int, n_vertices: int, n_edges: int, kmax: int, membership: str = "uniform",
+                      card_exponent: float = 2.0, ts_start: int = 0) -> CSR:
+    """``n_edges`` hyperedges with cardinality Zipf(``card_exponent``) in
+    [2, kmax], members by ``membership``, timestamps with Exp(1e3/s) gaps."""
+    rng = np.random.default_rng(seed)
+    sampler = _VertexSampler(rng, n_vertices, membership)
+    kmax = min(kmax, n_vertices)
+    ts = exp_gap_timestamps(rng, n_edges, ts_start)
+    return _csr(rng, zipf_cardinalities(rng, n_edges, card_exponent, 2, kmax), n_vertices, sampler, ts)
+
+
+def insert_batches(seed: int, n_vertices: int, n_batches: int, n_ins: int, kmax: int,
+                   membership: str = "uniform", card_exponent: float = 2.0, ts_start: int = 0) -> List[CSR]:
+    """``n_batches`` insert lists of ``n_ins`` hyperedges each, drawn as in
+    ``random_hypergraph`` (cardinality cap ``kmax``), timestamps continuing
+    from ``ts_start``.  Deletes are chosen by the caller among its live IDs."""
+    rng = np.random.default_rng(seed)
+    sampler = _VertexSampler(rng, n_vertices, membership)
+    kmax = min(kmax, n_vertices)
+    out, t = [], ts_start
+    for _ in range(n_batches):
+        ts = exp_gap_timestamps(rng, n_ins, t)
+        if n_ins:
+            t = int(ts[-1])
+        out.append(_csr(rng, zipf_cardinalities(rng, n_ins, card_exponent, 2, kmax), n_vertices, sampler, ts))
+    return out
+
+
+def _edge_csr(u: np.ndarray, v: np.ndarray, ts: np.ndarray) -> CSR:
+    off = np.arange(u.shape[0] + 1, dtype=np.int64) * 2
+    mem = np.empty(2 * u.shape[0], np.int32)
+    mem[0::2] = u
+    mem[1::2] = v
+    return CSR(off, mem, ts)
+
+
+def _other_end(rng: np.random.Generator, u: np.ndarray, n_vertices: int) -> np.ndarray:
+    """A uniform second endpoint distinct from ``u``."""
+    v = rng.integers(0, n_vertices - 1, size=u.shape[0], dtype=np.int64)
+    v = v + (v >= u)  # skip u: uniform over the other n-1 vertices
+    return v.astype(np.int32)
+
+
+def dyadic_graph(seed: int, n_vertices: int, n_edges: int) -> CSR:
+    """A dyadic graph as two-member hyperedges: ``n_edges`` edges with both
+    endpoints uniform and distinct (parallel edges possible, as in a
+    multigraph), timestamps with Exp(1e3/s) gaps."""
+    rng = np.random.default_rng(seed)
+    u = rng.integers(0, n_vertices, size=n_edges, dtype=np.int64).astype(np.int32)
+    return _edge_csr(u, _other_end(rng, u, n_vertices), exp_gap_timestamps(rng, n_edges, 0))
+
+
+def spread_cardinalities(rng: np.random.Generator, n: int, mean: float, std: float, kmax: int) -> np.ndarray:
+    """Cardinalities 2 + round(X), X ~ Gamma with mean ``mean`` - 2 and
+    standard deviation ``std`` (``std`` 0: every cardinality is round(mean)),
+    clipped to [2, kmax]."""
+    m = mean - 2.0
+    if std <= 0 or m <= 0:
+        return np.full(n, int(round(max(mean, 2.0))), dtype=np.int64)
+    x = rng.gamma(shape=m * m / (std * std), scale=std * std / m, size=n)
+    return np.clip(2 + np.rint(x).astype(np.int64), 2, kmax)
+
+
+def spread_inserts(seed: int, n_vertices: int, n_batches: int, n_ins: int, mean: float, std: float,
+                   kmax: int = 4096, ts_start: int = 0) -> List[CSR]:
+    """Insert lists whose cardinalities have a set mean and standard
+    deviation (``spread_cardinalities``); members uniform and distinct within
+    a hyperedge.  ``mean`` 2 with ``std`` 0 gives plain edges."""
+    rng = np.random.default_rng(seed)
+    sampler = _VertexSampler(rng, n_vertices, "uniform")
+    kmax = min(kmax, n_vertices)
+    out, t = [], ts_start
+    for _ in range(n_batches):
+        ts = exp_gap_timestamps(rng, n_ins, t)
+        if n_ins:
+            t = int(ts[-1])
+        out.append(_csr(rng, spread_cardinalities(rng, n_ins, mean, std, kmax), n_vertices, sampler, ts))
+    return out

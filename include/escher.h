@@ -217,6 +217,19 @@ esc_status esc_export_sizes(esc_graph* g, int64_t* n_live, int64_t* n_incidences
 esc_status esc_export(esc_graph* g, int32_t* ids, int64_t* timestamps, int64_t* offsets,
                       int32_t* members, int64_t* v_offsets, int32_t* v_members);
 
+/* The h2h mapping (Sec. III, Table II: the line graph, each hyperedge with the list
+ * of hyperedges it is connected to): for the n_live live hyperedges in
+ * ascending ID order (the order of esc_export), offsets int64[n_live+1] and
+ * neighbours int32[n_entries] list the other live hyperedges that share at
+ * least s vertices with it (s >= 1; s = 1 is the line graph, s > 1 the
+ * s-line graph), ascending, and overlaps int32[n_entries] the number of
+ * vertices shared.  *n_entries receives the total.  Any pointer may be NULL
+ * (call once with neighbours NULL to size the arrays).  Assembled on the
+ * host from a copy of the store: meant for small graphs and tests.
+ * Errors: INVALID_ARG (s < 1), CUDA. */
+esc_status esc_export_h2h(esc_graph* g, int32_t s, int64_t* n_entries, int64_t* offsets, int32_t* neighbours,
+                          int32_t* overlaps);
+
 /* Per-batch measurements of the last esc_apply_batch, filled when
  * esc_set_profiling(g, 1) is on.  Stage times are device times measured with
  * CUDA events on the graph's stream (the time split of the paper's Fig. 11b:
@@ -312,6 +325,8 @@ esc_status esc_group_insert_with_ids(esc_group* grp, int32_t graph, int64_t n, c
 esc_status esc_group_export_sizes(esc_group* grp, int32_t graph, int64_t* n_live, int64_t* n_incidences);
 esc_status esc_group_export(esc_group* grp, int32_t graph, int32_t* ids, int64_t* timestamps, int64_t* offsets,
                             int32_t* members, int64_t* v_offsets, int32_t* v_members);
+esc_status esc_group_export_h2h(esc_group* grp, int32_t graph, int32_t s, int64_t* n_entries, int64_t* offsets,
+                                int32_t* neighbours, int32_t* overlaps);
 
 esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window,
                             uint64_t* out, int32_t n_out);

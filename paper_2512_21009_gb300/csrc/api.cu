@@ -869,6 +869,50 @@ static esc_status export_graph(Engine* E, int32_t g, int64_t* n_live, int64_t* n
     return ESC_OK;
 }
 
+// The h2h mapping (line graph) of graph g, assembled on the host from a copy
+// of the store: for each live hyperedge in ascending ID order, the other live
+// hyperedges sharing at least s of its vertices, ascending, with the number
+// shared.  s = 1 gives the line graph, s > 1 the s-line graph.
+static esc_status export_h2h(Engine* E, int32_t g, int32_t s, int64_t* n_entries, int64_t* offsets,
+                             int32_t* neighbours, int32_t* overlaps) {
+    if (s < 1) return E->fail(ESC_ERR_INVALID_ARG, "s must be at least 1");
+    int64_t nl = 0, ni = 0;
+    esc_status st = export_graph(E, g, &nl, &ni, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st != ESC_OK) return st;
+    const size_t nvt = size_t(E->nv[g]);
+    std::vector<int32_t> ids(size_t(nl) + 1), mem(size_t(ni) + 1), vmem(size_t(ni) + 1);
+    std::vector<int64_t> off(size_t(nl) + 1), voff(nvt + 1);
+    st = export_graph(E, g, nullptr, nullptr, ids.data(), nullptr, off.data(), mem.data(), voff.data(), vmem.data());
+    if (st != ESC_OK) return st;
+    std::vector<int32_t> pos(size_t(E->ecap[g]), -1), cnt(size_t(nl), 0), touched;
+    for (int64_t k = 0; k < nl; ++k) pos[size_t(ids[k])] = int32_t(k);
+    int64_t q = 0;
+    if (offsets) offsets[0] = 0;
+    for (int64_t k = 0; k < nl; ++k) {
+        touched.clear();
+        for (int64_t j = off[k]; j < off[k + 1]; ++j) {
+            const int32_t x = mem[j];
+            for (int64_t e = voff[x]; e < voff[x + 1]; ++e) {
+                const int32_t p = pos[size_t(vmem[e])];
+                if (p == k) continue;
+                if (cnt[p]++ == 0) touched.push_back(p);
+            }
+        }
+        std::sort(touched.begin(), touched.end());
+        for (int32_t p : touched) {
+            if (cnt[p] >= s) {
+                if (neighbours) neighbours[q] = ids[p];
+                if (overlaps) overlaps[q] = cnt[p];
+                ++q;
+            }
+            cnt[p] = 0;
+        }
+        if (offsets) offsets[k + 1] = q;
+    }
+    if (n_entries) *n_entries = q;
+    return ESC_OK;
+}
+
 static esc_status read_counts(Engine* E, int32_t g, esc_triad_type type, int64_t window, uint64_t* out,
                               int32_t n_out) {
     if (g < 0 || g >= E->G || !out) return E->fail(ESC_ERR_INVALID_ARG, "bad graph or output");
@@ -1143,6 +1187,12 @@ esc_status esc_group_export(esc_group* grp, int32_t graph, int32_t* ids, int64_t
                              v_members);
 }
 
+esc_status esc_group_export_h2h(esc_group* grp, int32_t graph, int32_t s, int64_t* n_entries, int64_t* offsets,
+                                int32_t* neighbours, int32_t* overlaps) {
+    if (!grp) return ESC_ERR_INVALID_ARG;
+    return esc::export_h2h(grp->e, graph, s, n_entries, offsets, neighbours, overlaps);
+}
+
 esc_status esc_group_triads(esc_group* grp, int32_t graph, esc_triad_type type, int64_t window, uint64_t* out,
                             int32_t n_out) {
     if (!grp) return ESC_ERR_INVALID_ARG;
@@ -1305,6 +1355,12 @@ esc_status esc_export(esc_graph* g, int32_t* ids, int64_t* timestamps, int64_t* 
                       int64_t* v_offsets, int32_t* v_members) {
     if (!g) return ESC_ERR_INVALID_ARG;
     return esc::export_graph(g->e, 0, nullptr, nullptr, ids, timestamps, offsets, members, v_offsets, v_members);
+}
+
+esc_status esc_export_h2h(esc_graph* g, int32_t s, int64_t* n_entries, int64_t* offsets, int32_t* neighbours,
+                          int32_t* overlaps) {
+    if (!g) return ESC_ERR_INVALID_ARG;
+    return esc::export_h2h(g->e, 0, s, n_entries, offsets, neighbours, overlaps);
 }
 
 esc_status esc_insert_with_ids(esc_graph* g, int64_t n, const int32_t* ids, const int64_t* offsets,

@@ -39,7 +39,8 @@ EXPORTED = [
     "esc_server_triads", "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
     "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members", "esc_group_update_members",
     "esc_version", "esc_count_static_noalloc", "esc_insert_with_ids", "esc_restore",
-    "esc_group_insert_with_ids", "esc_group_export_sizes", "esc_group_export",
+    "esc_group_insert_with_ids", "esc_group_export_sizes", "esc_group_export", "esc_export_h2h",
+    "esc_group_export_h2h",
 ]
 
 
@@ -142,6 +143,8 @@ def load(path: str = LIB_PATH):
     L.esc_group_insert_with_ids.argtypes = [vp, i32, i64, vp, vp, vp, vp]
     L.esc_group_export_sizes.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(i64)]
     L.esc_group_export.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+    L.esc_export_h2h.argtypes = [vp, i32, C.POINTER(i64), vp, vp, vp]
+    L.esc_group_export_h2h.argtypes = [vp, i32, i32, C.POINTER(i64), vp, vp, vp]
     L.esc_version.restype = C.c_char_p
     L.esc_count_static_noalloc.argtypes = [i32, i64, vp, vp, vp, u32, i64, vp, vp]
     L.esc_count_static_noalloc.restype = st
@@ -153,7 +156,7 @@ def load(path: str = LIB_PATH):
                  "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
                  "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members",
                  "esc_group_update_members", "esc_insert_with_ids", "esc_restore", "esc_group_insert_with_ids",
-                 "esc_group_export_sizes", "esc_group_export"):
+                 "esc_group_export_sizes", "esc_group_export", "esc_export_h2h", "esc_group_export_h2h"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -265,6 +268,33 @@ def esc_group_export(grp: int, graph: int, n_vertices: int) -> dict:
     _check(rc, L.esc_group_last_error, grp)
     return dict(ids=ids[:n], timestamps=ts[:n], offsets=off, members=mem[:m], v_offsets=voff,
                 v_members=vmem[:m])
+
+
+def _h2h(call, err, handle, n_live: int, s: int) -> dict:
+    n = C.c_int64()
+    off = np.zeros(n_live + 1, np.int64)
+    _check(call(C.byref(n), off.ctypes.data, None, None), err, handle)
+    nbr = np.zeros(max(n.value, 1), np.int32)
+    ov = np.zeros(max(n.value, 1), np.int32)
+    _check(call(C.byref(n), off.ctypes.data, nbr.ctypes.data, ov.ctypes.data), err, handle)
+    return dict(offsets=off, neighbours=nbr[:n.value], overlaps=ov[:n.value])
+
+
+def esc_export_h2h(g: int, s: int = 1) -> dict:
+    """Line graph (s = 1) or s-line graph: per live hyperedge, in ascending
+    ID order, the hyperedges sharing at least s vertices and how many."""
+    L = load()
+    nl = C.c_int64()
+    _check(L.esc_export_sizes(g, C.byref(nl), None), L.esc_last_error, g)
+    return _h2h(lambda *a: L.esc_export_h2h(g, int(s), *a), L.esc_last_error, g, nl.value, s)
+
+
+def esc_group_export_h2h(grp: int, graph: int, s: int = 1) -> dict:
+    L = load()
+    nl = C.c_int64()
+    _check(L.esc_group_export_sizes(grp, int(graph), C.byref(nl), None), L.esc_group_last_error, grp)
+    return _h2h(lambda *a: L.esc_group_export_h2h(grp, int(graph), int(s), *a), L.esc_group_last_error, grp,
+                nl.value, s)
 
 
 def esc_insert_with_ids(g: int, ids, offsets, members, timestamps=None) -> None:
@@ -591,6 +621,9 @@ class Graph:
         self.h = esc_restore(self.cfg, checkpoint["ids"], checkpoint["offsets"], checkpoint["members"],
                              checkpoint.get("timestamps"), stream)
         return self
+
+    def export_h2h(self, s: int = 1) -> dict:
+        return esc_export_h2h(self.h, s)
 
     def insert_with_ids(self, ids, offsets, members, timestamps=None) -> None:
         esc_insert_with_ids(self.h, ids, offsets, members, timestamps)

@@ -161,3 +161,30 @@ def test_group_export_and_restore(E):
     finally:
         E.esc_group_destroy(grp)
         E.esc_group_destroy(grp2)
+
+
+@pytest.mark.parametrize("s_min", [1, 2])
+def test_h2h_export_is_the_line_graph(E, s_min):
+    import networkx as nx
+    s = gen.random_small(97, 90, 80, 2, 7, n_batches=2, n_ins=20, n_del=15)
+    g, og = run_stream(E, s, 1, 0, caps=caps_for(s.n_vertices, 200, 4000, 200, 4000))
+    ex = g.export_h2h(s_min)
+    ids = og.live_ids()
+    sets = {int(h): set(og.edge(int(h)).tolist()) for h in ids}
+    for k, h in enumerate(ids):
+        want = [(int(x), len(sets[int(h)] & sets[int(x)])) for x in ids
+                if x != h and len(sets[int(h)] & sets[int(x)]) >= s_min]
+        lo, hi = ex["offsets"][k], ex["offsets"][k + 1]
+        got = list(zip(ex["neighbours"][lo:hi].tolist(), ex["overlaps"][lo:hi].tolist()))
+        assert got == want, f"hyperedge {h}"
+    if s_min == 1:
+        # closed hyperedge triads (pairwise intersecting) are the line graph's triangles
+        L = nx.Graph()
+        L.add_nodes_from(ids.tolist())
+        for k, h in enumerate(ids):
+            for x in ex["neighbours"][ex["offsets"][k]:ex["offsets"][k + 1]]:
+                L.add_edge(int(h), int(x))
+        closed = O.tables()["static_closed"]
+        h_counts = g.triads(E.TRIAD_HYPEREDGE)
+        assert sum(int(h_counts[i]) for i in range(30) if closed[i]) == sum(nx.triangles(L).values()) // 3
+    g.close()

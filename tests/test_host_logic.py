@@ -42,3 +42,22 @@ def test_serving_generators_are_seeded_and_shaped():
     assert u.dtype == np.float32 and 0.0 <= u.min() and u.max() < 1.0
     t, g, s = gen.serving_arrivals(7, 10, 500, 100.0)
     assert np.all(np.diff(t) > 0) and g.max() < 10 and s.min() >= 10 and s.max() <= 10000
+
+
+def test_sweep_generators_are_seeded_and_shaped():
+    a = gen.spread_cardinalities(np.random.default_rng(0), 100_000, 4.0, 8.0, 4096)
+    b = gen.spread_cardinalities(np.random.default_rng(0), 100_000, 4.0, 8.0, 4096)
+    assert np.array_equal(a, b) and a.min() >= 2
+    assert abs(a.mean() - 4.0) < 0.1 and abs(a.std() - 8.0) < 0.8
+    assert np.all(gen.spread_cardinalities(np.random.default_rng(0), 50, 4.0, 0.0, 10) == 4)
+    d = gen.dyadic_graph(3, 40, 500)
+    assert np.array_equal(d.offsets, np.arange(501) * 2)
+    assert np.all(d.members[0::2] != d.members[1::2]) and d.members.max() < 40
+    for L in (gen.spread_inserts(4, 30, 2, 20, 4.0, 2.0, kmax=30), gen.insert_batches(5, 30, 2, 20, 12)):
+        for c in L:
+            assert c.n == 20 and np.all(np.diff(c.offsets) >= 2)
+            for i in range(c.n):
+                e = c.members[c.offsets[i]:c.offsets[i + 1]]
+                assert np.unique(e).size == e.size and e.max() < 30
+    h = gen.random_hypergraph(6, 300, 1000, 50)
+    assert h.n == 1000 and np.diff(h.offsets).max() <= 50 and np.all(np.diff(h.timestamps) > 0)
