@@ -579,9 +579,9 @@ def run_sweep(args):
     50K inserts with cardinality Zipf(2.0) capped at 50/100/200; these three
     share the uniform 1M-vertex graph of the default workload.  size: graphs
     of 20M-55M hyperedges (times --size-scale), |V| = |E|/3, cardinality
-    Zipf(2.0) in [2, --size-kmax], 50K updates (with the cap at 10,000 one
+    Zipf(2.0) in [2, --size-kmax] (default 1,000; at the paper's 10,000 one
     point at 1M hyperedges takes minutes: the largest hyperedges meet ~4e5
-    neighbours each).  spread: a dyadic graph (1M
+    neighbours each), 50K updates.  spread: a dyadic graph (1M
     vertices, 4M two-member hyperedges), 50K updates whose inserted
     cardinalities have mean 4 and standard deviation 0-16 (first point: plain
     edges), incident-vertex family."""
@@ -1071,7 +1071,7 @@ def main():
     ap.add_argument("--sweep", default="batch", choices=["batch", "delete", "card", "size", "spread"],
                     help="sweep workload: which parameter varies")
     ap.add_argument("--size-scale", type=float, default=0.05, help="size sweep: fraction of 20M-55M hyperedges")
-    ap.add_argument("--size-kmax", type=int, default=10_000, help="size sweep: cardinality cap")
+    ap.add_argument("--size-kmax", type=int, default=1000, help="size sweep: cardinality cap (the paper's: 10000)")
     ap.add_argument("--size-points", type=int, nargs="*", default=None,
                     help="size sweep: which of 20 30 40 55 (million hyperedges before --size-scale) to run")
     ap.add_argument("--graphs", type=int, default=None)
