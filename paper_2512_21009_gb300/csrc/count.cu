@@ -85,9 +85,13 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
     return x;
 }
 
-// bit of key k in the membership filter of a large N(h) (8 bits per table slot)
-__device__ __forceinline__ uint32_t filter_bit(int32_t k, uint32_t tcap) {
-    return fmix32(uint32_t(k) ^ 0x27d4eb2fu) & (8u * tcap - 1u);
+// word of key k in the membership filter of a large N(h), and its two bits
+// there: a blocked filter of 4 bits per table slot (tcap / 8 words) with both
+// of a key's bits in one word, so that a query is one load
+__device__ __forceinline__ uint32_t filter_word(int32_t k, uint32_t tcap, uint32_t& bits) {
+    const uint32_t x = fmix32(uint32_t(k) ^ 0x27d4eb2fu);
+    bits = (1u << (x & 31u)) | (1u << ((x >> 5) & 31u));
+    return (x >> 10) & (tcap / 8u - 1u);
 }
 
 // bit of key k in a shared-memory filter of N(g1) of w words (w a power of two)
@@ -400,10 +404,10 @@ __global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t 
             u = 0;
         }
         // list of up to u entries; a large N(h) also gets its hash table
-        // (2u rounded up to a power of two slots) and a one-hash membership
-        // filter of 8 bits per slot (a quarter of the slots, as words)
+        // (2u rounded up to a power of two slots) and a membership filter of
+        // 4 bits per slot (an eighth of the slots, as words)
         const long long t = u > big_nh ? (long long)pow2_at_least(2 * u) : 0;
-        sizes[i] = int32_t(u + t + t / 4);
+        sizes[i] = int32_t(u + t + t / 8);
     }
     }
 }
@@ -576,7 +580,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         const bool big = uh > cs.big_nh;
         uint32_t* const filt = reinterpret_cast<uint32_t*>(cs.nh_g + base + uh + cap);
         if (big)
-            for (uint32_t t = tid; t < cap / 4; t += NT_NH) filt[t] = 0;
+            for (uint32_t t = tid; t < cap / 8; t += NT_NH) filt[t] = 0;
         acc.n_h2v += (tid < kh) ? (kh - tid + NT_NH - 1) / NT_NH : 0;
         if (tid == 0) acc.n_alg += (unsigned long long)(uh + kh);
         for (int m0 = 0; m0 < kh; m0 += NT_NH) {
@@ -610,8 +614,9 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             cs.nh_xv[base + q] = (xvt & 0xffffffff00000000ull) | x | (uint64_t(kg) << 16) | (chg_g ? 1ull << 31 : 0ull);
             if (cs.nh_ts) cs.nh_ts[base + q] = S.h_ts[gg];
             if (big) {
-                const uint32_t fb = filter_bit(gg, cap);
-                atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+                uint32_t bits;
+                const uint32_t w = filter_word(gg, cap, bits);
+                atomicOr(&filt[w], bits);
             }
             if (gg < h && chg_g) continue;  // pair attributed elsewhere
             if (atomicAdd(&cs.lcnt[gg], 1) == 0) cs.d_list[atomicAdd(&A.sc->n_d[A.side], 1)] = gg;
@@ -1266,10 +1271,10 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                             // most g2 are not in N(h): the filter answers them
                             // with one load; the rest probe the table
                             const uint32_t tcap = uint32_t(s.htcap[l]);
-                            const uint32_t fb = filter_bit(g2, tcap);
-                            const uint32_t fw =
-                                reinterpret_cast<const uint32_t*>(cs.nh_g + s.htoff[l] + tcap)[fb >> 5];
-                            const int ps = ((fw >> (fb & 31)) & 1u)
+                            uint32_t bits;
+                            const uint32_t fw = reinterpret_cast<const uint32_t*>(
+                                cs.nh_g + s.htoff[l] + tcap)[filter_word(g2, tcap, bits)];
+                            const int ps = (fw & bits) == bits
                                                ? probe_list_table(cs.nh_g + s.htoff[l], tcap - 1, g2)
                                                : -1;
                             if (ps >= 0) {
@@ -1851,7 +1856,7 @@ __global__ void k_pre_sizes(Store S, Call C, int32_t* sizes, int64_t max_u, int6
         if (lane == 0) {
             if (u > max_u) u = 0;  // the ingest check reports it
             const long long t = u > big_nh ? (long long)pow2_at_least(2 * u) : 0;
-            sizes[j] = int32_t(u + t + t / 4);
+            sizes[j] = int32_t(u + t + t / 8);
         }
     }
 }
