@@ -73,3 +73,50 @@ def test_full_size_batches(E):
     assert np.array_equal(loc["hyperedge"], h30)
     assert int(h30.sum()) > 0
     g.close()
+
+
+def test_full_size_temporal_stream(E):
+    """The temporal stream at full size (4M hyperedges over 2M vertices in
+    batches of 2^16, each batch deleting every live hyperedge older than
+    T - delta): IDs after every batch, the store at the end, the running
+    temporal counts against a full recount, and sampled enumerations by
+    the oracle."""
+    ts = gen.temporal(seed=3, scale=1.0)
+    delta = ts.delta
+    n_total = sum(b.n for b in ts.batches)
+    bmax = max(b.n for b in ts.batches)
+    g = E.Graph(ts.n_vertices, None, None, None, capacity_hyperedges=n_total + 64,
+                capacity_incidences=sum(b.nnz for b in ts.batches) + 1024, max_batch_hyperedges=4 * bmax,
+                max_batch_incidences=max(b.nnz for b in ts.batches) + 1024, families=4, delta=delta)
+    og = OracleHypergraph(ts.n_vertices)
+    # each side keeps its own live list in insertion order (timestamps grow
+    # along the stream, so a batch's expirations are a prefix of it)
+    o_ids, o_ts = np.zeros(0, np.int64), np.zeros(0, np.int64)
+    g_ids, g_ts = np.zeros(0, np.int64), np.zeros(0, np.int64)
+    n_exp_total = 0
+    for k, b in enumerate(ts.batches):
+        t_cut = int(b.timestamps.max()) - delta
+        ne_o = int(np.searchsorted(o_ts, t_cut, side="left"))
+        ne_g = int(np.searchsorted(g_ts, t_cut, side="left"))
+        want = og.apply_batch(b.offsets, b.members, b.timestamps, np.sort(o_ids[:ne_o]))
+        got = g.apply_batch(b.offsets, b.members, b.timestamps, np.sort(g_ids[:ne_g]).astype(np.int32))
+        assert np.array_equal(got, want), f"batch {k}: assigned IDs differ"
+        o_ids, o_ts = np.concatenate([o_ids[ne_o:], want]), np.concatenate([o_ts[ne_o:], b.timestamps])
+        g_ids, g_ts = np.concatenate([g_ids[ne_g:], got]), np.concatenate([g_ts[ne_g:], b.timestamps])
+        n_exp_total += ne_o
+    assert n_exp_total > 0  # the window filled and hyperedges expired
+    ex = g.export()
+    off, mem, tsv, ids = og.csr()
+    assert np.array_equal(ex["ids"], ids)
+    assert np.array_equal(ex["offsets"], off)
+    assert np.array_equal(ex["members"], mem)
+    assert np.array_equal(ex["timestamps"], tsv)
+    running = g.triads(E.TRIAD_TEMPORAL)
+    full = g.local_triads(ids.astype(np.int32))["temporal"]
+    assert np.array_equal(running, full)
+    rng = np.random.default_rng(23)
+    sel = np.sort(rng.choice(ids.size, size=3, replace=False))
+    _, t96 = O.count_containing(off, mem, tsv, ids, delta, O.FAM_TEMPORAL, sel)
+    assert np.array_equal(g.local_triads(ids[sel].astype(np.int32))["temporal"], t96)
+    assert int(t96.sum()) > 0
+    g.close()
