@@ -119,6 +119,30 @@ class OracleHypergraph:
         for hid, s in zip(ids, new_sets):
             self.members[int(hid)] = s
 
+    @classmethod
+    def from_checkpoint(cls, n_vertices: int, ids, offsets, members, timestamps=None) -> "OracleHypergraph":
+        """The live hyperedges of a checkpoint placed under their IDs; every
+        other ID below the largest one + 1 is free.  Under the ID rule above
+        this hands later inserts the IDs the checkpointed graph would: its
+        free IDs between the largest live one and its own high-water mark
+        come next in ascending order either way."""
+        g = cls(n_vertices)
+        ids = np.asarray(ids, dtype=np.int64)
+        offsets = np.asarray(offsets, dtype=np.int64)
+        members = np.asarray(members, dtype=np.int64)
+        if np.unique(ids).size != ids.size or (ids.size and ids.min() < 0):
+            raise ValueError("bad checkpoint IDs")
+        hw = int(ids.max()) + 1 if ids.size else 0
+        g.members = [None] * hw
+        g.ts = [None] * hw
+        for j, hid in enumerate(ids):
+            e = np.unique(members[offsets[j]:offsets[j + 1]])
+            if e.size == 0 or e[0] < 0 or e[-1] >= g.n_vertices:
+                raise ValueError("bad checkpoint hyperedge")
+            g.members[int(hid)] = e.astype(np.int32)
+            g.ts[int(hid)] = int(timestamps[j]) if timestamps is not None else 0
+        return g
+
     # ------------------------------------------------------------------ views
     def csr(self):
         """Live hyperedges in ascending ID order: (offsets, members, ts, ids)."""

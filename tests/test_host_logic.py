@@ -61,3 +61,36 @@ def test_sweep_generators_are_seeded_and_shaped():
                 assert np.unique(e).size == e.size and e.max() < 30
     h = gen.random_hypergraph(6, 300, 1000, 50)
     assert h.n == 1000 and np.diff(h.offsets).max() <= 50 and np.all(np.diff(h.timestamps) > 0)
+
+
+def test_restored_oracle_graph_hands_out_the_same_ids():
+    """A graph rebuilt from its live hyperedges alone (the largest live ID +
+    1 as its high-water mark) gives later inserts the same IDs as the graph
+    it was taken from, also after its largest IDs were deleted."""
+    rng = np.random.default_rng(5)
+    nv = 40
+    og = OracleHypergraph(nv)
+    for step in range(60):
+        live = og.live_ids()
+        nd = int(rng.integers(0, min(6, live.size) + 1))
+        dels = rng.choice(live, size=nd, replace=False) if nd else np.zeros(0, np.int64)
+        if step % 7 == 3 and live.size > 3:  # delete the top IDs: holes above the largest live one
+            dels = np.union1d(dels, live[-3:])
+        ni = int(rng.integers(0, 8))
+        off = np.arange(ni + 1, dtype=np.int64) * 3
+        og.apply_batch(off, rng.integers(0, nv, size=3 * ni), np.full(ni, step, np.int64), dels)
+        if step % 10 == 9:
+            off_c, mem_c, ts_c, ids_c = og.csr()
+            r = OracleHypergraph.from_checkpoint(nv, ids_c, off_c, mem_c, ts_c)
+            assert r.high_water <= og.high_water
+            for _ in range(3):
+                live = og.live_ids()
+                dels = rng.choice(live, size=min(2, live.size), replace=False)
+                ni = int(rng.integers(1, 12))
+                off = np.arange(ni + 1, dtype=np.int64) * 2
+                mem = rng.integers(0, nv, size=2 * ni)
+                a = og.apply_batch(off, mem, np.zeros(ni, np.int64), dels)
+                b = r.apply_batch(off, mem, np.zeros(ni, np.int64), dels)
+                assert np.array_equal(a, b)
+            for x, y in zip(og.csr(), r.csr()):
+                assert np.array_equal(x, y)
