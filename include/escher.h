@@ -213,7 +213,9 @@ esc_status esc_export_sizes(esc_graph* g, int64_t* n_live, int64_t* n_incidences
  * for every vertex, v_offsets int64[n_vertices+1] and v_members
  * int32[n_incidences] holding the IDs of the hyperedges that contain it, in
  * ascending order.  Any pointer may be NULL to skip that part.  Meant for
- * tests and checkpoints (Table II: the h2v and v2h views). */
+ * tests and checkpoints (Table II: the h2v and v2h views); esc_restore
+ * rebuilds a graph from the ids, timestamps, offsets and members arrays.
+ * Errors: INVALID_ARG, CUDA. */
 esc_status esc_export(esc_graph* g, int32_t* ids, int64_t* timestamps, int64_t* offsets,
                       int32_t* members, int64_t* v_offsets, int32_t* v_members);
 
