@@ -414,3 +414,35 @@ def test_autotune_keeps_counts_exact(E, families):
         assert_counts_equal(g.counts(), O.counts(og, families, delta), "after a batch")
     with pytest.raises(E.EscError):
         g.autotune(np.array([10 ** 6], np.int32))
+
+
+def test_maximum_cardinality(E):
+    """A hyperedge of exactly the largest accepted size (16,384 members)
+    among small ones; one member more is rejected with nothing changed; a
+    16,384-member input with every vertex twice collapses to 8,192."""
+    nv = 20000
+    fam = 5  # hyperedge + temporal (the oracle's vertex counter enumerates vertex triples)
+    rng = np.random.default_rng(31)
+    sets = [rng.permutation(nv)[:16384]] + [rng.choice(nv, size=int(rng.integers(2, 6)), replace=False)
+                                           for _ in range(300)]
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in sets])
+    mem = np.concatenate(sets).astype(np.int32)
+    ts = np.arange(len(sets), dtype=np.int64) * 3
+    delta = 400
+    og = OracleHypergraph(nv, off, mem, ts)
+    g = E.Graph(nv, off, mem, ts, families=fam, delta=delta, **caps_for(nv, 1000, 60000, 400, 40000))
+    assert_counts_equal(g.counts(), O.counts(og, fam, delta), "initial")
+    before = g.counts()
+    with pytest.raises(E.EscError) as ei:
+        g.apply_batch(np.array([0, 16385], np.int64), rng.permutation(nv)[:16385].astype(np.int32),
+                      np.array([999], np.int64), None)
+    assert ei.value.status == 4
+    assert_counts_equal(g.counts(), before, "after the rejected batch")
+    twice = np.repeat(rng.permutation(nv)[:8192], 2).astype(np.int32)
+    want = og.apply_batch(np.array([0, 16384], np.int64), twice, np.array([1000], np.int64), np.array([0]))
+    got = g.apply_batch(np.array([0, 16384], np.int64), twice, np.array([1000], np.int64), np.array([0], np.int32))
+    assert np.array_equal(got, want)
+    assert_counts_equal(g.counts(), O.counts(og, fam, delta), "after the big replacement")
+    assert_store_equal(g, og)
+    g.close()
