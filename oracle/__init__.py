@@ -16,6 +16,13 @@ Parity status of each function (what pins it, besides the GPU comparison):
                                fold onto the static classes.
 * count_containing          -- pinned: equals brute(after) - brute(before) for
                                single-batch edits (incremental = recount).
+* count_vertex_containing   -- pinned: per-triple form equals the literal
+                               assignment enumeration restricted to
+                               assignments with a selected witness; the
+                               incremental identity count_vertex(after) -
+                               count_vertex(before) = containing(after,
+                               inserted) - containing(before, deleted); all
+                               selected = count_vertex; none selected = 0.
 * count_vertex              -- pinned: literal assignment enumeration vs the
                                per-triple closed form; type 1 = sum C(|h|,3);
                                total = trace(M^3)/6 of the co-membership

@@ -660,3 +660,161 @@ int orc_vertex_triples(int64_t n, const int64_t* off, const int32_t* mem, uint64
     free_v2h(&V);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* incident-vertex instances with at least one selected witness              */
+/* ------------------------------------------------------------------------ */
+
+/* Literal (tiny inputs): as orc_vertex_literal, but an assignment (a, b, c)
+ * of witnesses to the pairs uv, vw, uw counts only when at least one of a, b,
+ * c is selected (sel[position] != 0).  With every hyperedge selected this is
+ * orc_vertex_literal itself. */
+int orc_vertex_literal_containing(int64_t n, const int64_t* off, const int32_t* mem, int32_t n_vertices,
+                                  const uint8_t* sel, uint64_t* v3) {
+    int rc = check_csr(n, off, mem);
+    if (rc) return rc;
+    if (!sel && n > 0) return ORC_ERR_INPUT;
+    memset(v3, 0, 3 * sizeof(uint64_t));
+    int64_t *Luv = malloc(sizeof(int64_t) * (size_t)(n + 1)), *Lvw = malloc(sizeof(int64_t) * (size_t)(n + 1)),
+            *Luw = malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!Luv || !Lvw || !Luw) return ORC_ERR_NOMEM;
+    for (int32_t u = 0; u < n_vertices && !rc; ++u)
+        for (int32_t v = u + 1; v < n_vertices && !rc; ++v)
+            for (int32_t w = v + 1; w < n_vertices && !rc; ++w) {
+                int64_t nuv = 0, nvw = 0, nuw = 0;
+                for (int64_t h = 0; h < n; ++h) {
+                    int hu = contains(EDGE(h), u), hv = contains(EDGE(h), v), hw = contains(EDGE(h), w);
+                    if (hu && hv) Luv[nuv++] = h;
+                    if (hv && hw) Lvw[nvw++] = h;
+                    if (hu && hw) Luw[nuw++] = h;
+                }
+                for (int64_t i = 0; i < nuv; ++i)
+                    for (int64_t j = 0; j < nvw; ++j)
+                        for (int64_t k = 0; k < nuw; ++k) {
+                            int64_t a = Luv[i], b = Lvw[j], c = Luw[k];
+                            if (!sel[a] && !sel[b] && !sel[c]) continue;
+                            int distinct = 1 + (b != a) + (c != a && c != b);
+                            rc |= add_u64(&v3[distinct - 1], 1);
+                        }
+            }
+    free(Luv); free(Lvw); free(Luw);
+    return rc;
+}
+
+/* Common members of two ascending position lists: all of them (*all) and
+ * those at unselected positions (*unsel). */
+static void isect2_sel(const int64_t* a, int64_t na, const int64_t* b, int64_t nb, const uint8_t* sel,
+                       uint64_t* all, uint64_t* unsel) {
+    int64_t i = 0, j = 0;
+    *all = *unsel = 0;
+    while (i < na && j < nb) {
+        if (a[i] < b[j]) ++i;
+        else if (a[i] > b[j]) ++j;
+        else {
+            ++*all;
+            if (!sel[a[i]]) ++*unsel;
+            ++i;
+            ++j;
+        }
+    }
+}
+
+static void isect3_sel(const int64_t* a, int64_t na, const int64_t* b, int64_t nb, const int64_t* c, int64_t nc,
+                       const uint8_t* sel, uint64_t* all, uint64_t* unsel) {
+    int64_t i = 0, j = 0, k = 0;
+    *all = *unsel = 0;
+    while (i < na && j < nb && k < nc) {
+        int64_t m = a[i];
+        if (b[j] > m) m = b[j];
+        if (c[k] > m) m = c[k];
+        while (i < na && a[i] < m) ++i;
+        while (j < nb && b[j] < m) ++j;
+        while (k < nc && c[k] < m) ++k;
+        if (i < na && j < nb && k < nc && a[i] == m && b[j] == m && c[k] == m) {
+            ++*all;
+            if (!sel[m]) ++*unsel;
+            ++i;
+            ++j;
+            ++k;
+        }
+    }
+}
+
+/* The three type counts of one vertex triple from its pair multiplicities
+ * m_uv, m_vw, m_uw and its triple multiplicity m_uvw (see
+ * orc_vertex_triples): type 1 = m_uvw, type 2 = m_uvw (m_uv + m_vw + m_uw - 3),
+ * type 3 = the remaining m_uv m_vw m_uw.  Computed in 128 bits. */
+static void triple_types(uint64_t muv, uint64_t mvw, uint64_t muw, uint64_t muvw, unsigned __int128 t[3]) {
+    unsigned __int128 total = (unsigned __int128)muv * mvw * muw;
+    t[0] = muvw;
+    t[1] = muvw ? (unsigned __int128)muvw * (muv + mvw + muw - 3) : 0;
+    t[2] = total - t[0] - t[1];
+}
+
+/* Per vertex triple (large graphs, small selections).  An instance has at
+ * least one selected witness unless all three of its witnesses are
+ * unselected, and the instances with only unselected witnesses are exactly
+ * those of the hypergraph without the selected hyperedges.  So, per triple,
+ * each type's count here is its value over all hyperedges minus its value
+ * with the multiplicities counted among unselected hyperedges only.  Only a
+ * triple with a pair inside a selected hyperedge s can give a difference;
+ * those triples are listed from every pair {u, v} of s and every co-member w
+ * of u, then sorted and deduplicated.  Cost grows as the sum over selected s
+ * of |s|^2 times the co-membership degree. */
+int orc_vertex_containing(int64_t n, const int64_t* off, const int32_t* mem, int64_t n_sel,
+                          const int64_t* sel_pos, uint64_t* v3) {
+    int rc = check_csr(n, off, mem);
+    if (rc) return rc;
+    memset(v3, 0, 3 * sizeof(uint64_t));
+    uint8_t* sel = calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!sel) return ORC_ERR_NOMEM;
+    for (int64_t s = 0; s < n_sel; ++s) {
+        if (sel_pos[s] < 0 || sel_pos[s] >= n) { free(sel); return ORC_ERR_INPUT; }
+        sel[sel_pos[s]] = 1;
+    }
+    v2h_t V;
+    rc = build_v2h(n, off, mem, &V);
+    if (rc) { free(sel); return rc; }
+    trip* buf = NULL;
+    int64_t len = 0, cap = 0;
+    for (int64_t s = 0; s < n_sel && !rc; ++s) {
+        const int64_t h = sel_pos[s];
+        for (int64_t p = off[h]; p < off[h + 1] && !rc; ++p)
+            for (int64_t q = p + 1; q < off[h + 1] && !rc; ++q) {
+                const int64_t u = mem[p], v = mem[q];
+                for (int64_t e = V.voff[u]; e < V.voff[u + 1] && !rc; ++e) {
+                    const int64_t f = V.vh[e];
+                    for (int64_t r = off[f]; r < off[f + 1] && !rc; ++r) {
+                        const int64_t w = mem[r];
+                        if (w == u || w == v) continue;
+                        rc = push_trip(&buf, &len, &cap, u, v, w);
+                    }
+                }
+            }
+    }
+    if (!rc) qsort(buf, (size_t)len, sizeof(trip), cmp_trip);
+    for (int64_t i = 0; i < len && !rc; ++i) {
+        if (i > 0 && cmp_trip(&buf[i], &buf[i - 1]) == 0) continue;
+        const int64_t u = buf[i].x, v = buf[i].y, w = buf[i].z;
+        const int64_t *Eu = V.vh + V.voff[u], *Ev = V.vh + V.voff[v], *Ew = V.vh + V.voff[w];
+        const int64_t du = V.voff[u + 1] - V.voff[u], dv = V.voff[v + 1] - V.voff[v],
+                      dw = V.voff[w + 1] - V.voff[w];
+        uint64_t muv, muv0, mvw, mvw0, muw, muw0, muvw, muvw0;
+        isect2_sel(Eu, du, Ev, dv, sel, &muv, &muv0);
+        isect2_sel(Ev, dv, Ew, dw, sel, &mvw, &mvw0);
+        isect2_sel(Eu, du, Ew, dw, sel, &muw, &muw0);
+        isect3_sel(Eu, du, Ev, dv, Ew, dw, sel, &muvw, &muvw0);
+        unsigned __int128 all[3], rest[3];
+        triple_types(muv, mvw, muw, muvw, all);
+        triple_types(muv0, mvw0, muw0, muvw0, rest);
+        for (int t = 0; t < 3 && !rc; ++t) {
+            const unsigned __int128 d = all[t] - rest[t];
+            if (d >> 64) rc = ORC_ERR_OVERFLOW;
+            else rc |= add_u64(&v3[t], (uint64_t)d);
+        }
+    }
+    free(buf);
+    free_v2h(&V);
+    free(sel);
+    return rc;
+}

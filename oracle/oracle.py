@@ -63,6 +63,10 @@ def lib():
         L.orc_vertex_literal.argtypes = [C.c_int64, p64, p32, C.c_int32, pu64]
         L.orc_vertex_triples.restype = C.c_int
         L.orc_vertex_triples.argtypes = [C.c_int64, p64, p32, pu64]
+        L.orc_vertex_literal_containing.restype = C.c_int
+        L.orc_vertex_literal_containing.argtypes = [C.c_int64, p64, p32, C.c_int32, C.POINTER(C.c_uint8), pu64]
+        L.orc_vertex_containing.restype = C.c_int
+        L.orc_vertex_containing.argtypes = [C.c_int64, p64, p32, C.c_int64, p64, pu64]
         _lib = L
     return _lib
 
@@ -149,6 +153,25 @@ def count_vertex(off, mem, n_vertices: Optional[int] = None, method: str = "trip
     else:
         _check(lib().orc_vertex_triples(n, _ptr(off, C.c_int64), _ptr(mem, C.c_int32),
                                         _ptr(v3, C.c_uint64)))
+    return v3
+
+
+def count_vertex_containing(off, mem, sel_pos: Sequence[int], n_vertices: Optional[int] = None,
+                            method: str = "triples"):
+    """uint64[3]: incident-vertex instances (types 1, 2, 3) with at least one
+    witness among the hyperedges at the given positions of the CSR."""
+    n, off, mem, _, _ = _prep(off, mem, None, None)
+    v3 = np.zeros(3, np.uint64)
+    if method == "literal":
+        sel = np.zeros(max(n, 1), np.uint8)
+        sel[np.asarray(sel_pos, dtype=np.int64)] = 1
+        _check(lib().orc_vertex_literal_containing(n, _ptr(off, C.c_int64), _ptr(mem, C.c_int32),
+                                                   int(n_vertices), _ptr(sel, C.c_uint8),
+                                                   _ptr(v3, C.c_uint64)))
+    else:
+        sp = np.ascontiguousarray(sel_pos, dtype=np.int64)
+        _check(lib().orc_vertex_containing(n, _ptr(off, C.c_int64), _ptr(mem, C.c_int32), sp.size,
+                                           _ptr(sp, C.c_int64), _ptr(v3, C.c_uint64)))
     return v3
 
 

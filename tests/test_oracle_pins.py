@@ -459,3 +459,59 @@ def test_horizontal_update_counts_as_delete_and_insert():
     a.update_members(np.array([4]), np.array([0, old.size]), old)
     back = O.counts(a, 3, 0)
     assert np.array_equal(back["hyperedge"], before["hyperedge"]) and np.array_equal(back["vertex"], before["vertex"])
+
+
+# ---------------------------------------------------------------------------
+# incident-vertex instances holding a selected witness (Alg. 3 for the
+# vertex family: the count change of a batch is the instances holding an
+# inserted hyperedge on the new graph minus those holding a deleted one on
+# the old graph)
+# ---------------------------------------------------------------------------
+
+def test_vertex_containing_hand_case():
+    # A = {0,1,2}, B = {0,1}, C = {1,2}.  Triple {0,1,2}: pair 01 has
+    # witnesses A, B; pair 12 has A, C; pair 02 has A.  The four assignments
+    # (01, 12, 02) are (A,A,A) type 1, (A,C,A) and (B,A,A) type 2, (B,C,A)
+    # type 3.  Those holding B: (B,A,A), (B,C,A).  Those holding C: (A,C,A),
+    # (B,C,A).  Every assignment holds A.
+    off, mem = csr_of([[0, 1, 2], [0, 1], [1, 2]])
+    assert O.count_vertex(off, mem, 3, "literal").tolist() == [1, 2, 1]
+    for method in ("literal", "triples"):
+        assert O.count_vertex_containing(off, mem, [1], 3, method).tolist() == [0, 1, 1], method
+        assert O.count_vertex_containing(off, mem, [2], 3, method).tolist() == [0, 1, 1], method
+        assert O.count_vertex_containing(off, mem, [0], 3, method).tolist() == [1, 2, 1], method
+        assert O.count_vertex_containing(off, mem, [1, 2], 3, method).tolist() == [0, 2, 1], method
+        assert O.count_vertex_containing(off, mem, [], 3, method).tolist() == [0, 0, 0], method
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_vertex_containing_per_triple_equals_literal(seed):
+    E = _random_edges(40 + seed, 11, 10, 1, 6, dup_frac=0.2)
+    off, mem = csr_of(E)
+    rng = np.random.default_rng(seed)
+    for k in (1, 2, 4):
+        sel = np.sort(rng.choice(len(E), size=k, replace=False))
+        lit = O.count_vertex_containing(off, mem, sel, 11, "literal")
+        tri = O.count_vertex_containing(off, mem, sel, 11, "triples")
+        assert np.array_equal(lit, tri), (k, lit, tri)
+    every = np.arange(len(E))
+    assert np.array_equal(O.count_vertex_containing(off, mem, every, 11, "triples"),
+                          O.count_vertex(off, mem, 11, "literal"))
+
+
+def test_vertex_containing_gives_the_incremental_change():
+    s = gen.random_small(31, 260, 200, 2, 8, n_batches=3, n_ins=20, n_del=20)
+    g = OracleHypergraph(s.n_vertices, s.initial.offsets, s.initial.members)
+    before = [int(x) for x in O.count_vertex(*g.csr()[:2])]
+    moved = 0
+    for b in s.batches:
+        off0, mem0, _, ids0 = g.csr()
+        dels, new_ids = _apply(g, b)
+        off1, mem1, _, ids1 = g.csr()
+        d = O.count_vertex_containing(off0, mem0, np.searchsorted(ids0, dels))
+        i = O.count_vertex_containing(off1, mem1, np.searchsorted(ids1, new_ids))
+        after = [int(x) for x in O.count_vertex(off1, mem1)]
+        assert after == [before[t] - int(d[t]) + int(i[t]) for t in range(3)]
+        moved += int(d.sum()) + int(i.sum())
+        before = after
+    assert moved > 0
