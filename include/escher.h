@@ -405,9 +405,9 @@ esc_status esc_server_get_stats(esc_server* srv, esc_server_stats* out);
 esc_status esc_server_destroy(esc_server* srv);
 
 /* Allocation-free counting.  The paper has no counterpart of this call; it
- * exists for callers that cannot allocate device memory -- code running
- * while a stream is captured into a CUDA graph, code confined to a memory
- * budget handed out by its own allocator -- and so cannot use esc_create.
+ * exists for callers that cannot allocate device memory -- code confined to a
+ * memory budget handed out by its own allocator, or code whose allocator must
+ * not be re-entered -- and so cannot use esc_create.
  *
  * Counts every triad of one static hypergraph: n_he hyperedges in CSR form
  * (offsets int64[n_he+1] with offsets[0] == 0; members int32[offsets[n_he]],
@@ -415,16 +415,17 @@ esc_status esc_server_destroy(esc_server* srv);
  * [0, n_vertices)); timestamps int64[n_he] or NULL (all zero).  families and
  * delta as in esc_config.  out_counts receives uint64[129]: 30 hyperedge
  * classes, then the 3 vertex types, then the 96 temporal classes (families
- * not asked for read 0).  Hyperedge i has ID i.  Every pointer must be
- * device memory of the current device; the call runs on cuda_stream and
- * returns once out_counts is written.
+ * not asked for read 0, and all 129 read 0 after an error).  Hyperedge i
+ * has ID i.  Every pointer must be device memory of the current device; the
+ * call runs on cuda_stream, synchronises it (it reads the member count and
+ * its status back) and returns once out_counts is written.
  *
  * It calls no cudaMalloc or cudaFree: its temporary buffers live in one
  * fixed array of device memory (80 MiB) that every GPU which loads the
  * library holds until the process exits.  The first call on a device looks
- * up that array's device address; make it before any stream capture.  All
- * calls share the array and every call resets what it needs, so calls whose
- * GPU work overlaps race on it: serialise them.
+ * up that array's device address.  All calls share the array and every call
+ * resets what it needs, so calls whose GPU work overlaps race on it:
+ * serialise them.
  *
  * Limits: n_he <= 262,144; offsets[n_he] <= 2,097,152; n_vertices <=
  * 524,288; each hyperedge at most ESC_MAX_CARDINALITY members; for every

@@ -47,6 +47,7 @@
 // (a vertex in each pairwise intersection, all three distinct).
 #include <algorithm>
 #include <climits>
+#include <mutex>
 #include <vector>
 
 #include "escher_internal.cuh"
@@ -563,6 +564,20 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         // a neighbourhood too large for the block's tables is built in place,
         // in the table part of its own list region (see k_nh_size)
         const bool huge = cap > A.nh_smem_cap && (int64_t)cap > gs;
+        const bool big = uh > cs.big_nh;
+        // the list region k_nh_size reserved must hold what is written below
+        // (it reserves nothing for a hyperedge over the size limit, which it
+        // reports); a hyperedge that does not fit is skipped, never written
+        if (uh + ((big || huge) ? (long long)cap + cap / 8 : 0) > cs.nh_off[i + 1] - cs.nh_off[i]) {
+            if (tid == 0) {
+                set_error(A.sc, kErrUnsupported, -12, h, uh);
+                cs.nh_n[i] = 0;
+                cs.nh_toff[i] = 0;
+                cs.nh_tcap[i] = 0;
+                cs.r_off[i] = -1;
+            }
+            continue;
+        }
         uint64_t* const xv_t = cs.nh_xv + base + uh;
         if (cap <= A.nh_smem_cap) {
             NH = Tab{s.keys, s.vals, s.aux, s.list, &s.n_list, cap - 1, NH_S / 2};
@@ -577,7 +592,6 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
             }
             __syncthreads();
         }
-        const bool big = uh > cs.big_nh;
         uint32_t* const filt = reinterpret_cast<uint32_t*>(cs.nh_g + base + uh + cap);
         if (big)
             for (uint32_t t = tid; t < cap / 8; t += NT_NH) filt[t] = 0;
@@ -1681,17 +1695,19 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
 
 cudaError_t upload_tables(cudaStream_t st) {
     static ClassTables t;
-    static bool built = false;
-    if (!built) {
-        build_class_tables(&t);
-        built = true;
-    }
+    static std::once_flag built;
+    std::call_once(built, [] { build_class_tables(&t); });
     return cudaMemcpyToSymbolAsync(c_tables, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st);
 }
 
+// The centre and neighbourhood kernels' shared-memory limits, raised once per
+// device (function attributes belong to the device they are set on).
 void count_prepare() {
-    static bool done = false;
-    if (done) return;
+    constexpr int kDev = 64;
+    static std::once_flag once[kDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) dev = 0;
+    std::call_once(once[dev], [] {
     cudaFuncSetAttribute(k_nh_build, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemNH)));
     cudaFuncSetAttribute(k_center<512, 8192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(SmemC<512, 8192>)));
@@ -1701,7 +1717,7 @@ void count_prepare() {
                          int(sizeof(SmemC<512, 4096>)));
     cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(SmemC<256, 2048>)));
-    done = true;
+    });
 }
 
 // One count run: the changed hyperedges [lo, lo + n) (host-planned), or the

@@ -1,21 +1,24 @@
 // noalloc.cu -- esc_count_static_noalloc: triad counts of a static hypergraph
 // computed without allocating any memory.
 //
-// Some callers cannot call cudaMalloc: code running while a stream is being
-// captured into a CUDA graph, code that owns a fixed memory budget handed out
-// by its own allocator, or code in a process whose allocator must not be
-// re-entered.  This entry point serves them.  The caller passes the inputs
-// and the output; every temporary buffer (vertex->hyperedge lists, work
-// lists, counter hash tables, status words) lives in one file-scope device
-// array of fixed size, kNoAllocBytes, that every GPU which loads this library
-// holds until the process exits.
+// Some callers cannot call cudaMalloc: code that owns a fixed memory budget
+// handed out by its own allocator, or code in a process whose allocator must
+// not be re-entered.  This entry point serves them.  The caller passes the
+// inputs and the output; every temporary buffer (vertex->hyperedge lists,
+// work lists, counter hash tables, status words) lives in one file-scope
+// device array of fixed size, kNoAllocBytes, that every GPU which loads this
+// library holds until the process exits.
+//
+// The call synchronises the stream it is given (it reads the member count and
+// the status back to the host), so it returns only when the counts are
+// written.
 //
 // The device address of that array is looked up once per device with
 // cudaGetSymbolAddress, with the device current, on the first call made on
-// that device; make that first call before any stream capture.  All calls
-// share the array and it keeps the last call's contents, so each call clears
-// what must start at zero; calls whose GPU work overlaps (two streams, two
-// host threads) race on it and must be serialised by the caller.
+// that device.  All calls share the array and it keeps the last call's
+// contents, so each call clears what must start at zero; calls whose GPU work
+// overlaps (two streams, two host threads) race on it and must be serialised
+// by the caller.
 #include <mutex>
 
 #include "escher.h"
@@ -79,16 +82,23 @@ Layout layout() {
     return L;
 }
 
-// Check every hyperedge (non-empty, at most kMaxCard members, members sorted
-// ascending without repeats and inside [0, n_vertices)), record its size and
-// count vertex degrees.
-__global__ void k_na_check(const int64_t* off, const int32_t* mem, int64_t n, int32_t nv, int32_t* card,
-                           int32_t* changed, int32_t* vdeg, Scalars* sc) {
+// Check every hyperedge (its offsets inside [0, nnz] and not decreasing,
+// non-empty, at most kMaxCard members, members sorted ascending without
+// repeats and inside [0, n_vertices)), record its size and count vertex
+// degrees.  Members are read only once the offsets are known to lie inside
+// the member array.
+__global__ void k_na_check(const int64_t* off, const int32_t* mem, int64_t n, int64_t nnz, int32_t nv,
+                           int32_t* card, int32_t* changed, int32_t* vdeg, Scalars* sc) {
     int64_t h = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (h >= n) return;
     int64_t a = off[h], b = off[h + 1];
     int64_t k = b - a;
     changed[h] = int32_t(h);
+    if (a < 0 || b < a || b > nnz) {
+        set_error(sc, kErrInvalid, -1, h, b);
+        card[h] = 0;
+        return;
+    }
     if (k < 1 || k > kMaxCard) {
         set_error(sc, k < 1 ? kErrInvalid : kErrUnsupported, -1, h, k);
         card[h] = 0;
@@ -231,7 +241,7 @@ extern "C" esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he,
     LaunchCounter lc;
     if (n_he > 0) {
         unsigned gb = unsigned((n_he + 255) / 256);
-        k_na_check<<<gb, 256, 0, st>>>(offsets, members, n_he, n_vertices, card, changed, vdeg, sc);
+        k_na_check<<<gb, 256, 0, st>>>(offsets, members, n_he, nnz, n_vertices, card, changed, vdeg, sc);
         k_na_scan<<<1, 1024, 0, st>>>(vdeg, n_vertices, voff);
         k_na_fill<<<gb, 256, 0, st>>>(offsets, members, n_he, voff, vfill, v2h, sc);
         k_na_latch<<<1, 1, 0, st>>>(sc);

@@ -569,6 +569,20 @@ def esc_count_static_noalloc(n_vertices: int, offsets, members, timestamps, fami
     written to ``out_counts`` (a CUDA int64/uint64 tensor of 129 entries),
     without any device allocation by the library."""
     L = load()
+
+    def cuda_tensor(t, name, dtype, optional=False):
+        if t is None and optional:
+            return
+        ok = (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and str(t.dtype) == dtype)
+        if not ok:
+            raise EscError(1, f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+    cuda_tensor(offsets, "offsets", "torch.int64")
+    cuda_tensor(members, "members", "torch.int32")
+    cuda_tensor(timestamps, "timestamps", "torch.int64", optional=True)
+    if not (hasattr(out_counts, "is_cuda") and out_counts.is_cuda and out_counts.is_contiguous()
+            and out_counts.element_size() == 8 and out_counts.numel() >= 129):
+        raise EscError(1, "out_counts must be a contiguous CUDA tensor of at least 129 8-byte entries")
     po, ko = _ptr(offsets, np.int64)
     pm, km = _ptr(members, np.int32)
     pt, kt = _ptr(timestamps, np.int64)

@@ -30,6 +30,22 @@ class GpuLive:
             self.ts[int(i)] = int(t)
 
 
+class LiveIds:
+    """Live IDs of the CUDA side as a sorted array, kept from the IDs it
+    returns (a client's copy; for large graphs where a dict is slow)."""
+
+    def __init__(self, ids):
+        self.ids = np.sort(np.asarray(ids, dtype=np.int64))
+
+    def resolve(self, ranks):
+        return self.ids[np.asarray(ranks, dtype=np.int64)] if len(ranks) else np.zeros(0, np.int64)
+
+    def apply(self, dels, new_ids):
+        keep = np.ones(self.ids.size, bool)
+        keep[np.searchsorted(self.ids, np.asarray(dels, dtype=np.int64))] = False
+        self.ids = np.sort(np.concatenate([self.ids[keep], np.asarray(new_ids, dtype=np.int64)]))
+
+
 def caps_for(n_vertices, n_edges, nnz, batch_hyperedges, batch_incidences, slack=2.0):
     return dict(capacity_hyperedges=int(max(64, n_edges * slack)),
                 capacity_incidences=int(max(1024, nnz * slack)),

@@ -7,11 +7,16 @@ After two batches: the assigned IDs and the whole store equal the oracle's;
 the incrementally kept counts equal a full recount of every live hyperedge
 (a property that holds at any size); and the triads holding a few sampled
 hyperedges, counted by the oracle's own enumeration on its own copy of the
-graph, equal the library's local counts for the same hyperedges."""
+graph, equal the library's local counts for the same hyperedges.  Then a
+small batch on the same graph: its count change, for both families, equals
+the oracle's count of the triads (hyperedge family) and witness assignments
+(incident-vertex family) holding an inserted hyperedge on the new graph
+minus those holding a deleted one on the old graph (Alg. 3)."""
 import numpy as np
 import pytest
 
 import gen
+from harness import LiveIds
 from oracle import OracleHypergraph
 from oracle import oracle as O
 
@@ -25,6 +30,43 @@ def E():
     from paper_2512_21009_gb300 import escher
     escher.load()
     return escher
+
+
+M64 = 1 << 64
+
+
+def check_small_batch(g, og, live, seed, families, n=3, kmax=64):
+    """Apply n inserts and n deletes (cardinality <= kmax, so that the oracle
+    enumerates their triads in seconds) and compare the library's count
+    change with the oracle's Alg. 3 terms for every family in `families`."""
+    rng = np.random.default_rng(seed)
+    off0, mem0, ts0, ids0 = og.csr()
+    small = np.flatnonzero(np.diff(off0) <= kmax)
+    ranks = np.sort(rng.choice(small, size=n, replace=False))   # positions = ranks among live IDs
+    ins = gen.insert_batches(seed, og.n_vertices, 1, n, kmax, ts_start=int(ts0.max()))[0]
+    before = g.counts()
+    dels_o = og.resolve_ranks(ranks)
+    want_ids = og.apply_batch(ins.offsets, ins.members, ins.timestamps, dels_o)
+    dels_g = live.resolve(ranks)
+    got_ids = g.apply_batch(ins.offsets, ins.members, ins.timestamps, dels_g.astype(np.int32))
+    assert np.array_equal(got_ids, want_ids), "small batch: assigned IDs differ"
+    live.apply(dels_g, got_ids)
+    after = g.counts()
+    off1, mem1, ts1, ids1 = og.csr()
+    p0, p1 = np.searchsorted(ids0, dels_o), np.searchsorted(ids1, want_ids)
+    terms = {}
+    if "hyperedge" in families:
+        terms["hyperedge"] = (O.count_containing(off0, mem0, ts0, ids0, 0, O.FAM_HYPEREDGE, p0)[0],
+                              O.count_containing(off1, mem1, ts1, ids1, 0, O.FAM_HYPEREDGE, p1)[0])
+    if "vertex" in families:
+        terms["vertex"] = (O.count_vertex_containing(off0, mem0, p0), O.count_vertex_containing(off1, mem1, p1))
+    moved = 0
+    for fam, (d, i) in terms.items():
+        got = [(int(a) - int(b)) % M64 for a, b in zip(after[fam], before[fam])]
+        want = [(int(x) - int(y)) % M64 for x, y in zip(i, d)]
+        assert got == want, f"small batch, {fam}: library change {got}, oracle {want}"
+        moved += int(d.sum()) + int(i.sum())
+    assert moved > 0
 
 
 def test_full_size_batches(E):
@@ -45,12 +87,15 @@ def test_full_size_batches(E):
     rng = np.random.default_rng(19)
     g.autotune(np.sort(rng.choice(init.n, size=100_000, replace=False)).astype(np.int32), reps=1)
     og = OracleHypergraph(s.n_vertices, init.offsets, init.members, init.timestamps)
+    live = LiveIds(np.arange(init.n))
     for k, b in enumerate(s.batches):
         dels_o = og.resolve_ranks(b.del_ranks)
         want = og.apply_batch(b.inserts.offsets, b.inserts.members, b.inserts.timestamps, dels_o)
+        dels_g = live.resolve(b.del_ranks)
         got = g.apply_batch(todev(b.inserts.offsets, np.int64), todev(b.inserts.members, np.int32),
-                            todev(b.inserts.timestamps, np.int64), todev(np.sort(b.del_ranks), np.int32))
+                            todev(b.inserts.timestamps, np.int64), todev(np.sort(dels_g), np.int32))
         assert np.array_equal(got, want), f"batch {k}: assigned IDs differ"
+        live.apply(dels_g, got)
     # the store, both views
     ex = g.export()
     off, mem, ts, ids = og.csr()
@@ -72,6 +117,9 @@ def test_full_size_batches(E):
     loc = g.local_triads(ids[sel].astype(np.int32))
     assert np.array_equal(loc["hyperedge"], h30)
     assert int(h30.sum()) > 0
+    # Alg. 3 on the benchmark graph, both families, against the oracle
+    for seed in (29, 31):
+        check_small_batch(g, og, live, seed, ("hyperedge", "vertex"))
     g.close()
 
 
