@@ -249,10 +249,11 @@ typedef struct {
     int64_t meta_reads;      /* per-neighbour metadata lookups by the counter  */
     int64_t triads;          /* triads classified by the counter               */
     int64_t alg_entries;     /* incidence entries the method reads for the
-                                changed hyperedges: for each changed h,
-                                |h| + sum of its members' degrees, plus, for
-                                each candidate neighbour g1 of h, |g1| + sum
-                                of g1's members' degrees                      */
+                                changed hyperedges (earlier accounting: for
+                                each changed h, |h| + sum of its members'
+                                degrees, plus, for each candidate neighbour
+                                g1 of h, |g1| + sum of g1's members' degrees;
+                                the four terms below replace it)             */
     int64_t work[6];         /* counter work: centre items, N(g1) build entries,
                                 pair-pass visits, closed pairs, slow-path
                                 triple-intersection steps, aggregate-pass visits */
@@ -261,6 +262,15 @@ typedef struct {
     int64_t alg_center;      /* the part of alg_entries read on behalf of the
                                 candidate neighbours g1 (the centre kernel's
                                 share: |g1| + sum of member degrees per pair)  */
+    /* Algorithmic int32 entries (4 bytes each) of the batch by term: what a
+     * method must read for the changed hyperedges, whatever it caches.     */
+    int64_t alg_store;       /* store: 2 |h| + a 4-entry header per changed h */
+    int64_t alg_build;       /* neighbourhoods: sum of the members' degrees
+                                per changed h                                 */
+    int64_t alg_closed;      /* closed pairs: min(|g1|, |g2|) per closed pair
+                                {g1, g2} of N(h) counted                      */
+    int64_t alg_open;        /* open paths: sum of g1's members' degrees per
+                                pair (h, g1), g1 a candidate neighbour of h   */
 } esc_batch_stats;
 
 esc_status esc_set_profiling(esc_graph* g, int32_t on);

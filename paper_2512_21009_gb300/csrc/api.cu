@@ -370,6 +370,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
         long long v = atoll(env);
         if (v >= 1) E->cs.r_min = v;
     }
+    if (const char* env = getenv("ESC_COUNT_ORIENT")) E->cs.orient = atoi(env) != 0;
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
         long long v = atoll(env);
         if (v >= 64 && (v & (v - 1)) == 0) E->cs.smem_slots = v;
@@ -687,6 +688,10 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs, const int32_t*
     E->last.alg_entries = int64_t(E->h_sc->stats[4]);
     for (int k = 0; k < 6; ++k) E->last.work[k] = int64_t(E->h_sc->stats[5 + k]);
     E->last.alg_center = int64_t(E->h_sc->stats[11]);
+    E->last.alg_open = int64_t(E->h_sc->stats[12]);
+    E->last.alg_closed = int64_t(E->h_sc->stats[13]);
+    E->last.alg_build = int64_t(E->h_sc->stats[14]);
+    E->last.alg_store = int64_t(E->h_sc->stats[15]);
     if (E->h_sc->status != 0) {
         E->err = describe(*E->h_sc);
         return esc_status(E->h_sc->status);

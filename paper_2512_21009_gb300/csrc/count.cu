@@ -261,6 +261,11 @@ struct Accum {
     unsigned long long n_v2h, n_h2v, n_meta, n_tri, n_alg;
     unsigned long long w[6];  // items, build entries, pair visits, closed pairs, slow t steps, agg visits
     unsigned long long n_alg_c;  // the part of n_alg counted by the centre kernel
+    // algorithmic int32 entries by term: open paths (sum of member degrees
+    // of g1 per pair (h, g1)), closed pairs (min(|g1|, |g2|) per closed
+    // pair), neighbour build (sum of member degrees of h per changed h) and
+    // store (2 |h| + a 4-entry header per changed h)
+    unsigned long long n_open, n_closed, n_build, n_store;
 };
 
 struct Tables {
@@ -317,6 +322,7 @@ struct CountArgs {
     CountScratch cs;
     uint32_t nh_smem_cap, c_smem_cap;
     bool dev;                   // the run's range comes from the device (planned by k_run_plan)
+    bool orient;                // closed pairs searched in (|g|, g) order (k_center_o)
 };
 
 // The changed hyperedges of one count run, [lo, lo + n) of the side, and the
@@ -366,9 +372,17 @@ __device__ void flush_stats(const CountArgs& A, Accum& acc, long long* red) {
     long long r5 = block_sum<NT>((long long)acc.n_alg_c, red);
     long long wk[6];
     for (int k = 0; k < 6; ++k) wk[k] = block_sum<NT>((long long)acc.w[k], red);
+    const long long r6 = block_sum<NT>((long long)acc.n_open, red);
+    const long long r7 = block_sum<NT>((long long)acc.n_closed, red);
+    const long long r8 = block_sum<NT>((long long)acc.n_build, red);
+    const long long r9 = block_sum<NT>((long long)acc.n_store, red);
     if (threadIdx.x == 0) {
         for (int k = 0; k < 6; ++k)
             if (wk[k]) atomicAdd(&A.sc->stats[5 + k], (unsigned long long)wk[k]);
+        if (r6) atomicAdd(&A.sc->stats[12], (unsigned long long)r6);
+        if (r7) atomicAdd(&A.sc->stats[13], (unsigned long long)r7);
+        if (r8) atomicAdd(&A.sc->stats[14], (unsigned long long)r8);
+        if (r9) atomicAdd(&A.sc->stats[15], (unsigned long long)r9);
         atomicAdd(&A.sc->stats[0], (unsigned long long)r0);
         atomicAdd(&A.sc->stats[1], (unsigned long long)r1);
         atomicAdd(&A.sc->stats[2], (unsigned long long)r2);
@@ -413,7 +427,12 @@ __global__ void k_nh_size(Store S, Scalars* sc, const int32_t* changed, int64_t 
     }
 }
 
+// N(h) lists of at most this many entries are sorted by (|g|, g) when the
+// oriented centre kernel runs (larger ones are met through their table)
+constexpr int kSortMax = 4096;
+
 struct SmemNH {
+    unsigned long long skey[kSortMax];  // sort keys |g| << 43 | g << 12 | list index
     int32_t keys[NH_S];
     uint32_t vals[NH_S];
     int32_t aux[NH_S];
@@ -538,7 +557,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
     const int64_t gs = cs.gs_nh;
     Tab gNH{cs.onh_keys + blockIdx.x * gs, cs.onh_vals + blockIdx.x * gs, cs.onh_aux + blockIdx.x * gs,
             cs.onh_list + blockIdx.x * (gs / 2), &s.n_list, uint32_t(gs - 1), int(gs / 2)};
-    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0};
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0, 0, 0};
     int cur_g = -1;
     const int32_t* v2h = S.vp.arena;
     for (;;) {
@@ -574,6 +593,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
                 cs.nh_n[i] = 0;
                 cs.nh_toff[i] = 0;
                 cs.nh_tcap[i] = 0;
+                cs.nh_flag[i] = 0;
                 cs.r_off[i] = -1;
             }
             continue;
@@ -596,7 +616,11 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         if (big)
             for (uint32_t t = tid; t < cap / 8; t += NT_NH) filt[t] = 0;
         acc.n_h2v += (tid < kh) ? (kh - tid + NT_NH - 1) / NT_NH : 0;
-        if (tid == 0) acc.n_alg += (unsigned long long)(uh + kh);
+        if (tid == 0) {
+            acc.n_alg += (unsigned long long)(uh + kh);
+            acc.n_build += (unsigned long long)uh;
+            acc.n_store += 2ull * (unsigned long long)kh + 4ull;
+        }
         for (int m0 = 0; m0 < kh; m0 += NT_NH) {
             const int n = min(NT_NH, kh - m0);
             const int tot = load_segment<NT_NH>(S, hmem + m0, n, s.seg_off, s.seg_v, s.seg_pre, s.warp_tmp);
@@ -613,20 +637,50 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         // distinct neighbours never outnumber the region reserved for them
         // (sum of member degrees); the clamp only matters after an error
         const int nn = int(min((long long)min(s.n_list, NH.list_cap), uh));
-        for (int q = tid; q < nn; q += NT_NH) {
+        // for the oriented centre kernel the list goes out sorted by (|g|, g),
+        // so that the neighbours of h above a given g1 are a suffix of it
+        const bool sorted = A.orient && !huge && nn <= kSortMax;
+        if (sorted) {
+            int n2 = 2;
+            while (n2 < nn) n2 <<= 1;
+            for (int q = tid; q < n2; q += NT_NH) {
+                unsigned long long key = ~0ull;
+                if (q < nn) {
+                    const int32_t gg = NH.keys[NH.list[q]];
+                    key = (uint64_t(S.h_card[gg]) << 43) | (uint64_t(uint32_t(gg)) << 12) | uint64_t(q);
+                }
+                s.skey[q] = key;
+            }
+            __syncthreads();
+            // bitonic sort of skey[0, n2)
+            for (int k = 2; k <= n2; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int t = tid; t < (n2 >> 1); t += NT_NH) {
+                        const int a = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+                        const unsigned long long x0 = s.skey[a], x1 = s.skey[a + j];
+                        if ((x0 > x1) == ((a & k) == 0)) {
+                            s.skey[a] = x1;
+                            s.skey[a + j] = x0;
+                        }
+                    }
+                    __syncthreads();
+                }
+        }
+        for (int p = tid; p < nn; p += NT_NH) {
             // in place, the list of taken slots is the list region itself:
             // each entry is read and then overwritten by the same thread
+            const int q = sorted ? int(s.skey[p] & 0xfffu) : p;
             const int sl = NH.list[q];
             const int32_t gg = NH.keys[sl];
             const uint64_t xvt = huge ? xv_t[sl] : uint64_t(NH.vals[sl]) | (uint64_t(uint32_t(NH.aux[sl])) << 32);
             const uint32_t x = uint32_t(xvt) & kXMask;
-            const int kg = S.h_card[gg];
+            const int kg = sorted ? int(s.skey[p] >> 43) : S.h_card[gg];
             const bool chg_g = bit_test(A.chg, gg);
             // the list entry also carries |g| and whether g changed, read
             // in order by k_center instead of gathered per visit
-            cs.nh_g[base + q] = gg;
-            cs.nh_xv[base + q] = (xvt & 0xffffffff00000000ull) | x | (uint64_t(kg) << 16) | (chg_g ? 1ull << 31 : 0ull);
-            if (cs.nh_ts) cs.nh_ts[base + q] = S.h_ts[gg];
+            cs.nh_g[base + p] = gg;
+            cs.nh_xv[base + p] = (xvt & 0xffffffff00000000ull) | x | (uint64_t(kg) << 16) | (chg_g ? 1ull << 31 : 0ull);
+            if (cs.nh_ts) cs.nh_ts[base + p] = S.h_ts[gg];
             if (big) {
                 uint32_t bits;
                 const uint32_t w = filter_word(gg, cap, bits);
@@ -649,6 +703,7 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
         }
         if (tid == 0) {
             cs.nh_n[i] = nn;
+            cs.nh_flag[i] = sorted ? 1 : 0;
             cs.nh_toff[i] = big ? base + uh : 0;
             cs.nh_tcap[i] = big ? int32_t(NH.mask + 1) : 0;
             if ((fam & kFamV) && kh >= 3) acc.v1 += (unsigned long long)kh * (kh - 1) * (kh - 2) / 6;
@@ -849,6 +904,7 @@ __global__ void k_scatter(CountArgs A) {
             const int64_t pos = cs.loffg[gg] + atomicAdd(&cs.lfill[gg], 1);
             cs.l_i[pos] = int32_t(i);
             cs.l_xv[pos] = cs.nh_xv[base + q];
+            cs.l_q[pos] = q;
         }
     }
 }
@@ -1008,7 +1064,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
     int64_t* g_lts = cs.oc_lts + blockIdx.x * (gs / 2);
     int32_t* g_lkey = cs.oc_lkey + blockIdx.x * (gs / 2);
     uint32_t* hist = s.hist[wid];
-    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0};
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0, 0, 0};
     const int64_t n_items = A.sc->items[A.side];
     const int nd = A.sc->n_d[A.side];
     int cur_g = -1;
@@ -1045,6 +1101,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
         if (tid == 0) {
             acc.n_alg += (unsigned long long)(u1 + k1) * (unsigned long long)nh_all;
             acc.n_alg_c += (unsigned long long)(u1 + k1) * (unsigned long long)nh_all;
+            acc.n_open += (unsigned long long)u1 * (unsigned long long)nh_all;
             ++acc.w[0];
             acc.w[1] += (unsigned long long)u1;
         }
@@ -1228,6 +1285,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
                     if (g2 > g1 && !(g2 < h && chg2)) {
                         ++acc.n_meta;
                         ++acc.w[3];
+                        acc.n_closed += (unsigned long long)min(k1, k2);
                         const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
                                                   kh, s.hI[l], s.hIn[l], acc.w[4]);
                         if (want_open)
@@ -1498,6 +1556,505 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// 3b. oriented centre kernel (hyperedge and incident-vertex families)
+// ---------------------------------------------------------------------------
+//
+// Without the temporal family every open triad is counted in aggregate, so
+// the pair pass only has to find the closed pairs {g1, g2} of N(h).  Each is
+// searched from one side only: from the smaller of g1, g2 in the order
+// (|g|, g).  For a pair (h, g1) that is either the part of N(h) above g1 (a
+// suffix of h's list, sorted by k_nh_build), each probing N(g1)'s table
+// (mode 0), or the part of N(g1) above g1 (the "plus list" built here), each
+// probing N(h)'s filter and table (mode 1), whichever is shorter; an N(h) too
+// long to sort is met through its table, or, when it has none, visited whole
+// with the order tested per entry (mode 3).
+//
+// The aggregates count every pair of N'(h) (open at h, k_nh_build) and every
+// f of N(g1) (open at g1, below) as open.  A closed triad {h, g1, g2} found
+// here takes back the three open classes the aggregates gave it -- centred
+// at h, at g1 (with f = g2) and at g2 (with f = g1) -- and adds its closed
+// class.  The changed f < h of N(g1) are left out of h's aggregate at g1
+// whether or not they lie in N(h): their triads belong to f.  So no mark of
+// N(h) inside N(g1) is kept, and every closed triad is classified once.
+
+template <int NT_C, int T1_S>
+struct SmemCO {
+    static constexpr int NW_C = NT_C / 32;
+    static constexpr int BLOOM_W = T1_S >= 4096 ? 2048 : 4096;
+    Tables tb;
+    uint32_t hist[NW_C][32];
+    uint32_t hneg[NW_C][32];     // open classes taken back for closed triads
+    unsigned long long acc[32];
+    int32_t keys[T1_S];
+    uint32_t vals[T1_S];
+    int32_t list[T1_S / 2];
+    int32_t lk[T1_S / 2];        // |f|, bit 31: f is changed
+    int32_t pf[T1_S / 2];        // plus list: f above g1 ...
+    uint32_t pm[T1_S / 2];       // ... and |g1 & f| | |f| << 16 | changed << 31
+    long long cl[T1_S / 2];      // changed f: f | |g1 & f| << 31 | |f| << 46
+    int64_t seg_off[NT_C];
+    int32_t seg_pre[NT_C + 1];
+    int warp_tmp[32];
+    long long red[NW_C];
+    long long item;
+    int n_list, n_plus, n_cl, n_c;
+    uint32_t tot[2];
+    uint32_t win[kWin][2];
+    // the changed hyperedges h of a chunk
+    int32_t hh[LCH], hk[LCH], hx[LCH], hvf[LCH], hnn[LCH], htcap[LCH], hpos[LCH], hmode[LCH];
+    int64_t hnb[LCH], htoff[LCH];
+    const int32_t* hmem[LCH];
+    int32_t hord[LCH];           // the h with work in the pair pass, and the prefix of their work
+    int32_t hpre[LCH + 1];
+    uint32_t sub[LCH][4];
+    uint32_t xc[LCH][2];
+    int32_t hI[LCH][kIC];
+    int hIn[LCH];
+    uint32_t bloom[BLOOM_W];     // one-hash filter of N(g1)
+};
+
+static_assert(sizeof(SmemCO<256, 2048>) + 1024 <= 233472 / 3, "three 256-thread oriented centre blocks per SM");
+
+__device__ __forceinline__ unsigned long long order_key(int k, int32_t g) {
+    return (uint64_t(uint32_t(k)) << 32) | uint64_t(uint32_t(g));
+}
+
+template <int NT_C, int T1_S, int MINB>
+__global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
+    constexpr int NW_C = NT_C / 32;
+    using Sm = SmemCO<NT_C, T1_S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sm& s = *reinterpret_cast<Sm*>(smem_raw);
+    const Store& S = A.S;
+    if (A.sc->gate) return;
+    const int tid = threadIdx.x;
+    const int lane = lane_id();
+    const int wid = warp_id();
+    const uint32_t fam = S.fam;
+    const bool agg = (fam & kFamH) != 0;   // the open triads, in aggregate
+    const CountScratch& cs = A.cs;
+    const RunRange R = run_of(A);
+    const int32_t* v2h = S.vp.arena;
+    const int32_t* h2v = S.hp.arena;
+    load_tables(s.tb, NT_C);
+    for (int i = tid; i < NW_C * 32; i += NT_C) {
+        s.hist[i / 32][i % 32] = 0;
+        s.hneg[i / 32][i % 32] = 0;
+    }
+    for (int i = tid; i < 32; i += NT_C) s.acc[i] = 0;
+    for (int i = tid; i < T1_S; i += NT_C) {
+        s.keys[i] = EMPTY;
+        s.vals[i] = 0;
+    }
+    for (int i = tid; i < Sm::BLOOM_W; i += NT_C) s.bloom[i] = 0;
+    for (int i = tid; i < LCH * 4; i += NT_C) s.sub[i >> 2][i & 3] = 0;
+    for (int i = tid; i < LCH * 2; i += NT_C) s.xc[i >> 1][i & 1] = 0;
+    if (tid < 2) s.tot[tid] = 0;
+    for (int i = tid; i < kWin * 2; i += NT_C) s.win[i >> 1][i & 1] = 0;
+    if (tid == 0) {
+        s.n_list = 0;
+        s.n_plus = 0;
+        s.n_cl = 0;
+    }
+    __syncthreads();
+    const int64_t gs = cs.gs_c;
+    int32_t* g_keys = cs.oc_keys + blockIdx.x * gs;
+    uint32_t* g_vals = cs.oc_vals + blockIdx.x * gs;
+    int32_t* g_list = cs.oc_list + blockIdx.x * (gs / 2);
+    int32_t* g_lk = cs.oc_lk + blockIdx.x * (gs / 2);
+    int32_t* g_pf = cs.oc_pf + blockIdx.x * (gs / 2);
+    uint32_t* g_pm = cs.oc_pm + blockIdx.x * (gs / 2);
+    long long* g_cl = reinterpret_cast<long long*>(cs.oc_lts) + blockIdx.x * (gs / 2);
+    uint32_t* hist = s.hist[wid];
+    uint32_t* hneg = s.hneg[wid];
+    Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0, 0, 0};
+    const int64_t n_items = A.sc->items[A.side];
+    const int nd = A.sc->n_d[A.side];
+    int cur_g = -1;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s.item = (long long)atomicAdd(&A.sc->queue[A.side], 1ull);
+        __syncthreads();
+        const int64_t item = s.item;
+        if (item >= n_items) break;
+        const int64_t j = upper_bound_dev(cs.d_item_start, int64_t(nd) + 1, item) - 1;
+        const int64_t sup = item - cs.d_item_start[j];
+        const int32_t g1 = cs.d_list[j];
+        const int64_t l_lo = cs.d_loff[j], l_hi = cs.d_loff[j + 1];
+        const int64_t n_chunks = (l_hi - l_lo + LCH - 1) / LCH;
+        const int64_t c_beg = sup * kSuper, c_end = min(c_beg + kSuper, n_chunks);
+        const int64_t nh_all = min(l_lo + c_end * LCH, l_hi) - (l_lo + c_beg * LCH);
+        const int g = A.changed_g ? A.changed_g[A.lo + cs.l_i[l_lo + c_beg * LCH]] : 0;
+        if (g != cur_g) {
+            if (cur_g >= 0) {
+                __syncthreads();
+                for (int b = tid; b < kNH; b += NT_C) {
+                    unsigned long long v = s.acc[b];
+                    if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(cur_g) * kCStride + b]), v);
+                    s.acc[b] = 0;
+                }
+                flush<NT_C>(A, nullptr, nullptr, 0, cur_g, acc, s.red);
+            }
+            cur_g = g;
+        }
+        const int k1 = S.h_card[g1];
+        const int32_t* g1mem = h2v + S.h_off[g1];
+        const unsigned long long key1 = order_key(k1, g1);
+        long long u1 = 0;
+        for (int t = tid; t < k1; t += NT_C) u1 += S.v_deg[g1mem[t]];
+        u1 = block_sum<NT_C>(u1, s.red);
+        acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
+        if (tid == 0) {
+            // open paths: N(g1) (sum of member degrees) per pair (h, g1)
+            acc.n_open += (unsigned long long)u1 * (unsigned long long)nh_all;
+            ++acc.w[0];
+            acc.w[1] += (unsigned long long)u1;
+        }
+        Tab T1;
+        int32_t* lk;
+        int32_t* pf;
+        uint32_t* pm;
+        long long* cl;
+        int P = 1;
+        const uint32_t t1_cap = pow2_at_least(2 * u1);
+        if (t1_cap <= min(A.c_smem_cap, uint32_t(T1_S))) {
+            T1 = Tab{s.keys, s.vals, nullptr, s.list, &s.n_list, t1_cap - 1, T1_S / 2};
+            lk = s.lk;
+            pf = s.pf;
+            pm = s.pm;
+            cl = s.cl;
+        } else {
+            T1 = Tab{g_keys, g_vals, nullptr, g_list, &s.n_list, uint32_t(gs - 1), int(gs / 2)};
+            lk = g_lk;
+            pf = g_pf;
+            pm = g_pm;
+            cl = g_cl;
+            if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
+            else P = int((4 * u1 + gs - 1) / gs);
+        }
+        // filter of N(g1): about 8 bits per entry, at most the array
+        int bw = 32;
+        while (bw < Sm::BLOOM_W && (long long)bw * 4 < u1 / P) bw <<= 1;
+        for (int p = 0; p < P; ++p) {
+            // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p)
+            for (int m0 = 0; m0 < k1; m0 += NT_C) {
+                const int n = min(NT_C, k1 - m0);
+                const int tot = load_segment<NT_C>(S, g1mem + m0, n, s.seg_off, nullptr, s.seg_pre, s.warp_tmp);
+                for (int e = tid; e < tot; e += NT_C) {
+                    const int m = seg_member(s.seg_pre, n, e);
+                    const int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
+                    if (f == g1) continue;
+                    if (P > 1 && part_of(f, P) != p) continue;
+                    tab_insert(T1, f, 1u, 0, A.sc);
+                }
+                acc.n_v2h += (tid < tot) ? (tot - tid + NT_C - 1) / NT_C : 0;
+                __syncthreads();
+            }
+            const int n1 = min(s.n_list, T1.list_cap);
+            // ---- per f: size and changed flag, the filter, the plus list; in
+            //      aggregate mode the totals, the x window and the changed f
+            const int wlo = k1 - kWin;
+            for (int q0 = 0; q0 < n1; q0 += NT_C) {
+                const int q = q0 + tid;
+                int wkey = -1, C = 0;
+                if (q < n1) {
+                    const int sl = T1.list[q];
+                    const int32_t f = T1.keys[sl];
+                    const int kf = S.h_card[f];
+                    const bool changed_f = bit_test(A.chg, f);
+                    const int x = int(T1.vals[sl]);
+                    lk[q] = kf | (changed_f ? int32_t(0x80000000u) : 0);
+                    const uint32_t bb = bloom_bit(f, bw);
+                    atomicOr(&s.bloom[bb >> 5], 1u << (bb & 31));
+                    if (order_key(kf, f) > key1) {
+                        const int c = atomicAdd(&s.n_plus, 1);
+                        pf[c] = f;
+                        pm[c] = uint32_t(x) | (uint32_t(kf) << 16) | (changed_f ? 0x80000000u : 0u);
+                    }
+                    if (agg) {
+                        C = kf > x ? 1 : 0;
+                        if (x >= wlo && x < k1) wkey = (x - wlo) * 2 + C;
+                        if (changed_f) {
+                            const int c = atomicAdd(&s.n_cl, 1);
+                            cl[c] = (long long)f | ((long long)x << 31) | ((long long)kf << 46);
+                        }
+                    }
+                }
+                if (agg) {
+                    const unsigned in = __ballot_sync(0xffffffffu, q < n1);
+                    const unsigned c1 = __ballot_sync(0xffffffffu, q < n1 && C == 1);
+                    if (lane == 0) {
+                        if (__popc(in & ~c1)) atomicAdd(&s.tot[0], __popc(in & ~c1));
+                        if (__popc(c1)) atomicAdd(&s.tot[1], __popc(c1));
+                    }
+                    warp_count(&s.win[0][0], wkey);
+                }
+            }
+            acc.n_meta += (tid < n1) ? (n1 - tid + NT_C - 1) / NT_C : 0;
+            __syncthreads();
+            const int n_plus = s.n_plus;
+            const int n_cl = s.n_cl;
+            for (int64_t ch = c_beg; ch < c_end; ++ch) {
+                const int64_t lbeg = l_lo + ch * LCH;
+                const int nh = int(min(lbeg + LCH, l_hi) - lbeg);
+                __syncthreads();
+                if (tid < nh) {
+                    const int64_t e = lbeg + tid;
+                    const int32_t li = cs.l_i[e];
+                    const uint64_t xv1 = cs.l_xv[e];
+                    const int32_t h = A.changed[A.lo + li];
+                    s.hh[tid] = h;
+                    s.hk[tid] = S.h_card[h];
+                    s.hx[tid] = int(xv1 & kXMask);
+                    s.hvf[tid] = int32_t(uint32_t(xv1 >> 32));
+                    s.hmem[tid] = h2v + S.h_off[h];
+                    s.hnb[tid] = cs.nh_off[li] - R.base;
+                    s.hnn[tid] = cs.nh_n[li];
+                    s.htcap[tid] = cs.nh_tcap[li];
+                    s.htoff[tid] = cs.nh_toff[li];
+                    // sorted list: the neighbours above g1 start after g1's place
+                    s.hpos[tid] = (cs.nh_flag[li] & 1) ? cs.l_q[e] : -1;
+                    s.hIn[tid] = 0;
+                }
+                __syncthreads();
+                for (int l = 0; l < nh; ++l) {
+                    const int xh1 = s.hx[l];
+                    if (xh1 < 2 || xh1 > kIC) continue;
+                    const int kh = s.hk[l];
+                    const bool from_h = kh <= k1;
+                    const int32_t* a = from_h ? s.hmem[l] : g1mem;
+                    const int32_t* b = from_h ? g1mem : s.hmem[l];
+                    const int na = from_h ? kh : k1, nb = from_h ? k1 : kh;
+                    for (int i = tid; i < na; i += NT_C) {
+                        const int32_t u = a[i];
+                        if (contains_sorted(b, nb, u)) {
+                            const int c = atomicAdd(&s.hIn[l], 1);
+                            if (c < kIC) s.hI[l][c] = u;
+                        }
+                    }
+                }
+                if (tid == 0) {
+                    // work of the pair pass per h; the h with work are listed
+                    // in hord with the prefix of their work in hpre
+                    int run = 0, nc = 0;
+                    for (int l = 0; l < nh; ++l) {
+                        int mode, work;
+                        if (s.hpos[l] >= 0) {
+                            const int sfx = s.hnn[l] - s.hpos[l] - 1;
+                            if (s.htcap[l] > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
+                                mode = 1;
+                                work = n_plus;
+                            } else {
+                                mode = 0;
+                                work = sfx;
+                            }
+                        } else if (s.htcap[l] > 0) {
+                            mode = 1;
+                            work = n_plus;
+                        } else {
+                            mode = 3;
+                            work = s.hnn[l];
+                        }
+                        s.hmode[l] = mode;
+                        if (work > 0) {
+                            s.hord[nc] = l;
+                            s.hpre[nc] = run;
+                            ++nc;
+                            run += work;
+                        }
+                    }
+                    s.hpre[nc] = run;
+                    s.n_c = nc;
+                }
+                __syncthreads();
+                const int nc = s.n_c;
+                const int wtot = s.hpre[nc];
+                if (tid == 0) acc.w[2] += (unsigned long long)wtot;
+                // each lane holds one h of the pass: its start and index
+                const int my_pre = lane < nc ? s.hpre[lane] : INT_MAX;
+                const int my_l = lane < nc ? s.hord[lane] : 0;
+
+                // ---- the pair pass: a warp takes 32 consecutive work indices
+                for (int w0 = wid * 32; w0 < wtot; w0 += NT_C) {
+                    const int idx = w0 + lane;
+                    // the h of each index: the last one starting at or before it
+                    const unsigned le = __ballot_sync(0xffffffffu, my_pre <= w0);
+                    const int c0 = 31 - __clz(le);
+                    const unsigned bnd = (my_pre > w0 && my_pre < w0 + 32) ? 1u << (my_pre - w0) : 0u;
+                    const unsigned B = __reduce_or_sync(0xffffffffu, bnd);
+                    const int c = c0 + __popc(B & ((2u << lane) - 1u));
+                    const int l = __shfl_sync(0xffffffffu, my_l, c & 31);
+                    const int q = idx - __shfl_sync(0xffffffffu, my_pre, c & 31);
+                    do {
+                    if (idx >= wtot) break;
+                    const int mode = s.hmode[l];
+                    int32_t g2;
+                    int x12, xh2, k2;
+                    int32_t vf2;
+                    bool chg2;
+                    if (mode == 1) {
+                        g2 = pf[q];
+                        const uint32_t tcap = uint32_t(s.htcap[l]);
+                        uint32_t bits;
+                        const uint32_t fw = reinterpret_cast<const uint32_t*>(
+                            cs.nh_g + s.htoff[l] + tcap)[filter_word(g2, tcap, bits)];
+                        if ((fw & bits) != bits) break;
+                        const int ps = probe_list_table(cs.nh_g + s.htoff[l], tcap - 1, g2);
+                        if (ps < 0) break;
+                        const uint64_t xv2 = cs.nh_xv[s.htoff[l] + ps];
+                        const uint32_t m = pm[q];
+                        x12 = int(m & 0xffffu);
+                        k2 = int((m >> 16) & 0x7fffu);
+                        chg2 = (m >> 31) != 0;
+                        xh2 = int(uint32_t(xv2) & kXMask);
+                        vf2 = int32_t(uint32_t(xv2 >> 32));
+                    } else {
+                        const int64_t at = s.hnb[l] + (mode == 0 ? s.hpos[l] + 1 + q : q);
+                        g2 = cs.nh_g[at];
+                        uint64_t xv2 = 0;
+                        if (mode == 3) {
+                            xv2 = cs.nh_xv[at];
+                            if (order_key(int((xv2 >> 16) & 0x7fffu), g2) <= key1) break;
+                        }
+                        if (P > 1 && part_of(g2, P) != p) break;
+                        const uint32_t bb = bloom_bit(g2, bw);
+                        if (!((s.bloom[bb >> 5] >> (bb & 31)) & 1u)) break;
+                        const int sl = tab_find(T1, g2);
+                        if (sl < 0) break;
+                        if (mode != 3) xv2 = cs.nh_xv[at];
+                        x12 = int(T1.vals[sl]);
+                        xh2 = int(xv2 & kXMask);
+                        k2 = int((xv2 >> 16) & 0x7fffu);
+                        chg2 = ((xv2 >> 31) & 1u) != 0;
+                        vf2 = int32_t(uint32_t(xv2 >> 32));
+                    }
+                    // a closed triad {h, g1, g2}, g1 below g2
+                    const int32_t h = s.hh[l];
+                    if (g2 < h && chg2) break;  // it belongs to g2 (or a smaller changed member)
+                    const int kh = s.hk[l], xh1 = s.hx[l];
+                    ++acc.w[3];
+                    const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
+                                              kh, s.hI[l], s.hIn[l], acc.w[4]);
+                    acc.n_meta += 1;
+                    acc.n_closed += (unsigned long long)min(k1, k2);  // closed pairs: min(|g1|, |g2|) entries
+                    if (agg) {
+                        const int ra = kh - xh1 - xh2 + t, rb = k1 - xh1 - x12 + t, rc = k2 - x12 - xh2 + t;
+                        const int mk = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xh1 - t > 0) << 3) |
+                                       ((x12 - t > 0) << 4) | ((xh2 - t > 0) << 5) | ((t > 0) << 6);
+                        ++acc.n_tri;
+                        // every mask formed here is a valid triad (its pairwise
+                        // intersections are non-empty), so each class is >= 0
+                        const int cc = s.tb.cls30[mk];
+                        // the open classes the aggregates gave this triple
+                        const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
+                        const int m1 = (kh > xh1 ? 1 : 0) | (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 4 : 0) | 8 | 16;
+                        const int m2 = (kh > xh2 ? 1 : 0) | (x12 != k2 - xh2 ? 2 : 0) | (k1 > x12 ? 4 : 0) | 8 | 16;
+                        const int c1 = s.tb.cls30[m1], c2 = s.tb.cls30[m2];
+                        if (cc >= 0) atomicAdd(&hist[cc], 1u);
+                        if (ch >= 0) atomicAdd(&hneg[ch], 1u);
+                        if (c1 >= 0) atomicAdd(&hneg[c1], 1u);
+                        if (c2 >= 0) atomicAdd(&hneg[c2], 1u);
+                    }
+                    if (fam & kFamV)
+                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
+                                  2ull * t;
+                    } while (0);
+                }
+                __syncthreads();
+                if (agg) {
+                    // open triads {h, g1, f} centred at g1, in aggregate: the
+                    // class is set by A = [h not inside g1] and the bucket
+                    // b = 2B + C of f, B = [|g1&f| != |g1| - |h&g1|],
+                    // C = [f not inside g1]; from the totals over N(g1) are
+                    // taken f = h and the changed f < h
+                    const int wc = nh * n_cl;
+                    if (tid == 0) acc.w[5] += (unsigned long long)wc;
+                    for (int idx0 = 0; idx0 < wc; idx0 += NT_C) {
+                        const int idx = idx0 + tid;
+                        int skey = -1;
+                        if (idx < wc) {
+                            const int l = idx / n_cl, c = idx - l * n_cl;
+                            const long long v = cl[c];
+                            const int32_t f = int32_t(v & 0x7fffffffll);
+                            if (f < s.hh[l]) {
+                                const int x = int((v >> 31) & 0x7fffll), kf = int(v >> 46);
+                                skey = l * 4 + ((x != k1 - s.hx[l] ? 2 : 0) | (kf > x ? 1 : 0));
+                            }
+                        }
+                        warp_count(&s.sub[0][0], skey);
+                    }
+                    if (tid < nh && (P == 1 || part_of(s.hh[tid], P) == p)) {
+                        const int xh1 = s.hx[tid];
+                        atomicAdd(&s.sub[tid][(xh1 != k1 - xh1 ? 2 : 0) | (s.hk[tid] > xh1 ? 1 : 0)], 1u);
+                    }
+                    for (int l = 0; l < nh; ++l) {  // x = |g1| - |h&g1| outside the window
+                        if (s.hx[l] <= kWin) continue;
+                        const int xstar = k1 - s.hx[l];
+                        for (int q = tid; q < n1; q += NT_C)
+                            if (int(T1.vals[T1.list[q]]) == xstar)
+                                atomicAdd(&s.xc[l][(lk[q] & 0x7fffffff) > xstar ? 1 : 0], 1u);
+                    }
+                    __syncthreads();
+                    if (tid < nh) {
+                        const int xh1 = s.hx[tid], kh = s.hk[tid];
+                        const int A_bit = kh > xh1 ? 1 : 0;
+                        for (int b = 0; b < 4; ++b) {
+                            const int B = b >> 1, C = b & 1;
+                            const uint32_t h0 = xh1 <= kWin ? s.win[kWin - xh1][C] : s.xc[tid][C];
+                            const uint32_t total = B == 0 ? h0 : s.tot[C] - h0;
+                            const uint32_t n = total - s.sub[tid][b];
+                            if (n) {
+                                const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
+                                atomicAdd(&hist[s.tb.cls30[m]], n);
+                                acc.n_tri += n;
+                            }
+                            s.sub[tid][b] = 0;
+                        }
+                        s.xc[tid][0] = s.xc[tid][1] = 0;
+                    }
+                }
+                __syncthreads();
+                // fold the warp histograms of this chunk
+                for (int b = tid; b < kNH; b += NT_C) {
+                    unsigned long long v = 0;
+                    for (int w = 0; w < NW_C; ++w) {
+                        v += s.hist[w][b];
+                        v -= s.hneg[w][b];
+                        s.hist[w][b] = 0;
+                        s.hneg[w][b] = 0;
+                    }
+                    s.acc[b] += v;
+                }
+                __syncthreads();
+            }  // chunks
+            tab_clear<NT_C>(T1, n1);
+            for (int i = tid; i < bw; i += NT_C) s.bloom[i] = 0;
+            if (agg) {
+                if (tid < 2) s.tot[tid] = 0;
+                for (int i = tid; i < kWin * 2; i += NT_C) s.win[i >> 1][i & 1] = 0;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s.n_list = 0;
+                s.n_plus = 0;
+                s.n_cl = 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (cur_g >= 0) {
+        for (int b = tid; b < kNH; b += NT_C) {
+            unsigned long long v = s.acc[b];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(cur_g) * kCStride + b]), v);
+            s.acc[b] = 0;
+        }
+        flush<NT_C>(A, nullptr, nullptr, 0, cur_g, acc, s.red);
+    }
+    flush_stats<NT_C>(A, acc, s.red);
+}
+
+// ---------------------------------------------------------------------------
 // scans: host-known length, and device-known length (read from a counter)
 // ---------------------------------------------------------------------------
 
@@ -1608,6 +2165,7 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += al(sizeof(int64_t) * sh.cap) + al(sizeof(int32_t) * sh.cap);
     b += al(sizeof(uint32_t) * sh.n_cta_nh * 2 * (kMaxCard + 1));
     b += 2 * (al(sizeof(int32_t) * sh.list_cap) + al(sizeof(uint64_t) * sh.list_cap));
+    b += al(sizeof(int32_t) * sh.list_cap) + al(sizeof(int32_t) * sh.cap);
     b += sh.with_ts ? al(sizeof(int64_t) * sh.list_cap) : 0;
     b += 2 * al(sizeof(int32_t) * sh.e_cap) + al(sizeof(int64_t) * sh.e_cap);
     b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
@@ -1616,7 +2174,7 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 2 * al(sizeof(int32_t) * sh.cap) + al(sizeof(int64_t) * (sh.cap + 1));
     const int64_t rn = sh.n_cta_nh, rc = int64_t(sh.c_per_sm) * sh.n_cta_c;
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
-    b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 3 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
+    b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 5 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
     return b + 4096;
 }
@@ -1650,6 +2208,8 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->nh_ts = sh.with_ts ? static_cast<int64_t*>(take(sizeof(int64_t) * sh.list_cap)) : nullptr;
     cs->l_i = static_cast<int32_t*>(take(sizeof(int32_t) * sh.list_cap));
     cs->l_xv = static_cast<uint64_t*>(take(sizeof(uint64_t) * sh.list_cap));
+    cs->l_q = static_cast<int32_t*>(take(sizeof(int32_t) * sh.list_cap));
+    cs->nh_flag = static_cast<int32_t*>(take(sizeof(int32_t) * sh.cap));
     cs->lcnt = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
     cs->lfill = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
     cs->loffg = static_cast<int64_t*>(take(sizeof(int64_t) * sh.e_cap));
@@ -1679,6 +2239,8 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->oc_lk = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_lts = static_cast<int64_t*>(take(sizeof(int64_t) * rc * (sh.gs_c / 2)));
     cs->oc_lkey = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
+    cs->oc_pf = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
+    cs->oc_pm = static_cast<uint32_t*>(take(sizeof(uint32_t) * rc * (sh.gs_c / 2)));
     cs->h_total = pinned_word;
     cudaError_t e;
     if ((e = cudaMemsetAsync(cs->lcnt, 0, sizeof(int32_t) * sh.e_cap, st))) return e;
@@ -1717,6 +2279,14 @@ void count_prepare() {
                          int(sizeof(SmemC<512, 4096>)));
     cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(SmemC<256, 2048>)));
+    cudaFuncSetAttribute(k_center_o<512, 8192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemCO<512, 8192>)));
+    cudaFuncSetAttribute(k_center_o<256, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemCO<256, 4096>)));
+    cudaFuncSetAttribute(k_center_o<512, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemCO<512, 4096>)));
+    cudaFuncSetAttribute(k_center_o<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemCO<256, 2048>)));
     });
 }
 
@@ -1725,9 +2295,12 @@ void count_prepare() {
 static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                              const uint32_t* chg_bits, int64_t lo, int64_t n, bool dev, int side,
                              uint64_t* dcounts_side, const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
+    // without the temporal family (and without restricted lists) closed pairs
+    // are searched in (|g|, g) order by k_center_o
+    const bool orient = cs.orient && !(S.fam & kFamT) && cs.r_cap == 0;
     CountArgs A{S, sc, changed, changed_g, chg_bits, lo, n, side, dcounts_side, cs,
                 uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
-                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small == 0 ? 8192 : 4096)), dev};
+                uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small == 0 ? 8192 : 4096)), dev, orient};
     const unsigned gd = blocks_for(cs.e_cap, kScanBlock);
     const unsigned ge = capped(blocks_for(cs.e_cap, 256));
     const int64_t nmax = dev ? cs.cap : n;  // what the grids are made for
@@ -1757,11 +2330,21 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     const bool timed = cs.cev && cs.n_cev && *cs.n_cev < cs.max_cev;
     if (timed) cudaEventRecord(cs.cev[2 * *cs.n_cev], st);
     // three blocks per SM need the tables sized for them
-    switch (cs.center_small == 3 && cs.c_per_sm < 3 ? 1 : cs.center_small) {
-        case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;
-        case 2: k_center<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemC<512, 4096>), st>>>(A); break;
-        case 3: k_center<256, 2048, 3><<<cs.n_cta_c * 3, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;
-        default: k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A); break;
+    const int shape = cs.center_small == 3 && cs.c_per_sm < 3 ? 1 : cs.center_small;
+    if (orient) {
+        switch (shape) {
+            case 0: k_center_o<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemCO<512, 8192>), st>>>(A); break;
+            case 2: k_center_o<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemCO<512, 4096>), st>>>(A); break;
+            case 3: k_center_o<256, 2048, 3><<<cs.n_cta_c * 3, 256, sizeof(SmemCO<256, 2048>), st>>>(A); break;
+            default: k_center_o<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemCO<256, 4096>), st>>>(A); break;
+        }
+    } else {
+        switch (shape) {
+            case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;
+            case 2: k_center<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemC<512, 4096>), st>>>(A); break;
+            case 3: k_center<256, 2048, 3><<<cs.n_cta_c * 3, 256, sizeof(SmemC<256, 2048>), st>>>(A); break;
+            default: k_center<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemC<256, 4096>), st>>>(A); break;
+        }
     }
     if (timed) cudaEventRecord(cs.cev[2 * (*cs.n_cev)++ + 1], st);
     k_d_clean<<<ge, 256, 0, st>>>(A);

@@ -43,6 +43,8 @@ struct CountScratch {
     int64_t* nh_ts = nullptr;        // [list_cap] timestamp of g (temporal family only)
     int32_t* l_i = nullptr;          // [list_cap] index of h in the run
     uint64_t* l_xv = nullptr;        // [list_cap] as nh_xv
+    int32_t* l_q = nullptr;          // [list_cap] position of g1 in the list of N(h)
+    int32_t* nh_flag = nullptr;      // [cap] bit 0: N(h)'s list is sorted by (|g|, g)
     // per hyperedge ID
     int64_t e_cap = 0;
     int32_t* lcnt = nullptr;         // [e_cap] candidate pairs (g1, .) per g1; zero between runs
@@ -70,6 +72,8 @@ struct CountScratch {
     int32_t* oc_lk = nullptr;
     int64_t* oc_lts = nullptr;
     int32_t* oc_lkey = nullptr;      // keys of a global N(g1) in list order
+    int32_t* oc_pf = nullptr;        // the part of a global N(g1) above g1 in (|f|, f) order: f
+    uint32_t* oc_pm = nullptr;       // ... and |g1 & f| | |f| << 16 | f changed << 31
     // restricted incidence lists of a large N(h): for each vertex u of the
     // graph, the neighbours f of h that hold u (a dense index over the
     // graph's vertices, then the lists)
@@ -81,6 +85,7 @@ struct CountScratch {
     int64_t m1_pct = 100;            // visit N(g1) instead of N(h) when |N(g1)| * 100 < |N(h)| * m1_pct
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 3 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
+    bool orient = true;              // search closed pairs in (|g|, g) order (no temporal family, no restricted lists)
     int c_per_sm = 4;                // centre blocks per SM the overflow tables were sized for
     int64_t* h_total = nullptr;      // pinned host word for the list total
     // profiling: events around each centre-kernel launch of a call

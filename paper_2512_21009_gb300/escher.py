@@ -63,7 +63,8 @@ class esc_batch_stats(C.Structure):
                 ("count_launches", C.c_int64), ("v2h_reads", C.c_int64), ("h2v_reads", C.c_int64),
                 ("meta_reads", C.c_int64), ("triads", C.c_int64), ("alg_entries", C.c_int64),
                 ("work", C.c_int64 * 6), ("ms_center", C.c_float), ("center_launches", C.c_int32),
-                ("alg_center", C.c_int64)]
+                ("alg_center", C.c_int64), ("alg_store", C.c_int64), ("alg_build", C.c_int64),
+                ("alg_closed", C.c_int64), ("alg_open", C.c_int64)]
 
 
 class esc_batch(C.Structure):
