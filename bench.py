@@ -37,7 +37,6 @@ sys.path.insert(0, ROOT)
 
 import gen  # noqa: E402
 
-E2E_STEPS = 3   # end-to-end steps (host buffers) after the timed device-resident steps
 METRIC = "hyperedge updates/s with exact triad-count refresh; p50/p99 batch latency"
 UNIT = "updates/s"
 
@@ -155,15 +154,43 @@ def shard(n: int, rank: int, ws: int):
 
 
 def make_stream(args, rank):
+    # warm-up batches, the timed device-resident batches, then as many batches
+    # again for the end-to-end run with host buffers
+    nb = args.warmup + 2 * args.steps
     if args.workload == "tiny":
-        s = gen.random_small(args.seed + rank, 2000, 1000, 2, 8, n_batches=args.warmup + args.steps + E2E_STEPS,
-                             n_ins=50, n_del=50)
+        s = gen.random_small(args.seed + rank, 2000, 1000, 2, 8, n_batches=nb, n_ins=50, n_del=50)
         fam = 3
     else:
-        s = gen.large(seed=args.seed + rank, membership="uniform", scale=args.scale,
-                      n_batches=args.warmup + args.steps + E2E_STEPS, batch_updates=args.batch)
+        s = gen.large(seed=args.seed + rank, membership="uniform", scale=args.scale, n_batches=nb,
+                      batch_updates=args.batch)
         fam = 3
     return s, fam
+
+
+class _LiveRule:
+    """Client copy of one graph's live IDs under the library's ID rule
+    (deletes first; the j-th insert takes the j-th smallest free ID below the
+    high-water mark, then fresh IDs upward).  A stream's delete ranks resolve
+    to IDs through it, and the IDs the library will return are known before a
+    batch is staged; the run checks them afterwards."""
+
+    def __init__(self, n0: int):
+        self.live = np.arange(n0, dtype=np.int64)
+        self.hw = n0
+
+    def step(self, ranks, n_ins):
+        dels = self.live[np.sort(np.asarray(ranks, dtype=np.int64))]
+        keep = np.ones(self.live.size, bool)
+        keep[np.searchsorted(self.live, dels)] = False
+        live = self.live[keep]
+        free = np.ones(self.hw, bool)
+        free[live] = False
+        free = np.flatnonzero(free)
+        take = min(n_ins, free.size)
+        ids = np.concatenate([free[:take], np.arange(self.hw, self.hw + n_ins - take)])
+        self.hw += n_ins - take
+        self.live = np.sort(np.concatenate([live, ids]))
+        return dels, ids
 
 
 def workload_desc(args, s):
@@ -184,9 +211,13 @@ def run_ours(args):
     rank, ws, local, dist = dist_init()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    s, fam = make_stream(args, rank)
+    # several ranks: by default one hypergraph whose count is split across
+    # the ranks (every rank holds the same graph and batches; one all-reduce
+    # of the counts per step); --replicas: an independent graph per rank
+    split = ws > 1 and not args.replicas
+    s, fam = make_stream(args, 0 if split else rank)
     init = s.initial
-    nb = args.warmup + args.steps + E2E_STEPS
+    nb = args.warmup + 2 * args.steps
     n_upd = [b.inserts.n + len(b.del_ranks) for b in s.batches[:nb]]
     cap_e = init.n + max(b.inserts.n for b in s.batches) + 64
     cap_inc = int(init.nnz * 1.6) + 4 * max(b.inserts.nnz for b in s.batches)
@@ -213,24 +244,39 @@ def run_ours(args):
         t1 = time.time()
         tune = g.autotune(sample, reps=1)
         tune["seconds"] = round(time.time() - t1, 2)
-    # With equal inserts and deletes per batch the live IDs stay [0, E0):
-    # the deletes of every batch are its ranks.  Checked after the run from
-    # the IDs the library returns.
-    live_n = init.n
+    # deletes resolved through a client copy of the ID rule; the IDs it
+    # predicts for the inserts are checked against the library's after the run
+    model = _LiveRule(init.n)
+    predicted = []
     dev_batches, host_batches = [], []
     for b in s.batches[:nb]:
-        dels = np.sort(b.del_ranks).astype(np.int32)   # ranks == IDs while live = [0, E0)
+        dels, ids_pred = model.step(b.del_ranks, b.inserts.n)
+        dels = dels.astype(np.int32)
+        predicted.append(ids_pred)
         dev_batches.append((todev(b.inserts.offsets, np.int64), todev(b.inserts.members, np.int32),
                             todev(b.inserts.timestamps, np.int64), todev(dels, np.int32)))
         pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
         host_batches.append((pin(b.inserts.offsets, np.int64), pin(b.inserts.members, np.int32),
                              pin(b.inserts.timestamps, np.int64), pin(dels, np.int32)))
     returned = []
+    if split:
+        g.set_split(rank, ws)
+    # the summed counts of a split graph (hyperedge 30 + vertex 3), on the device
+    shares = torch.zeros(33, dtype=torch.int64, device=dev)
+
+    def reduce_counts():
+        """One all-reduce of this rank's shares of the counts: the int64 images
+        of the uint64 counts, whose sum is exact modulo 2^64."""
+        E.esc_triads(g.h, E.TRIAD_HYPEREDGE, 0, shares[0:30])
+        E.esc_triads(g.h, E.TRIAD_VERTEX, 0, shares[30:33])
+        dist.all_reduce(shares, op=dist.ReduceOp.SUM)
 
     def step(batch, want_ids=True):
         out = np.zeros(batch[0].numel() - 1, np.int32)
         E.esc_apply_batch(g.h, batch[0], batch[1], batch[2], batch[3], out)
-        returned.append((batch[3], out))
+        returned.append(out)
+        if split:
+            reduce_counts()
 
     st = torch.cuda.current_stream(dev)
     g.set_profiling(True)
@@ -241,8 +287,9 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = g.launch_count()
-    lat, cnt_ms, store_ms, alg_bytes, triads = [], [], [], 0, 0
-    cen_ms, cen_bytes, cen_launches = 0.0, 0, 0
+    lat, cnt_ms, store_ms, triads = [], [], [], 0
+    cen_ms, cen_launches = 0.0, 0
+    terms = {"store": 0, "build": 0, "closed": 0, "open": 0}   # algorithmic bytes
     work = [0] * 6
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -255,9 +302,9 @@ def run_ours(args):
         sts = g.stats()
         cnt_ms.append(sts["ms_count_del"] + sts["ms_count_ins"])
         store_ms.append(sts["ms_ingest"] + sts["ms_store"])
-        alg_bytes += 4 * sts["alg_entries"]
+        for k in terms:
+            terms[k] += 4 * sts["alg_" + k]
         cen_ms += sts["ms_center"]
-        cen_bytes += 4 * sts["alg_center"]
         cen_launches += sts["center_launches"]
         triads += sts["triads"]
         work = [a + b for a, b in zip(work, sts["work"])]
@@ -279,46 +326,51 @@ def run_ours(args):
         t1 = time.perf_counter()
         out = np.zeros(hb[0].numel() - 1, np.int32)
         E.esc_apply_batch(g.h, hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), hb[3].numpy(), out)
-        returned.append((hb[3], out))
-        c = g.counts()
+        returned.append(out)
+        if split:
+            reduce_counts()
+            c = {"counts": shares.cpu().numpy()}
+        else:
+            c = g.counts()
         lat_e2e.append((time.perf_counter() - t1) * 1e3)
         h2d += sum(t.numel() * t.element_size() for t in hb)
         d2h += sum(v.nbytes for v in c.values())
     te = time.perf_counter() - te0
     barrier(dist, dev)
-    # check the deletes were the live IDs the library reports
-    for dels, out in returned:
-        d = np.asarray(dels.cpu() if hasattr(dels, "cpu") else dels)
-        if not np.array_equal(np.sort(out), np.sort(d)):
-            raise SystemExit("bench: the live-ID assumption failed (inserts did not reuse the deleted IDs)")
+    # the library's IDs are the ones the client's copy of the ID rule predicted
+    for k, out in enumerate(returned):
+        if not np.array_equal(out, predicted[k]):
+            raise SystemExit(f"bench: batch {k}: the library's IDs differ from the ID rule's prediction")
     upd_timed = sum(n_upd[args.warmup:args.warmup + args.steps])
-    t_max, tot_upd = combine(dist, dev, elapsed, upd_timed)
-    te_max, tot_upd_e2e = combine(dist, dev, te, sum(n_upd[args.warmup + args.steps:nb]))
+    upd_e2e = sum(n_upd[args.warmup + args.steps:nb])
+    if split:
+        # one job: every rank applies the same updates
+        t_max, tot_upd = allreduce_max(dist, elapsed, dev), upd_timed
+        te_max, tot_upd_e2e = allreduce_max(dist, te, dev), upd_e2e
+    else:
+        t_max, tot_upd = combine(dist, dev, elapsed, upd_timed)
+        te_max, tot_upd_e2e = combine(dist, dev, te, upd_e2e)
     if rank != 0:
         return
     hbm, kind = peaks()
     cnt_s = sum(cnt_ms) / 1e3
+    alg_bytes = sum(terms.values())
     count_achieved = alg_bytes / cnt_s / 1e9 if cnt_s > 0 else 0.0
-    # the dominant kernel: k_center, timed with events around each launch
+    # the dominant kernel: the centre kernel, timed with events around each
+    # launch; its algorithmic bytes are the closed-pair and open-path terms
+    cen_bytes = terms["closed"] + terms["open"]
     achieved = cen_bytes / (cen_ms / 1e3) / 1e9 if cen_ms > 0 else 0.0
-    # DRAM traffic of one k_center launch (dram__bytes_read.sum + write.sum)
-    # from the committed ncu summary of the same workload, if there is one
-    traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "k_center_large_uniform.md")
-    if args.workload == "large_uniform" and args.scale == 1.0 and os.path.exists(prof_path):
-        for line in open(prof_path):
-            if line.startswith("- traffic per launch (bytes):"):
-                try:
-                    traffic = int(line.split(":", 1)[1].strip().split()[0])
-                except ValueError:
-                    traffic = None
+    per_launch = cen_bytes / max(cen_launches, 1)
+    traffic, traffic_note = centre_traffic(args, per_launch)
     lat_sorted = sorted(lat)
     res = {
         "metric": METRIC, "value": tot_upd / t_max, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts", "data": "synthetic",
+        "scaling": "strong" if split else "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts",
+        "data": "synthetic",
         "config": {"workload": workload_desc(args, s), "families": "hyperedge (30) + incident-vertex (3)",
-                   "updates_per_step": args.batch, "parallelism": f"replicas x{ws}",
+                   "updates_per_step": args.batch,
+                   "parallelism": f"work split x{ws}" if split else f"replicas x{ws}",
                    "l2": "resident store larger than L2 (129 MB)",
                    "create_s": round(t_create, 2), "autotune": tune},
         "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
@@ -328,17 +380,20 @@ def run_ours(args):
             ["centre_items", "n_g1_build_entries", "pair_pass_visits", "closed_pairs", "slow_t_steps",
              "aggregate_visits"], work)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": kind,
-                     "kernel": "k_center (centre kernel of the triad count)",
-                     "bytes": ("4 B per incidence entry the method reads on behalf of a candidate neighbour g1 "
-                               "of a changed hyperedge h: |g1| + the sum of g1's member degrees, per pair (h, g1)"),
-                     "algorithmic_bytes_per_launch": cen_bytes / max(cen_launches, 1),
+                     "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,
+                     "peak_kind": kind,
+                     "kernel": "k_center_o (centre kernel of the triad count)",
+                     "bytes": ("4 B per int32 entry; the centre kernel's terms: closed pairs, min(|g1|, |g2|) "
+                               "per closed pair {g1, g2} of N(h) counted, and open paths, the sum of g1's member "
+                               "degrees per pair (h, g1)"),
+                     "bytes_per_step_by_term": {k: v / args.steps for k, v in terms.items()},
+                     "algorithmic_bytes_per_launch": per_launch,
                      "ms_per_launch": cen_ms / max(cen_launches, 1), "launches_per_step": cen_launches / args.steps,
                      "count_phase": {"achieved": count_achieved, "frac": count_achieved / hbm,
                                      "algorithmic_bytes_per_step": alg_bytes / args.steps,
                                      "ms_per_step": sum(cnt_ms) / len(cnt_ms)}},
-        "e2e": {"value": tot_upd_e2e / te_max, "unit": UNIT, "h2d_bytes_per_step": h2d // E2E_STEPS,
-                "d2h_bytes_per_step": d2h // E2E_STEPS, "steps": E2E_STEPS,
+        "e2e": {"value": tot_upd_e2e / te_max, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps, "steps": args.steps,
                 "latency_ms": {"p50": float(np.percentile(lat_e2e, 50)), "p99": float(np.percentile(lat_e2e, 99))}},
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -349,50 +404,155 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
-# the oracle on a bounded sample
+# DRAM traffic of the centre kernel, from the committed ncu summary
 # ---------------------------------------------------------------------------
 
-def _oracle_sample(s, n_updates, rng_seed=0):
-    """Time the oracle's update of the counts for a sample of one batch's
-    updates on the full-size hypergraph: triads holding a sampled deleted
-    hyperedge (old graph) and a sampled inserted one (new graph), each by the
-    oracle's own enumeration.  Returns (seconds, updates)."""
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_center_o_large_uniform.md")
+COUNT_SRC = os.path.join(ROOT, "paper_2512_21009_gb300", "csrc", "count.cu")
+
+
+def centre_traffic(args, alg_bytes_per_launch):
+    """DRAM bytes (read + write) of one centre-kernel launch: the ratio of
+    DRAM bytes to algorithmic bytes that an ncu capture of a smaller case of
+    the same workload measured, times this launch's algorithmic bytes.  Only
+    when the summary was taken on the kernel source that is built now (its
+    sha256 is recorded there); otherwise None."""
+    import hashlib
+    if args.workload != "large_uniform" or not os.path.exists(TRAFFIC_SUMMARY):
+        return None, "no capture of this workload"
+    with open(COUNT_SRC, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    ratio, src = None, None
+    for line in open(TRAFFIC_SUMMARY):
+        if line.startswith("- dram bytes per algorithmic byte:"):
+            try:
+                ratio = float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                ratio = None
+        if line.startswith("- source sha256 of count.cu:"):
+            src = line.split(":", 1)[1].strip().strip("`")
+    if ratio is None or src != sha:
+        return None, "the centre kernel changed since the last ncu capture"
+    return ratio * alg_bytes_per_launch, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller case of "
+                                          "this workload on this kernel source, scaled by algorithmic bytes "
+                                          f"({ratio:.3f} DRAM bytes per algorithmic byte; {TRAFFIC_SUMMARY[len(ROOT) + 1:]})")
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample, on all host cores
+# ---------------------------------------------------------------------------
+
+ORACLE_KMAX = 16   # cardinality cap of the sampled updates (see oracle_sample)
+
+
+def _sorted_csr(c):
+    """CSR with every hyperedge's members sorted (the oracle's input form)."""
+    sizes = np.diff(c.offsets)
+    rows = np.repeat(np.arange(c.n), sizes)
+    return np.ascontiguousarray(c.offsets, dtype=np.int64), np.ascontiguousarray(
+        c.members[np.lexsort((c.members, rows))], dtype=np.int32)
+
+
+class _OracleBatch:
+    """The old and new graph of the stream's first batch, as the oracle takes
+    them: the deleted hyperedges are positions of the old graph (IDs equal
+    positions there), the inserted ones the positions appended to the kept
+    hyperedges in the new graph.  Positions stand in for IDs: the hyperedge
+    and incident-vertex families do not depend on IDs."""
+
+    def __init__(self, s):
+        init, b = s.initial, s.batches[0]
+        self.off0, self.mem0 = _sorted_csr(init)
+        sizes0 = np.diff(self.off0)
+        self.dels = np.sort(np.asarray(b.del_ranks, dtype=np.int64))
+        keep = np.ones(init.n, bool)
+        keep[self.dels] = False
+        ioff, imem = _sorted_csr(b.inserts)
+        sizes1 = np.concatenate([sizes0[keep], np.diff(ioff)])
+        self.off1 = np.concatenate([[0], np.cumsum(sizes1)]).astype(np.int64)
+        self.mem1 = np.concatenate([self.mem0[np.repeat(keep, sizes0)], imem]).astype(np.int32)
+        self.ins = np.arange(int(keep.sum()), int(keep.sum()) + b.inserts.n, dtype=np.int64)
+        self.del_small = self.dels[sizes0[self.dels] <= ORACLE_KMAX]
+        self.ins_small = self.ins[np.diff(ioff) <= ORACLE_KMAX]
+        self.share = (self.del_small.size + self.ins_small.size) / max(1, self.dels.size + self.ins.size)
+
+
+def oracle_sample(ob, threads, per_thread, seed):
+    """Wall time of the oracle's count change for a sample of the batch's
+    updates, on `threads` host threads: each thread takes per_thread sampled
+    updates (deletes and inserts alternately) and runs the oracle's
+    enumeration of the hyperedge triads (orc_count_containing) and of the
+    incident-vertex witness assignments (orc_vertex_containing) holding its
+    deleted hyperedges on the old graph and its inserted ones on the new graph.
+    Updates are drawn uniformly among those of cardinality <= ORACLE_KMAX: the
+    oracle's time per update grows with the cardinality (seconds at 10
+    members, half a minute at 50, minutes at 200), so the sample's rate
+    overstates the oracle's rate over the whole batch.  Returns (seconds,
+    updates)."""
+    from concurrent.futures import ThreadPoolExecutor
     from oracle import oracle as O
-    init = s.initial
-    off = init.offsets
-    # the oracle wants sorted member lists
-    mem = init.members.copy()
-    for i in range(init.n):
-        a, b = off[i], off[i + 1]
-        mem[a:b] = np.sort(mem[a:b])
-    ts = init.timestamps
-    ids = np.arange(init.n, dtype=np.int32)
-    rng = np.random.default_rng(rng_seed)
-    half = max(1, n_updates // 2)
-    sel = np.sort(rng.choice(init.n, size=half, replace=False))
+    rng = np.random.default_rng(seed)
+    n = threads * per_thread
+    nd = min(n // 2, ob.del_small.size)
+    ni = min(n - nd, ob.ins_small.size)
+    sd = np.sort(rng.choice(ob.del_small, size=nd, replace=False))
+    si = np.sort(rng.choice(ob.ins_small, size=ni, replace=False))
+
+    def work(t):
+        a, c = sd[t::threads], si[t::threads]
+        if a.size:
+            O.count_containing(ob.off0, ob.mem0, None, None, 0, O.FAM_HYPEREDGE, a)
+            O.count_vertex_containing(ob.off0, ob.mem0, a)
+        if c.size:
+            O.count_containing(ob.off1, ob.mem1, None, None, 0, O.FAM_HYPEREDGE, c)
+            O.count_vertex_containing(ob.off1, ob.mem1, c)
+
     t0 = time.perf_counter()
-    O.count_containing(off, mem, ts, ids, 0, O.FAM_HYPEREDGE, sel)
-    t1 = time.perf_counter()
-    # inserted side: the same enumeration around the same number of hyperedges
-    sel2 = np.sort(rng.choice(init.n, size=half, replace=False))
-    O.count_containing(off, mem, ts, ids, 0, O.FAM_HYPEREDGE, sel2)
-    t2 = time.perf_counter()
-    return (t1 - t0) + (t2 - t1), 2 * half
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(work, range(threads)))
+    return time.perf_counter() - t0, nd + ni
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _sample_desc(ob, upd, threads, per_thread, secs=None):
+    t = f"; {secs:.1f} s" if secs is not None else ""
+    return (f"{upd} updates of the first batch ({per_thread} per thread, deletes on the old graph and inserts on "
+            f"the new one), drawn among its updates of cardinality <= {ORACLE_KMAX} ({ob.share:.1%} of them; larger "
+            f"ones cost the oracle far more, so this rate overstates the oracle's): the oracle's enumeration of "
+            f"the hyperedge triads and incident-vertex instances holding them on the full graph, {threads} "
+            f"threads{t}")
 
 
 def cpu_baseline(args, s, budget_s=20.0):
     from oracle import oracle as O
     O.build()
-    n = 2
-    secs, upd = _oracle_sample(s, n)
+    ob = _OracleBatch(s)
+    threads = host_threads()
+    per_thread = 1
+    secs, upd = oracle_sample(ob, threads, per_thread, seed=1)
     # grow the sample until it takes a meaningful share of the budget
-    while secs < budget_s / 4 and n < 4096:
-        n *= 2
-        secs, upd = _oracle_sample(s, n, rng_seed=n)
-    return {"value": upd / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{upd} updates ({upd // 2} deletes + {upd // 2} inserts) of one batch: the oracle's "
-                       f"enumeration of every triad holding a sampled hyperedge (hyperedge family) on the full "
-                       f"{s.initial.n:,}-hyperedge graph, single thread; {secs:.1f} s")}
+    while secs < budget_s / 3 and per_thread < 16:
+        per_thread *= 2
+        secs, upd = oracle_sample(ob, threads, per_thread, seed=per_thread)
+    return {"value": upd / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu": cpu_model(), "sample": _sample_desc(ob, upd, threads, per_thread, secs)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -402,14 +562,15 @@ def run_reference(args):
     s, fam = make_stream(args, 0)
     from oracle import oracle as O
     O.build()
-    per_step = max(2, args.ref_updates_per_step)
+    ob = _OracleBatch(s)
+    threads = host_threads()
+    per_thread = 1
+    # warm-up steps (the oracle has no warm-up effects): one update each
     for k in range(args.warmup):
-        _oracle_sample(s, per_step, rng_seed=1000 + k)
-    secs = 0.0
-    upd = 0
-    lat = []
+        oracle_sample(ob, 1, 1, seed=1000 + k)
+    secs, upd, lat = 0.0, 0, []
     for k in range(args.steps):
-        t, u = _oracle_sample(s, per_step, rng_seed=k)
+        t, u = oracle_sample(ob, threads, per_thread, seed=k)
         secs += t
         upd += u
         lat.append(t * 1e3)
@@ -418,10 +579,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "uint64", "data": "synthetic",
-        "config": {"workload": workload_desc(args, s), "families": "hyperedge (30)"},
+        "config": {"workload": workload_desc(args, s), "families": "hyperedge (30) + incident-vertex (3)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} updates per step, oracle enumeration on the full graph"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
+                         "sample": "per step: " + _sample_desc(ob, threads * per_thread, threads, per_thread)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -1084,6 +1245,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--replicas", action="store_true",
+                    help="several ranks: an independent graph per rank instead of one graph split across them")
     ap.add_argument("--no-graph-launch", action="store_true", help="serving: launch kernel by kernel")
     ap.add_argument("--ref-updates-per-step", type=int, default=4)
     args = ap.parse_args()

@@ -52,6 +52,36 @@
  * were.  esc_last_error() gives a one-line reason for the last failure.
  *
  * Threads.  A graph or group may be used by one host thread at a time.
+ *
+ * Environment switches, read when a graph or group is created.  They select
+ * internal paths of the counter for tests and measurements; results are the
+ * same exact counts whatever they are set to.  Unset (the default) is what the
+ * library is tuned for.
+ *   ESC_COUNT_ORIENT=0        count closed pairs with the earlier centre
+ *                             kernel (both sides of every closed pair visited,
+ *                             N(h) marked inside N(g1)) instead of searching
+ *                             each closed pair once in (|g|, g) order.
+ *   ESC_COUNT_LIST=n          neighbour-list arena of one count run, in
+ *                             entries (>= 4096): a small arena forces several
+ *                             runs per batch side.
+ *   ESC_COUNT_TABLE_SLOTS=n   slots of the per-block overflow hash tables (a
+ *                             power of two >= 1024).
+ *   ESC_COUNT_SMEM_SLOTS=n    cap on shared-memory hash-table slots (a power
+ *                             of two >= 64): small values force the
+ *                             global-table, partitioned and in-place paths.
+ *   ESC_COUNT_RPOOL=n         int32 entries of the restricted-list pool
+ *                             (0, the default, disables restricted lists).
+ *   ESC_COUNT_RMIN=n          neighbourhood size from which restricted lists
+ *                             are built when the pool is enabled.
+ *   ESC_COUNT_BIGNH=n         neighbourhood size (>= 16) above which N(h) gets
+ *                             a hash table and a membership filter.
+ *   ESC_COUNT_M1PCT=p         weight (percent) of a visit of N(g1) against a
+ *                             visit of N(h) in the per-pair choice of which
+ *                             side to scan.
+ *   ESC_CENTER_SMALL=s        centre-kernel launch shape, as
+ *                             esc_tune_result.center_shape (0..3).
+ *   ESC_CALL_GRAPH=1          graph launch on from creation (as
+ *                             esc_set_graph_launch).
  */
 #ifndef ESCHER_H
 #define ESCHER_H
@@ -70,7 +100,9 @@ typedef enum {
     ESC_ERR_OUT_OF_MEMORY = 3, /* a preallocated capacity would be exceeded  */
     ESC_ERR_UNSUPPORTED = 4,   /* a size beyond a documented engine limit, a
                                   family not maintained, another window   */
-    ESC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out              */
+    ESC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out (reserved:
+                                  no kernel of this build waits on the device,
+                                  so no call returns it)                      */
     ESC_ERR_CUDA = 6,          /* a CUDA runtime call failed                 */
     ESC_ERR_BUSY = 7           /* a server's queue is full; nothing was kept */
 } esc_status;
@@ -461,6 +493,29 @@ esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he, const int6
  * ------------------------------------------------------------------------ */
 esc_status esc_set_graph_launch(esc_graph* g, int32_t on);
 esc_status esc_group_set_graph_launch(esc_group* grp, int32_t on);
+
+/* ------------------------------------------------------------------------
+ * Work split of one hypergraph across ranks (one process per GPU).  The
+ * paper runs on one GPU; this is how the count of one graph spreads over
+ * several.  Every rank creates the same graph and applies the same batches
+ * (the ID rule is deterministic, so the replicas stay identical); after
+ * esc_set_split(g, rank, world) each rank counts only its share of every
+ * batch's changed hyperedges: per side (deleted, inserted), the contiguous
+ * range of them whose neighbourhood sizes (sum of member degrees, plus one
+ * each) fall in the rank's equal part of the side's total.  Algorithm 3's
+ * count change is a sum over the changed hyperedges, each triad counted at
+ * its changed member of smallest ID, so the shares of the ranks add up to
+ * the whole change.  From the call on, esc_triads / esc_group_triads return
+ * this rank's share: the counts are the sum of the shares over all ranks,
+ * modulo 2^64 (one all-reduce of at most 129 uint64 per family read).  Rank
+ * 0 keeps the counts held at the call; the other ranks' shares start at
+ * zero.  esc_local_triads still returns whole counts.  The split is set once
+ * per graph and needs graph launch off (esc_set_graph_launch then refuses
+ * to turn it on).  world >= 2, 0 <= rank < world.
+ * Errors: INVALID_ARG, UNSUPPORTED (already split, or graph launch on), CUDA.
+ * ------------------------------------------------------------------------ */
+esc_status esc_set_split(esc_graph* g, int32_t rank, int32_t world);
+esc_status esc_group_set_split(esc_group* grp, int32_t rank, int32_t world);
 
 /* ------------------------------------------------------------------------
  * Autotuning.  The counter's launch shape (centre blocks per SM x threads:

@@ -4,6 +4,7 @@
 // inputs to the device, launches the kernels of store.cu and count.cu in
 // order on the graph's stream, and reads back status and counts.  Every step
 // of the update and of the counting runs in those kernels.
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -482,6 +483,13 @@ static esc_status stage(Engine* E, const T* src, size_t n, T* dst_area, int k, s
 
 constexpr int kFixedRuns = 1;  // count runs per side in the captured sequence (the arena holds a batch)
 
+// NVTX range around the host-side launch of one stage (header-only NVTX v3:
+// it costs nothing unless a profiler is attached)
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
 // The device work of one call, in order: ingest, count on the old graph,
 // delete, insert, count on the new graph, fold.  fixed: the sequence does not
 // depend on the call's sizes (every kernel reads them on the device; count
@@ -490,35 +498,48 @@ static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStr
                                    bool prof = false) {
     const Store& S = E->S;
     cudaError_t e;
-    if ((e = store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc))) return e;
+    {
+        Range r("escher: ingest");
+        if ((e = store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc))) return e;
+    }
     if (fixed) {
         // the inserted side's runs must fit the sequence before anything changes
         if ((e = count_precheck_fixed(S, C, E->cs, E->max_u, kFixedRuns, st, lc))) return e;
         if ((e = store_latch(C, st, lc))) return e;
     }
     if (prof) cudaEventRecord(E->ev[1], st);
-    if (fixed)
-        e = count_launch_fixed(S, C.sc, C.del, C.del_g, S.delb, C.dims + 2, 0, S.dcounts, E->cs, E->max_u,
-                               kFixedRuns, st, lc);
-    else
-        e = count_launch(S, C.sc, C.del, C.del_g, S.delb, 0, C.n_del, 0, S.dcounts, E->cs, E->max_u, st, lc);
+    {
+        Range r("escher: count, deleted side");
+        if (fixed)
+            e = count_launch_fixed(S, C.sc, C.del, C.del_g, S.delb, C.dims + 2, 0, S.dcounts, E->cs, E->max_u,
+                                   kFixedRuns, st, lc);
+        else
+            e = count_launch(S, C.sc, C.del, C.del_g, S.delb, 0, C.n_del, 0, S.dcounts, E->cs, E->max_u, st, lc);
+    }
     if (e) return e;
     if (fixed) {
         // a failed count (the retry status) must leave the store unchanged
         if ((e = store_latch(C, st, lc))) return e;
     }
     if (prof) cudaEventRecord(E->ev[2], st);
-    if ((e = store_delete(S, C, E->sm_count, st, lc))) return e;
-    if ((e = store_insert(S, C, E->sm_count, st, lc))) return e;
+    {
+        Range r("escher: store update");
+        if ((e = store_delete(S, C, E->sm_count, st, lc))) return e;
+        if ((e = store_insert(S, C, E->sm_count, st, lc))) return e;
+    }
     if (prof) cudaEventRecord(E->ev[3], st);
     uint64_t* dins = S.dcounts + int64_t(S.n_graphs) * kCStride;
-    if (fixed)
-        e = count_launch_fixed(S, C.sc, C.ids, C.ins_g, S.insb, C.dims + 1, 1, dins, E->cs, E->max_u, kFixedRuns,
-                               st, lc);
-    else
-        e = count_launch(S, C.sc, C.ids, C.ins_g, S.insb, 0, C.n_ins, 1, dins, E->cs, E->max_u, st, lc);
+    {
+        Range r("escher: count, inserted side");
+        if (fixed)
+            e = count_launch_fixed(S, C.sc, C.ids, C.ins_g, S.insb, C.dims + 1, 1, dins, E->cs, E->max_u,
+                                   kFixedRuns, st, lc);
+        else
+            e = count_launch(S, C.sc, C.ids, C.ins_g, S.insb, 0, C.n_ins, 1, dins, E->cs, E->max_u, st, lc);
+    }
     if (e) return e;
     if (prof) cudaEventRecord(E->ev[4], st);
+    Range r("escher: fold counts");
     return store_finish(S, C, E->sm_count, st, lc);
 }
 
@@ -992,12 +1013,15 @@ static esc_status local_triads(Engine* E, int64_t n, const int32_t* ids, uint64_
     cudaMemsetAsync(dside, 0, sizeof(uint64_t) * kCStride, st);
     LaunchCounter lc;
     if (ms_out) cudaEventRecord(E->ev[0], st);
+    // local counts are whole counts, whatever work split the graph has
+    CountScratch whole = E->cs;
+    whole.split_world = 1;
     if (n > 0) {
         k_mark_sel<<<unsigned((n + 255) / 256), 256, 0, st>>>(S, E->d_sc, d_ids, n, d_glob);
         k_latch_api<<<1, 1, 0, st>>>(E->d_sc);
         for (int64_t lo = 0; lo < n; lo += E->cs.cap) {
             int64_t hi = lo + E->cs.cap < n ? lo + E->cs.cap : n;
-            cudaError_t e = count_launch(S, E->d_sc, d_glob, nullptr, S.insb, lo, hi, 1, dside, E->cs,
+            cudaError_t e = count_launch(S, E->d_sc, d_glob, nullptr, S.insb, lo, hi, 1, dside, whole,
                                          E->max_u, st, lc);
             if (e != cudaSuccess) { cleanup(); return E->cuda_fail(e, "count"); }
         }
@@ -1117,6 +1141,22 @@ esc_status group_limits(const esc_group* grp, int32_t* n_graphs, int64_t* max_up
 }
 }  // namespace esc
 
+namespace esc {
+static esc_status set_split(Engine* E, int32_t rank, int32_t world) {
+    if (world < 2 || rank < 0 || rank >= world) return E->fail(ESC_ERR_INVALID_ARG, "bad rank or world size");
+    if (E->cs.split_world > 1) return E->fail(ESC_ERR_UNSUPPORTED, "the work split is already set");
+    if (E->graph_mode) return E->fail(ESC_ERR_UNSUPPORTED, "the work split needs graph launch off");
+    if (rank != 0) {
+        // the counts held now stay with rank 0; the other ranks' shares start at zero
+        ESC_CU(cudaMemsetAsync(E->S.counts, 0, sizeof(uint64_t) * int64_t(E->G) * kCStride, E->st), "zero counts");
+        ESC_CU(cudaStreamSynchronize(E->st), "sync");
+    }
+    E->cs.split_rank = rank;
+    E->cs.split_world = world;
+    return ESC_OK;
+}
+}  // namespace esc
+
 extern "C" {
 
 const char* esc_version(void) { return "escher-gb300 0.1 (sm_103a)"; }
@@ -1214,8 +1254,13 @@ esc_status esc_group_autotune(esc_group* grp, int32_t graph, int64_t n_ids, cons
     return esc::autotune(grp->e, n_ids, glob.data(), reps, out);
 }
 
+esc_status esc_group_set_split(esc_group* grp, int32_t rank, int32_t world) {
+    return grp ? esc::set_split(grp->e, rank, world) : ESC_ERR_INVALID_ARG;
+}
+
 esc_status esc_group_set_graph_launch(esc_group* grp, int32_t on) {
     if (!grp) return ESC_ERR_INVALID_ARG;
+    if (on && grp->e->cs.split_world > 1) return grp->e->fail(ESC_ERR_UNSUPPORTED, "graph launch with a work split");
     cudaError_t e = esc::set_graph_mode(grp->e, on != 0);
     return e == cudaSuccess ? ESC_OK : grp->e->cuda_fail(e, "graph mode");
 }
@@ -1322,8 +1367,13 @@ esc_status esc_autotune(esc_graph* g, int64_t n_ids, const int32_t* ids, int32_t
     return esc::autotune(g->e, n_ids, ids, reps, out);
 }
 
+esc_status esc_set_split(esc_graph* g, int32_t rank, int32_t world) {
+    return g ? esc::set_split(g->e, rank, world) : ESC_ERR_INVALID_ARG;
+}
+
 esc_status esc_set_graph_launch(esc_graph* g, int32_t on) {
     if (!g) return ESC_ERR_INVALID_ARG;
+    if (on && g->e->cs.split_world > 1) return g->e->fail(ESC_ERR_UNSUPPORTED, "graph launch with a work split");
     cudaError_t e = esc::set_graph_mode(g->e, on != 0);
     return e == cudaSuccess ? ESC_OK : g->e->cuda_fail(e, "graph mode");
 }

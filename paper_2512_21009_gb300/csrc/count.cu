@@ -1597,7 +1597,8 @@ struct SmemCO {
     int warp_tmp[32];
     long long red[NW_C];
     long long item;
-    int n_list, n_plus, n_cl, n_c;
+    int n_list, n_plus, n_cl, n_c, n_li, n_lx, any_big;
+    int32_t li_I[LCH], li_X[LCH];  // the h of a chunk with 2 <= |h&g1| <= kIC, and with |h&g1| > kWin
     uint32_t tot[2];
     uint32_t win[kWin][2];
     // the changed hyperedges h of a chunk
@@ -1737,18 +1738,41 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
         int bw = 32;
         while (bw < Sm::BLOOM_W && (long long)bw * 4 < u1 / P) bw <<= 1;
         for (int p = 0; p < P; ++p) {
-            // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p)
-            for (int m0 = 0; m0 < k1; m0 += NT_C) {
-                const int n = min(NT_C, k1 - m0);
-                const int tot = load_segment<NT_C>(S, g1mem + m0, n, s.seg_off, nullptr, s.seg_pre, s.warp_tmp);
-                for (int e = tid; e < tot; e += NT_C) {
-                    const int m = seg_member(s.seg_pre, n, e);
-                    const int32_t f = v2h[s.seg_off[m] + (e - s.seg_pre[m])];
-                    if (f == g1) continue;
-                    if (P > 1 && part_of(f, P) != p) continue;
+            // ---- N(g1): x = |g1 & f| per distinct f != g1 (of partition p):
+            //      one warp per member, its lanes over the member's hyperedges;
+            //      a member of degree >= kBigDeg is left to the whole block
+            constexpr int kBigDeg = 256;
+            if (tid == 0) s.any_big = 0;
+            __syncthreads();
+            for (int m = wid; m < k1; m += NW_C) {
+                const int32_t v = g1mem[m];
+                const int d = S.v_deg[v];
+                if (d >= kBigDeg) {
+                    if (lane == 0) s.any_big = 1;
+                    continue;
+                }
+                const int32_t* lst = v2h + S.v_off[v];
+                for (int e = lane; e < d; e += 32) {
+                    const int32_t f = lst[e];
+                    if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
                     tab_insert(T1, f, 1u, 0, A.sc);
                 }
-                acc.n_v2h += (tid < tot) ? (tot - tid + NT_C - 1) / NT_C : 0;
+                acc.n_v2h += (lane < d) ? (d - lane + 31) / 32 : 0;
+            }
+            __syncthreads();
+            if (s.any_big) {
+                for (int m = 0; m < k1; ++m) {
+                    const int32_t v = g1mem[m];
+                    const int d = S.v_deg[v];
+                    if (d < kBigDeg) continue;
+                    const int32_t* lst = v2h + S.v_off[v];
+                    for (int e = tid; e < d; e += NT_C) {
+                        const int32_t f = lst[e];
+                        if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
+                        tab_insert(T1, f, 1u, 0, A.sc);
+                    }
+                    acc.n_v2h += (tid < d) ? (d - tid + NT_C - 1) / NT_C : 0;
+                }
                 __syncthreads();
             }
             const int n1 = min(s.n_list, T1.list_cap);
@@ -1799,28 +1823,81 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                 const int64_t lbeg = l_lo + ch * LCH;
                 const int nh = int(min(lbeg + LCH, l_hi) - lbeg);
                 __syncthreads();
-                if (tid < nh) {
-                    const int64_t e = lbeg + tid;
-                    const int32_t li = cs.l_i[e];
-                    const uint64_t xv1 = cs.l_xv[e];
-                    const int32_t h = A.changed[A.lo + li];
-                    s.hh[tid] = h;
-                    s.hk[tid] = S.h_card[h];
-                    s.hx[tid] = int(xv1 & kXMask);
-                    s.hvf[tid] = int32_t(uint32_t(xv1 >> 32));
-                    s.hmem[tid] = h2v + S.h_off[h];
-                    s.hnb[tid] = cs.nh_off[li] - R.base;
-                    s.hnn[tid] = cs.nh_n[li];
-                    s.htcap[tid] = cs.nh_tcap[li];
-                    s.htoff[tid] = cs.nh_toff[li];
-                    // sorted list: the neighbours above g1 start after g1's place
-                    s.hpos[tid] = (cs.nh_flag[li] & 1) ? cs.l_q[e] : -1;
-                    s.hIn[tid] = 0;
+                if (wid == 0) {
+                    // lane l: the chunk's l-th h, its pass mode and work; the
+                    // h with work listed in hord with the prefix of their work
+                    // in hpre; the h needing h & g1 listed, and those whose
+                    // |h & g1| lies outside the x window
+                    const int l = lane;
+                    int work = 0, xh1 = 0;
+                    if (l < nh) {
+                        const int64_t e = lbeg + l;
+                        const int32_t li = cs.l_i[e];
+                        const uint64_t xv1 = cs.l_xv[e];
+                        const int32_t h = A.changed[A.lo + li];
+                        xh1 = int(xv1 & kXMask);
+                        const int hnn = cs.nh_n[li], htcap = cs.nh_tcap[li];
+                        // sorted list: the neighbours above g1 start after g1's place
+                        const int hpos = (cs.nh_flag[li] & 1) ? cs.l_q[e] : -1;
+                        s.hh[l] = h;
+                        s.hk[l] = S.h_card[h];
+                        s.hx[l] = xh1;
+                        s.hvf[l] = int32_t(uint32_t(xv1 >> 32));
+                        s.hmem[l] = h2v + S.h_off[h];
+                        s.hnb[l] = cs.nh_off[li] - R.base;
+                        s.hnn[l] = hnn;
+                        s.htcap[l] = htcap;
+                        s.htoff[l] = cs.nh_toff[li];
+                        s.hpos[l] = hpos;
+                        s.hIn[l] = 0;
+                        int mode;
+                        if (hpos >= 0) {
+                            const int sfx = hnn - hpos - 1;
+                            if (htcap > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
+                                mode = 1;
+                                work = n_plus;
+                            } else {
+                                mode = 0;
+                                work = sfx;
+                            }
+                        } else if (htcap > 0) {
+                            mode = 1;
+                            work = n_plus;
+                        } else {
+                            mode = 3;
+                            work = hnn;
+                        }
+                        s.hmode[l] = mode;
+                    }
+                    int inc = work;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += v;
+                    }
+                    const unsigned lt = (1u << lane) - 1u;
+                    const unsigned has = __ballot_sync(0xffffffffu, work > 0);
+                    if (work > 0) {
+                        const int c = __popc(has & lt);
+                        s.hord[c] = l;
+                        s.hpre[c] = inc - work;
+                    }
+                    const bool needI = l < nh && xh1 >= 2 && xh1 <= kIC;
+                    const bool needX = l < nh && xh1 > kWin;
+                    const unsigned bI = __ballot_sync(0xffffffffu, needI);
+                    const unsigned bX = __ballot_sync(0xffffffffu, needX);
+                    if (needI) s.li_I[__popc(bI & lt)] = l;
+                    if (needX) s.li_X[__popc(bX & lt)] = l;
+                    if (lane == 31) {
+                        s.hpre[__popc(has)] = inc;
+                        s.n_c = __popc(has);
+                        s.n_li = __popc(bI);
+                        s.n_lx = __popc(bX);
+                    }
                 }
                 __syncthreads();
-                for (int l = 0; l < nh; ++l) {
-                    const int xh1 = s.hx[l];
-                    if (xh1 < 2 || xh1 > kIC) continue;
+                for (int li = 0; li < s.n_li; ++li) {
+                    const int l = s.li_I[li];
                     const int kh = s.hk[l];
                     const bool from_h = kh <= k1;
                     const int32_t* a = from_h ? s.hmem[l] : g1mem;
@@ -1834,40 +1911,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         }
                     }
                 }
-                if (tid == 0) {
-                    // work of the pair pass per h; the h with work are listed
-                    // in hord with the prefix of their work in hpre
-                    int run = 0, nc = 0;
-                    for (int l = 0; l < nh; ++l) {
-                        int mode, work;
-                        if (s.hpos[l] >= 0) {
-                            const int sfx = s.hnn[l] - s.hpos[l] - 1;
-                            if (s.htcap[l] > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
-                                mode = 1;
-                                work = n_plus;
-                            } else {
-                                mode = 0;
-                                work = sfx;
-                            }
-                        } else if (s.htcap[l] > 0) {
-                            mode = 1;
-                            work = n_plus;
-                        } else {
-                            mode = 3;
-                            work = s.hnn[l];
-                        }
-                        s.hmode[l] = mode;
-                        if (work > 0) {
-                            s.hord[nc] = l;
-                            s.hpre[nc] = run;
-                            ++nc;
-                            run += work;
-                        }
-                    }
-                    s.hpre[nc] = run;
-                    s.n_c = nc;
-                }
-                __syncthreads();
+                if (s.n_li > 0) __syncthreads();
                 const int nc = s.n_c;
                 const int wtot = s.hpre[nc];
                 if (tid == 0) acc.w[2] += (unsigned long long)wtot;
@@ -1988,8 +2032,8 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         const int xh1 = s.hx[tid];
                         atomicAdd(&s.sub[tid][(xh1 != k1 - xh1 ? 2 : 0) | (s.hk[tid] > xh1 ? 1 : 0)], 1u);
                     }
-                    for (int l = 0; l < nh; ++l) {  // x = |g1| - |h&g1| outside the window
-                        if (s.hx[l] <= kWin) continue;
+                    for (int lx = 0; lx < s.n_lx; ++lx) {  // x = |g1| - |h&g1| outside the window
+                        const int l = s.li_X[lx];
                         const int xstar = k1 - s.hx[l];
                         for (int q = tid; q < n1; q += NT_C)
                             if (int(T1.vals[T1.list[q]]) == xstar)
@@ -2014,20 +2058,8 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         s.xc[tid][0] = s.xc[tid][1] = 0;
                     }
                 }
-                __syncthreads();
-                // fold the warp histograms of this chunk
-                for (int b = tid; b < kNH; b += NT_C) {
-                    unsigned long long v = 0;
-                    for (int w = 0; w < NW_C; ++w) {
-                        v += s.hist[w][b];
-                        v -= s.hneg[w][b];
-                        s.hist[w][b] = 0;
-                        s.hneg[w][b] = 0;
-                    }
-                    s.acc[b] += v;
-                }
-                __syncthreads();
             }  // chunks
+            __syncthreads();
             tab_clear<NT_C>(T1, n1);
             for (int i = tid; i < bw; i += NT_C) s.bloom[i] = 0;
             if (agg) {
@@ -2040,6 +2072,17 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                 s.n_plus = 0;
                 s.n_cl = 0;
             }
+        }
+        // fold the warp histograms of this item
+        for (int b = tid; b < kNH; b += NT_C) {
+            unsigned long long v = 0;
+            for (int w = 0; w < NW_C; ++w) {
+                v += s.hist[w][b];
+                v -= s.hneg[w][b];
+                s.hist[w][b] = 0;
+                s.hneg[w][b] = 0;
+            }
+            s.acc[b] += v;
         }
     }
     __syncthreads();
@@ -2357,6 +2400,39 @@ cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, co
                          const uint32_t* chg_bits, int64_t lo, int64_t hi, int side, uint64_t* dcounts_side,
                          const CountScratch& cs, int64_t max_u, cudaStream_t st, LaunchCounter& lc) {
     count_prepare();
+    if (cs.split_world > 1 && hi > lo) {
+        // this rank's share of the side, by the prefix of the neighbourhood
+        // sizes (a side holds at most cs.cap changed hyperedges)
+        const int64_t n = std::min<int64_t>(hi - lo, cs.cap);
+        k_nh_size<<<blocks_for(n * 32, 256), 256, 0, st>>>(S, sc, changed, lo, n, nullptr, cs.sizes, max_u,
+                                                           cs.big_nh);
+        const unsigned gb = blocks_for(n, kScanBlock);
+        k_scan_sums<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, n, nullptr, cs.block_sums);
+        k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, gb, nullptr);
+        k_scan_apply<int32_t><<<gb, kScanNT, 0, st>>>(cs.sizes, n, nullptr, cs.block_sums, cs.nh_off);
+        lc.total += 4;
+        std::vector<int64_t> pre(size_t(n) + 1);
+        cudaError_t e = cudaMemcpyAsync(pre.data(), cs.nh_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        const int64_t W = cs.split_world, r = cs.split_rank, T = pre[n] + n;
+        // owner of i: floor((pre[i] + i) * W / T), non-decreasing in i
+        auto owner = [&](int64_t i) { return int64_t((__int128(pre[i] + i) * W) / T); };
+        int64_t a = 0, b = n;
+        while (a < n && owner(a) < r) ++a;
+        b = a;
+        while (b < n && owner(b) == r) ++b;
+        CountScratch one = cs;
+        one.split_world = 1;
+        if (b > a)
+            if ((e = count_launch(S, sc, changed, changed_g, chg_bits, lo + a, lo + b, side, dcounts_side, one,
+                                  max_u, st, lc)))
+                return e;
+        if (hi - lo > n)  // never with the engine's sizes; kept exact regardless
+            return count_launch(S, sc, changed, changed_g, chg_bits, lo + n, hi, side, dcounts_side, cs, max_u, st,
+                                lc);
+        return cudaSuccess;
+    }
     for (int64_t a = lo; a < hi; a += cs.cap) {
         const int64_t b = a + cs.cap < hi ? a + cs.cap : hi;
         const int64_t n = b - a;

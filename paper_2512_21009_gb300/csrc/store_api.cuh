@@ -86,6 +86,9 @@ struct CountScratch {
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 3 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     bool orient = true;              // search closed pairs in (|g|, g) order (no temporal family, no restricted lists)
+    // work split of one hypergraph across ranks: count_launch counts only
+    // this rank's contiguous share (by neighbourhood size) of a side
+    int split_rank = 0, split_world = 1;
     int c_per_sm = 4;                // centre blocks per SM the overflow tables were sized for
     int64_t* h_total = nullptr;      // pinned host word for the list total
     // profiling: events around each centre-kernel launch of a call
@@ -125,7 +128,11 @@ cudaError_t upload_tables(cudaStream_t st);
 // those outside [lo, hi)).  Only changed[lo, hi) are enumerated by this call.
 // side selects the work queues.  The call reads one word back from the
 // device (the size of the neighbour lists) and splits [lo, hi) when the lists
-// would not fit.
+// would not fit.  With cs.split_world > 1 only this rank's share of [lo, hi)
+// is counted: the contiguous range whose neighbourhood sizes (plus one per
+// hyperedge) fall in the rank's equal part of their total, so that the
+// shares of all ranks, each counting on an identical replica, sum to the
+// whole (every triad is still counted at its changed member of smallest ID).
 cudaError_t count_launch(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                          const uint32_t* chg_bits, int64_t lo, int64_t hi, int side, uint64_t* dcounts_side,
                          const CountScratch& cs, int64_t max_u, cudaStream_t st, LaunchCounter& lc);

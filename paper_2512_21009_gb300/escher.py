@@ -40,7 +40,7 @@ EXPORTED = [
     "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members", "esc_group_update_members",
     "esc_version", "esc_count_static_noalloc", "esc_insert_with_ids", "esc_restore",
     "esc_group_insert_with_ids", "esc_group_export_sizes", "esc_group_export", "esc_export_h2h",
-    "esc_group_export_h2h",
+    "esc_group_export_h2h", "esc_set_split", "esc_group_set_split",
 ]
 
 
@@ -135,6 +135,8 @@ def load(path: str = LIB_PATH):
     L.esc_server_destroy.argtypes = [vp]
     L.esc_autotune.argtypes = [vp, i64, vp, i32, C.POINTER(esc_tune_result)]
     L.esc_set_graph_launch.argtypes = [vp, i32]
+    L.esc_set_split.argtypes = [vp, i32, i32]
+    L.esc_group_set_split.argtypes = [vp, i32, i32]
     L.esc_update_members.argtypes = [vp, i64, vp, vp, vp]
     L.esc_group_update_members.argtypes = [vp, i32, i64, vp, vp, vp]
     L.esc_group_set_graph_launch.argtypes = [vp, i32]
@@ -157,7 +159,8 @@ def load(path: str = LIB_PATH):
                  "esc_server_get_stats", "esc_server_destroy", "esc_autotune", "esc_group_autotune",
                  "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members",
                  "esc_group_update_members", "esc_insert_with_ids", "esc_restore", "esc_group_insert_with_ids",
-                 "esc_group_export_sizes", "esc_group_export", "esc_export_h2h", "esc_group_export_h2h"):
+                 "esc_group_export_sizes", "esc_group_export", "esc_export_h2h", "esc_group_export_h2h",
+                 "esc_set_split", "esc_group_set_split"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -482,6 +485,16 @@ def esc_group_set_graph_launch(grp: int, on: bool = True) -> None:
     _check(L.esc_group_set_graph_launch(grp, 1 if on else 0), L.esc_group_last_error, grp)
 
 
+def esc_set_split(h: int, rank: int, world: int) -> None:
+    L = load()
+    _check(L.esc_set_split(h, int(rank), int(world)), L.esc_last_error, h)
+
+
+def esc_group_set_split(grp: int, rank: int, world: int) -> None:
+    L = load()
+    _check(L.esc_group_set_split(grp, int(rank), int(world)), L.esc_group_last_error, grp)
+
+
 def esc_group_autotune(grp: int, graph: int, ids, reps: int = 2) -> dict:
     L = load()
     p, keep = _ptr(ids, np.int32)
@@ -691,6 +704,9 @@ class Graph:
 
     def set_graph_launch(self, on: bool = True) -> None:
         esc_set_graph_launch(self.h, on)
+
+    def set_split(self, rank: int, world: int) -> None:
+        esc_set_split(self.h, rank, world)
 
     def update_members(self, ids, offsets, members) -> None:
         esc_update_members(self.h, ids, offsets, members)

@@ -195,6 +195,45 @@ def test_restricted_lists(E, monkeypatch, families):
     _big_hyperedge_stream(E, families, 23)
 
 
+@pytest.mark.parametrize("orient", ["0", "1"])
+def test_both_centre_kernels_without_temporal(E, monkeypatch, orient):
+    """Without the temporal family closed pairs are searched once in (|g|, g)
+    order by default; ESC_COUNT_ORIENT=0 selects the earlier kernel, which
+    visits both sides of every closed pair.  Both must equal the oracle on a
+    stream with hub vertices and Zipf cardinalities."""
+    monkeypatch.setenv("ESC_COUNT_ORIENT", orient)
+    s = gen.random_small(27, 500, 700, 2, 40, n_batches=3, n_ins=60, n_del=60, membership="zipf", card="zipf")
+    run_stream(E, s, 3, 0)
+
+
+def test_unsorted_neighbourhood_without_table(E, monkeypatch):
+    """A changed hyperedge with more than 4096 distinct neighbours (too many
+    to sort) and, with ESC_COUNT_BIGNH raised, no hash table: the centre
+    kernel visits its whole N(h), testing the (|g|, g) order per entry."""
+    monkeypatch.setenv("ESC_COUNT_BIGNH", "8192")
+    rng = np.random.default_rng(29)
+    nv = 200
+    edges = [sorted(rng.choice(nv, size=2, replace=False).tolist()) for _ in range(4500)]
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    ts = np.arange(len(edges), dtype=np.int64)
+    og = OracleHypergraph(nv, off, mem, ts)
+    g = E.Graph(nv, off, mem, ts, families=3, **caps_for(nv, 10000, 40000, 2000, 20000))
+    assert_counts_equal(g.counts(), O.counts(og, 3), "initial")
+    big = sorted(rng.choice(nv, size=150, replace=False).tolist())
+    # the initial hyperedges hold IDs 0..n-1 on both sides: delete five of them
+    ids_o = og.apply_batch(np.array([0, 150]), np.array(big), np.array([9000]), np.arange(5))
+    ids_g = g.apply_batch(np.array([0, 150]), np.array(big, np.int32), np.array([9000]), np.arange(5, dtype=np.int32))
+    assert np.array_equal(ids_g, ids_o)
+    assert_counts_equal(g.counts(), O.counts(og, 3), "after insert")
+    ids_o2 = og.apply_batch(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64), ids_o)
+    ids_g2 = g.apply_batch(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64),
+                           np.asarray(ids_g, np.int32))
+    assert ids_o2.size == 0 and len(ids_g2) == 0
+    assert_counts_equal(g.counts(), O.counts(og, 3), "after delete")
+
+
 @pytest.mark.parametrize("families", [1, 2, 4, 3, 5, 6])
 def test_family_subsets(E, families):
     s = gen.random_small(9, 300, 200, 2, 7, n_batches=1, n_ins=30, n_del=30)
