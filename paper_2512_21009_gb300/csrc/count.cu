@@ -882,8 +882,39 @@ __global__ void k_set_loffg(CountArgs A) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nd; j += gridDim.x * blockDim.x)
         cs.loffg[cs.d_list[j]] = cs.d_loff[j];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        A.sc->items[A.side] = A.sc->gate ? 0 : cs.d_item_start[nd];
+        const int64_t items = cs.d_item_start[nd];
+        // the item map holds every item (a bound the arena sizes guarantee)
+        if (items > cs.items_cap) set_error(A.sc, kErrUnsupported, -13, items, cs.items_cap);
+        A.sc->items[A.side] = (A.sc->gate || items > cs.items_cap) ? 0 : items;
         A.sc->queue[A.side] = 0;
+    }
+}
+
+// Per distinct g1 (a warp each): |g1|, the sum of its members' degrees (the
+// entries of N(g1) with repeats) and its h2v offset, read once here instead
+// of at the start of every centre item; and the index j of every item of g1.
+__global__ void k_item_prep(CountArgs A) {
+    const CountScratch& cs = A.cs;
+    const Store& S = A.S;
+    if (A.sc->gate) return;
+    const int nd = A.sc->n_d[A.side];
+    const int lane = lane_id();
+    for (int64_t j = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < nd;
+         j += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+        const int32_t g1 = cs.d_list[j];
+        const int k1 = S.h_card[g1];
+        const int64_t off = S.h_off[g1];
+        long long u = 0;
+        for (int t = lane; t < k1; t += 32) u += S.v_deg[S.hp.arena[off + t]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (lane == 0) {
+            cs.d_k1[j] = k1;
+            cs.d_u1[j] = u;
+            cs.d_hoff[j] = off;
+        }
+        const int64_t i0 = cs.d_item_start[j], i1 = cs.d_item_start[j + 1];
+        for (int64_t it = i0 + lane; it < i1 && it < cs.items_cap; it += 32) cs.item_j[it] = int32_t(j);
     }
 }
 
@@ -1580,7 +1611,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
 template <int NT_C, int T1_S>
 struct SmemCO {
     static constexpr int NW_C = NT_C / 32;
-    static constexpr int BLOOM_W = T1_S >= 4096 ? 2048 : 4096;
+    static constexpr int BLOOM_W = 2048;
     Tables tb;
     uint32_t hist[NW_C][32];
     uint32_t hneg[NW_C][32];     // open classes taken back for closed triads
@@ -1611,6 +1642,9 @@ struct SmemCO {
     uint32_t xc[LCH][2];
     int32_t hI[LCH][kIC];
     int hIn[LCH];
+    // per warp, the closed pairs found and not yet classified: g2 | vf2 << 32,
+    // and |g1 & g2| | |h & g2| << 16 | |g2| << 32 | l << 48
+    unsigned long long cq0[NW_C][64], cq1[NW_C][64];
     uint32_t bloom[BLOOM_W];     // one-hash filter of N(g1)
 };
 
@@ -1679,7 +1713,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
         __syncthreads();
         const int64_t item = s.item;
         if (item >= n_items) break;
-        const int64_t j = upper_bound_dev(cs.d_item_start, int64_t(nd) + 1, item) - 1;
+        const int64_t j = cs.item_j[item];
         const int64_t sup = item - cs.d_item_start[j];
         const int32_t g1 = cs.d_list[j];
         const int64_t l_lo = cs.d_loff[j], l_hi = cs.d_loff[j + 1];
@@ -1699,12 +1733,10 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
             }
             cur_g = g;
         }
-        const int k1 = S.h_card[g1];
-        const int32_t* g1mem = h2v + S.h_off[g1];
+        const int k1 = cs.d_k1[j];
+        const int32_t* g1mem = h2v + cs.d_hoff[j];
         const unsigned long long key1 = order_key(k1, g1);
-        long long u1 = 0;
-        for (int t = tid; t < k1; t += NT_C) u1 += S.v_deg[g1mem[t]];
-        u1 = block_sum<NT_C>(u1, s.red);
+        const long long u1 = cs.d_u1[j];
         acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
         if (tid == 0) {
             // open paths: N(g1) (sum of member degrees) per pair (h, g1)
@@ -1743,23 +1775,31 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
             //      a member of degree >= kBigDeg is left to the whole block
             constexpr int kBigDeg = 256;
             if (tid == 0) s.any_big = 0;
-            __syncthreads();
-            for (int m = wid; m < k1; m += NW_C) {
-                const int32_t v = g1mem[m];
-                const int d = S.v_deg[v];
-                if (d >= kBigDeg) {
-                    if (lane == 0) s.any_big = 1;
-                    continue;
+            for (int m0 = 0; m0 < k1; m0 += NT_C) {
+                // the segment's members' degrees and v2h offsets, loaded at once
+                const int n = min(NT_C, k1 - m0);
+                if (tid < n) {
+                    const int32_t v = g1mem[m0 + tid];
+                    s.seg_pre[tid] = S.v_deg[v];
+                    s.seg_off[tid] = S.v_off[v];
                 }
-                const int32_t* lst = v2h + S.v_off[v];
-                for (int e = lane; e < d; e += 32) {
-                    const int32_t f = lst[e];
-                    if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
-                    tab_insert(T1, f, 1u, 0, A.sc);
+                __syncthreads();
+                for (int m = wid; m < n; m += NW_C) {
+                    const int d = s.seg_pre[m];
+                    if (d >= kBigDeg) {
+                        if (lane == 0) s.any_big = 1;
+                        continue;
+                    }
+                    const int32_t* lst = v2h + s.seg_off[m];
+                    for (int e = lane; e < d; e += 32) {
+                        const int32_t f = lst[e];
+                        if (f == g1 || (P > 1 && part_of(f, P) != p)) continue;
+                        tab_insert(T1, f, 1u, 0, A.sc);
+                    }
+                    acc.n_v2h += (lane < d) ? (d - lane + 31) / 32 : 0;
                 }
-                acc.n_v2h += (lane < d) ? (d - lane + 31) / 32 : 0;
+                __syncthreads();
             }
-            __syncthreads();
             if (s.any_big) {
                 for (int m = 0; m < k1; ++m) {
                     const int32_t v = g1mem[m];
@@ -1919,7 +1959,48 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                 const int my_pre = lane < nc ? s.hpre[lane] : INT_MAX;
                 const int my_l = lane < nc ? s.hord[lane] : 0;
 
-                // ---- the pair pass: a warp takes 32 consecutive work indices
+                // ---- the pair pass: a warp takes 32 consecutive work indices.
+                // Closed pairs found go to the warp's queue and are classified
+                // 32 at a time, so that every lane of the classifying code is
+                // busy (about one visit in ten finds one).
+                unsigned long long* const q0 = s.cq0[wid];
+                unsigned long long* const q1 = s.cq1[wid];
+                auto classify = [&](int e) {
+                    const unsigned long long a = q0[e], b = q1[e];
+                    const int32_t g2 = int32_t(uint32_t(a));
+                    const int32_t vf2 = int32_t(uint32_t(a >> 32));
+                    const int x12 = int(b & 0xffffu), xh2 = int((b >> 16) & 0xffffu);
+                    const int k2 = int((b >> 32) & 0x7fffu), l = int(b >> 48);
+                    const int kh = s.hk[l], xh1 = s.hx[l];
+                    ++acc.w[3];
+                    const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
+                                              kh, s.hI[l], s.hIn[l], acc.w[4]);
+                    acc.n_meta += 1;
+                    acc.n_closed += (unsigned long long)min(k1, k2);  // closed pairs: min(|g1|, |g2|) entries
+                    if (agg) {
+                        const int ra = kh - xh1 - xh2 + t, rb = k1 - xh1 - x12 + t, rc = k2 - x12 - xh2 + t;
+                        const int mk = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xh1 - t > 0) << 3) |
+                                       ((x12 - t > 0) << 4) | ((xh2 - t > 0) << 5) | ((t > 0) << 6);
+                        ++acc.n_tri;
+                        // every mask formed here is a valid triad (its pairwise
+                        // intersections are non-empty), so each class is >= 0
+                        const int cc = s.tb.cls30[mk];
+                        // the open classes the aggregates gave this triple
+                        const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
+                        const int m1 = (kh > xh1 ? 1 : 0) | (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 4 : 0) | 8 | 16;
+                        const int m2 = (kh > xh2 ? 1 : 0) | (x12 != k2 - xh2 ? 2 : 0) | (k1 > x12 ? 4 : 0) | 8 | 16;
+                        const int c1 = s.tb.cls30[m1], c2 = s.tb.cls30[m2];
+                        if (cc >= 0) atomicAdd(&hist[cc], 1u);
+                        if (ch >= 0) atomicAdd(&hneg[ch], 1u);
+                        if (c1 >= 0) atomicAdd(&hneg[c1], 1u);
+                        if (c2 >= 0) atomicAdd(&hneg[c2], 1u);
+                    }
+                    if (fam & kFamV)
+                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
+                                  2ull * t;
+                };
+                int qn = 0;  // the warp's queue length (the same in every lane)
+                const unsigned lt = (1u << lane) - 1u;
                 for (int w0 = wid * 32; w0 < wtot; w0 += NT_C) {
                     const int idx = w0 + lane;
                     // the h of each index: the last one starting at or before it
@@ -1930,6 +2011,8 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     const int c = c0 + __popc(B & ((2u << lane) - 1u));
                     const int l = __shfl_sync(0xffffffffu, my_l, c & 31);
                     const int q = idx - __shfl_sync(0xffffffffu, my_pre, c & 31);
+                    bool found = false;
+                    unsigned long long e0 = 0, e1 = 0;
                     do {
                     if (idx >= wtot) break;
                     const int mode = s.hmode[l];
@@ -1973,38 +2056,31 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         chg2 = ((xv2 >> 31) & 1u) != 0;
                         vf2 = int32_t(uint32_t(xv2 >> 32));
                     }
-                    // a closed triad {h, g1, g2}, g1 below g2
-                    const int32_t h = s.hh[l];
-                    if (g2 < h && chg2) break;  // it belongs to g2 (or a smaller changed member)
-                    const int kh = s.hk[l], xh1 = s.hx[l];
-                    ++acc.w[3];
-                    const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
-                                              kh, s.hI[l], s.hIn[l], acc.w[4]);
-                    acc.n_meta += 1;
-                    acc.n_closed += (unsigned long long)min(k1, k2);  // closed pairs: min(|g1|, |g2|) entries
-                    if (agg) {
-                        const int ra = kh - xh1 - xh2 + t, rb = k1 - xh1 - x12 + t, rc = k2 - x12 - xh2 + t;
-                        const int mk = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xh1 - t > 0) << 3) |
-                                       ((x12 - t > 0) << 4) | ((xh2 - t > 0) << 5) | ((t > 0) << 6);
-                        ++acc.n_tri;
-                        // every mask formed here is a valid triad (its pairwise
-                        // intersections are non-empty), so each class is >= 0
-                        const int cc = s.tb.cls30[mk];
-                        // the open classes the aggregates gave this triple
-                        const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
-                        const int m1 = (kh > xh1 ? 1 : 0) | (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 4 : 0) | 8 | 16;
-                        const int m2 = (kh > xh2 ? 1 : 0) | (x12 != k2 - xh2 ? 2 : 0) | (k1 > x12 ? 4 : 0) | 8 | 16;
-                        const int c1 = s.tb.cls30[m1], c2 = s.tb.cls30[m2];
-                        if (cc >= 0) atomicAdd(&hist[cc], 1u);
-                        if (ch >= 0) atomicAdd(&hneg[ch], 1u);
-                        if (c1 >= 0) atomicAdd(&hneg[c1], 1u);
-                        if (c2 >= 0) atomicAdd(&hneg[c2], 1u);
-                    }
-                    if (fam & kFamV)
-                        acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
-                                  2ull * t;
+                    // a closed triad {h, g1, g2}, g1 below g2, unless it
+                    // belongs to g2 (or a smaller changed member)
+                    if (g2 < s.hh[l] && chg2) break;
+                    found = true;
+                    e0 = uint64_t(uint32_t(g2)) | (uint64_t(uint32_t(vf2)) << 32);
+                    e1 = uint64_t(x12) | (uint64_t(xh2) << 16) | (uint64_t(k2) << 32) | (uint64_t(l) << 48);
                     } while (0);
+                    const unsigned fm = __ballot_sync(0xffffffffu, found);
+                    if (fm) {
+                        if (found) {
+                            const int at = qn + __popc(fm & lt);
+                            q0[at] = e0;
+                            q1[at] = e1;
+                        }
+                        qn += __popc(fm);
+                        if (qn >= 32) {
+                            __syncwarp();
+                            classify(qn - 32 + lane);
+                            qn -= 32;
+                            __syncwarp();
+                        }
+                    }
                 }
+                __syncwarp();
+                if (lane < qn) classify(lane);
                 __syncthreads();
                 if (agg) {
                     // open triads {h, g1, f} centred at g1, in aggregate: the
@@ -2012,21 +2088,26 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     // b = 2B + C of f, B = [|g1&f| != |g1| - |h&g1|],
                     // C = [f not inside g1]; from the totals over N(g1) are
                     // taken f = h and the changed f < h
-                    const int wc = nh * n_cl;
-                    if (tid == 0) acc.w[5] += (unsigned long long)wc;
-                    for (int idx0 = 0; idx0 < wc; idx0 += NT_C) {
-                        const int idx = idx0 + tid;
-                        int skey = -1;
-                        if (idx < wc) {
-                            const int l = idx / n_cl, c = idx - l * n_cl;
-                            const long long v = cl[c];
-                            const int32_t f = int32_t(v & 0x7fffffffll);
-                            if (f < s.hh[l]) {
-                                const int x = int((v >> 31) & 0x7fffll), kf = int(v >> 46);
-                                skey = l * 4 + ((x != k1 - s.hx[l] ? 2 : 0) | (kf > x ? 1 : 0));
+                    if (tid == 0) acc.w[5] += (unsigned long long)nh * n_cl;
+                    for (int l = wid; l < nh; l += NW_C) {  // a warp per h, its lanes over the changed f
+                        const int32_t h = s.hh[l];
+                        const int xs = k1 - s.hx[l];
+                        uint32_t nb[4] = {0, 0, 0, 0};
+                        for (int c0 = 0; c0 < n_cl; c0 += 32) {
+                            int b = -1;
+                            if (c0 + lane < n_cl) {
+                                const long long v = cl[c0 + lane];
+                                if (int32_t(v & 0x7fffffffll) < h) {
+                                    const int x = int((v >> 31) & 0x7fffll), kf = int(v >> 46);
+                                    b = (x != xs ? 2 : 0) | (kf > x ? 1 : 0);
+                                }
                             }
+#pragma unroll
+                            for (int bb = 0; bb < 4; ++bb) nb[bb] += __popc(__ballot_sync(0xffffffffu, b == bb));
                         }
-                        warp_count(&s.sub[0][0], skey);
+                        if (lane == 0)
+                            for (int bb = 0; bb < 4; ++bb)
+                                if (nb[bb]) atomicAdd(&s.sub[l][bb], nb[bb]);
                     }
                     if (tid < nh && (P == 1 || part_of(s.hh[tid], P) == p)) {
                         const int xh1 = s.hx[tid];
@@ -2213,6 +2294,8 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 2 * al(sizeof(int32_t) * sh.e_cap) + al(sizeof(int64_t) * sh.e_cap);
     b += 3 * al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * (sh.e_cap + 1));
     b += al(sizeof(int64_t) * nbs);
+    b += al(sizeof(int32_t) * sh.e_cap) + 2 * al(sizeof(int64_t) * sh.e_cap) +
+         al(sizeof(int32_t) * (sh.e_cap + sh.list_cap / (LCH * kSuper) + 1));
     b += al(sizeof(int32_t) * sh.r_cap) + al(sizeof(int64_t) * sh.cap);
     b += 2 * al(sizeof(int32_t) * sh.cap) + al(sizeof(int64_t) * (sh.cap + 1));
     const int64_t rn = sh.n_cta_nh, rc = int64_t(sh.c_per_sm) * sh.n_cta_c;
@@ -2263,6 +2346,11 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->d_item_start = static_cast<int64_t*>(take(sizeof(int64_t) * (sh.e_cap + 1)));
     cs->block_sums = static_cast<int64_t*>(take(sizeof(int64_t) * nbs));
     cs->n_block_sums = nbs;
+    cs->d_k1 = static_cast<int32_t*>(take(sizeof(int32_t) * sh.e_cap));
+    cs->d_u1 = static_cast<int64_t*>(take(sizeof(int64_t) * sh.e_cap));
+    cs->d_hoff = static_cast<int64_t*>(take(sizeof(int64_t) * sh.e_cap));
+    cs->items_cap = sh.e_cap + sh.list_cap / (LCH * kSuper) + 1;
+    cs->item_j = static_cast<int32_t*>(take(sizeof(int32_t) * cs->items_cap));
     cs->r_cap = sh.r_cap;
     cs->r_pool = static_cast<int32_t*>(take(sizeof(int32_t) * sh.r_cap));
     cs->r_off = static_cast<int64_t*>(take(sizeof(int64_t) * sh.cap));
@@ -2369,6 +2457,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_top<<<1, 32, 0, st>>>(cs.block_sums, 0, &sc->n_d[side]);
     k_scan_apply<int32_t><<<gd, kScanNT, 0, st>>>(cs.d_items, 0, &sc->n_d[side], cs.block_sums, cs.d_item_start);
     k_set_loffg<<<ge, 256, 0, st>>>(A);
+    if (orient) k_item_prep<<<capped(blocks_for(int64_t(cs.e_cap) * 32, 256)), 256, 0, st>>>(A);
     k_scatter<<<capped(blocks_for(nmax * 32, 256)), 256, 0, st>>>(A);
     const bool timed = cs.cev && cs.n_cev && *cs.n_cev < cs.max_cev;
     if (timed) cudaEventRecord(cs.cev[2 * *cs.n_cev], st);
@@ -2391,7 +2480,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     }
     if (timed) cudaEventRecord(cs.cev[2 * (*cs.n_cev)++ + 1], st);
     k_d_clean<<<ge, 256, 0, st>>>(A);
-    lc.total += 22;
+    lc.total += orient ? 23 : 22;
     lc.count += 2;
     return cudaGetLastError();
 }

@@ -55,6 +55,13 @@ struct CountScratch {
     int32_t* d_items = nullptr;      // [e_cap] work items of d_list[j]
     int64_t* d_loff = nullptr;       // [e_cap+1]
     int64_t* d_item_start = nullptr; // [e_cap+1]
+    // per distinct g1 (oriented counter): its size, sum of member degrees and
+    // h2v offset; and for each centre item its g1's index j
+    int32_t* d_k1 = nullptr;         // [e_cap]
+    int64_t* d_u1 = nullptr;         // [e_cap]
+    int64_t* d_hoff = nullptr;       // [e_cap]
+    int32_t* item_j = nullptr;       // [items_cap]
+    int64_t items_cap = 0;
     int64_t* block_sums = nullptr;   // scan scratch
     int64_t n_block_sums = 0;
     // per-block overflow hash tables
