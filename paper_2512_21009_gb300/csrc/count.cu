@@ -1608,6 +1608,28 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
 // whether or not they lie in N(h): their triads belong to f.  So no mark of
 // N(h) inside N(g1) is kept, and every closed triad is classified once.
 
+constexpr int kG1M = 1024;  // members of g1 kept in shared memory, at most
+
+// t = |h & g1 & g2| for the oriented kernel (as triple_size).  When one of
+// |h & g1|, |h & g2| is 1, its vertex v lies in h, so v is in the other
+// intersection only if it is not below that one's smallest vertex: the order
+// of the two smallest shared vertices settles most cases without a search.
+// g1m holds g1's members (shared memory when they fit).
+__device__ __forceinline__ int triple_size_o(int xh1, int32_t vf1, int xh2, int32_t vf2, const int32_t* g1m, int k1,
+                                             const int32_t* g2mem, int k2, const int32_t* hmem, int kh,
+                                             const int32_t* hI, int nI, unsigned long long& slow) {
+    if (xh1 == 1 && xh2 == 1) return vf1 == vf2;
+    if (xh1 == 1) {  // t = [vf1 in g2]
+        if (vf1 <= vf2) return vf1 == vf2;
+        return contains_sorted(g2mem, k2, vf1);
+    }
+    if (xh2 == 1) {  // t = [vf2 in g1]
+        if (vf2 <= vf1) return vf2 == vf1;
+        return contains_sorted(g1m, k1, vf2);
+    }
+    return triple_size(xh1, vf1, xh2, vf2, g1m, k1, g2mem, k2, hmem, kh, hI, nI, slow);
+}
+
 template <int NT_C, int T1_S>
 struct SmemCO {
     static constexpr int NW_C = NT_C / 32;
@@ -1646,6 +1668,7 @@ struct SmemCO {
     // and |g1 & g2| | |h & g2| << 16 | |g2| << 32 | l << 48
     unsigned long long cq0[NW_C][64], cq1[NW_C][64];
     uint32_t bloom[BLOOM_W];     // one-hash filter of N(g1)
+    int32_t g1m[kG1M];           // g1's members, when |g1| <= kG1M
 };
 
 static_assert(sizeof(SmemCO<256, 2048>) + 1024 <= 233472 / 3, "three 256-thread oriented centre blocks per SM");
@@ -1735,6 +1758,11 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
         }
         const int k1 = cs.d_k1[j];
         const int32_t* g1mem = h2v + cs.d_hoff[j];
+        // g1's members in shared memory for the triple sizes (read after the
+        // build's barriers)
+        if (k1 <= kG1M)
+            for (int t = tid; t < k1; t += NT_C) s.g1m[t] = g1mem[t];
+        const int32_t* g1s = k1 <= kG1M ? s.g1m : g1mem;
         const unsigned long long key1 = order_key(k1, g1);
         const long long u1 = cs.d_u1[j];
         acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
@@ -1973,8 +2001,8 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     const int k2 = int((b >> 32) & 0x7fffu), l = int(b >> 48);
                     const int kh = s.hk[l], xh1 = s.hx[l];
                     ++acc.w[3];
-                    const int t = triple_size(xh1, s.hvf[l], xh2, vf2, g1mem, k1, h2v + S.h_off[g2], k2, s.hmem[l],
-                                              kh, s.hI[l], s.hIn[l], acc.w[4]);
+                    const int t = triple_size_o(xh1, s.hvf[l], xh2, vf2, g1s, k1, h2v + S.h_off[g2], k2, s.hmem[l],
+                                                kh, s.hI[l], s.hIn[l], acc.w[4]);
                     acc.n_meta += 1;
                     acc.n_closed += (unsigned long long)min(k1, k2);  // closed pairs: min(|g1|, |g2|) entries
                     if (agg) {
