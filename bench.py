@@ -1122,62 +1122,112 @@ def _drive(E, srv, models, nvs, pool, rng, rate, duration, max_pending, t_clock,
 
 
 def run_serving(args):
-    """Resident hypergraphs (sizes as the batched workload, times --scale),
-    admitted while their device memory fits; Poisson request arrivals.
-    Two server policies over the same group: continuous batching and one
-    request per call.  For each: an overload run at --rate requests/s, then
-    runs at 0.25, 0.5 and 1.0 of the capacity it sustained.  Afterwards a
-    few graphs are rebuilt alone from their logged requests and their counts
-    compared with the served ones."""
+    """Resident hypergraphs (sizes as the batched workload, times --scale) in
+    --shards groups, each group on its own stream with its own server worker
+    (so calls of different groups overlap on the device).  Groups are
+    admitted one at a time while the server runs under load: a group is
+    created only if it fits the device's free memory less a reserve
+    (esc_group_fits); later groups that do not fit are refused on the host.
+    Poisson request arrivals over the admitted graphs.  Two server policies:
+    continuous batching and one request per call.  Each is driven at offered
+    loads of 0.25, 0.5 and 1.0 of the capacity of one request per call (the
+    same offered mix for both policies), then at 1.0 of its own capacity and
+    under overload.  Afterwards a few graphs are rebuilt alone from their
+    logged requests and their counts compared with the served ones."""
     import torch
     from paper_2512_21009_gb300 import escher as E
     torch.cuda.set_device(0)
     n_graphs = args.graphs or 1024
     ms = gen.resident_graphs(seed=5, n_graphs=n_graphs, e_hi=1e6 * args.scale)
-    streams, delta, fam = ms.graphs, ms.delta, 1 | 4
-    max_bh, max_bi = 1 << 20, 1 << 24
-    shared, cfgs = _group_cfgs_resident(E, streams, delta, fam, max_bh, max_bi)
-    free = torch.cuda.mem_get_info()[0]
-    budget = min(free - (16 << 30), 120 << 30)
-    lo, hi = 1, len(cfgs)
-    while lo < hi:  # admission: most graphs whose group fits the budget
-        mid = (lo + hi + 1) // 2
-        if E.esc_group_bytes(shared, cfgs[:mid]) <= budget:
-            lo = mid
-        else:
-            hi = mid - 1
-    G = lo
-    streams, cfgs = streams[:G], cfgs[:G]
-    t0 = time.time()
-    grp = E.esc_group_create(shared, cfgs)
-    _load_group(E, grp, streams, max_bh, max_bi)
-    torch.cuda.synchronize()
-    t_load = time.time() - t0
-    if not args.no_graph_launch:
-        E.esc_group_set_graph_launch(grp, True)  # each call replays one captured CUDA graph
-    models = [_IdModel(st.initial.n) for st in streams]
-    nvs = [st.n_vertices for st in streams]
-    t_clock = time.monotonic_ns() // 1000 - 3600 * 10 ** 6   # timestamps after every initial one
+    all_streams, delta, fam = ms.graphs, ms.delta, 1 | 4
+    # per-call limits of each group (they size its count arena: 512 neighbour
+    # entries per batch hyperedge): 2^18 updates and 2^22 members per call
+    max_bh, max_bi = 1 << 18, 1 << 22
+    shared, all_cfgs = _group_cfgs_resident(E, all_streams, delta, fam, max_bh, max_bi)
+    # shards: graphs dealt round-robin by size, so the groups are alike;
+    # server graph numbers follow the shards in admission order
+    n_sh = max(1, min(args.shards, n_graphs))
+    by_size = np.argsort([st.initial.n for st in all_streams])[::-1]
+    shard_graphs = [list(by_size[k::n_sh]) for k in range(n_sh)]
+    reserve = 16 << 30
+    cap_bytes = 120 << 30
+    cuda_streams = [torch.cuda.Stream() for _ in range(n_sh)]
+    streams, cfgs, groups, refused = [], [], [], 0
+    models, nvs = [], []
     pool = gen.insert_pool(6, 1 << 21)
     rng = np.random.default_rng(args.seed + 100)
-    order = np.argsort([st.initial.n for st in streams])
-    sample = [int(order[0]), int(order[len(order) // 3]), int(order[2 * len(order) // 3])]
-    log = {g: [] for g in sample}
+    t_clock = time.monotonic_ns() // 1000 - 3600 * 10 ** 6   # timestamps after every initial one
     max_pending = args.queue
+    srv = None
+    t0 = time.time()
+    used = 0
+    admitted_under_load = 0
+    for k in range(n_sh):
+        sc = [all_cfgs[g] for g in shard_graphs[k]]
+        need = E.esc_group_bytes(shared, sc)
+        if used + need > cap_bytes or not E.esc_group_fits(shared, sc, reserve):
+            refused += len(sc)
+            continue
+        grp = E.esc_group_create(shared, sc, stream=cuda_streams[k])
+        ss = [all_streams[g] for g in shard_graphs[k]]
+        _load_group(E, grp, ss, max_bh, max_bi)
+        if not args.no_graph_launch:
+            E.esc_group_set_graph_launch(grp, True)  # each call replays one captured CUDA graph
+        used += need
+        groups.append(grp)
+        streams += ss
+        cfgs += sc
+        models += [_IdModel(st.initial.n) for st in ss]
+        nvs += [st.n_vertices for st in ss]
+        if srv is None:
+            srv = E.esc_server_create(grp, max_pending, 0)
+            # graphs of the first group rebuilt alone at the end: every
+            # request they receive is logged from now on
+            order = np.argsort([st.initial.n for st in streams])
+            sample = [int(order[0]), int(order[len(order) // 3]), int(order[2 * len(order) // 3])]
+            log = {g: [] for g in sample}
+        else:
+            E.esc_server_add_group(srv, grp)
+            admitted_under_load += 1
+        # load on the admitted graphs while the next group is prepared
+        _drive(E, srv, models, nvs, pool, rng, args.rate / 10, 1.0, max_pending, t_clock, log)
+    torch.cuda.synchronize()
+    t_load = time.time() - t0
+    G = len(streams)
+    E.esc_server_destroy(srv)
+    mean_size = float(np.mean(np.floor(10 ** np.random.default_rng(0).uniform(1, 4, 100000))))
     runs = {}
+
+    def server(per_call):
+        sv = E.esc_server_create(groups[0], max_pending, per_call)
+        for grp in groups[1:]:
+            E.esc_server_add_group(sv, grp)
+        return sv
+
+    # capacity of each policy: the updates/s it sustains under overload
+    caps = {}
     for policy, per_call in (("continuous", 0), ("one_per_call", 1)):
-        srv = E.esc_server_create(grp, max_pending, per_call)
+        sv = server(per_call)
         try:
-            over = _drive(E, srv, models, nvs, pool, rng, args.rate, args.duration, max_pending, t_clock, log)
-            cap = max(over["updates_per_s"], 1.0)
-            mean_size = float(np.mean(np.floor(10 ** np.random.default_rng(0).uniform(1, 4, 100000))))
-            curve = []
-            for f in (0.25, 0.5, 1.0):
-                curve.append(dict(fraction=f, **_drive(E, srv, models, nvs, pool, rng, f * cap / mean_size,
-                                                        args.duration, max_pending, t_clock, log)))
-            runs[policy] = {"overload": over, "curve": curve, "stats": E.esc_server_get_stats(srv)}
+            over = _drive(E, sv, models, nvs, pool, rng, args.rate, args.duration, max_pending, t_clock, log)
+            caps[policy] = max(over["updates_per_s"], 1.0)
+            runs[policy] = {"overload": over}
         finally:
-            E.esc_server_destroy(srv)
+            E.esc_server_destroy(sv)
+    base = caps["one_per_call"]
+    for policy, per_call in (("continuous", 0), ("one_per_call", 1)):
+        sv = server(per_call)
+        try:
+            equal = [dict(fraction=f, offered_updates_per_s=f * base,
+                          **_drive(E, sv, models, nvs, pool, rng, f * base / mean_size, args.duration, max_pending,
+                                   t_clock, log)) for f in (0.25, 0.5, 1.0)]
+            own = dict(fraction=1.0, offered_updates_per_s=caps[policy],
+                       **_drive(E, sv, models, nvs, pool, rng, caps[policy] / mean_size, args.duration, max_pending,
+                                t_clock, log))
+            runs[policy].update({"equal_offered_load": equal, "own_capacity": own,
+                                 "stats": E.esc_server_get_stats(sv)})
+        finally:
+            E.esc_server_destroy(sv)
     # each sampled graph alone, from its initial hyperedges and logged requests
     same = True
     for g in sample:
@@ -1188,11 +1238,17 @@ def run_serving(args):
                         max_batch_incidences=max_bi, families=fam, delta=delta)
         for off, mem, ts, dels in log[g]:
             alone.apply_batch(off, mem, ts, dels, return_ids=False)
+        sv = server(0)
         for tt in (E.TRIAD_HYPEREDGE, E.TRIAD_TEMPORAL):
-            same &= bool(np.array_equal(alone.triads(tt), E.esc_group_triads(grp, g, tt, delta)))
+            same &= bool(np.array_equal(alone.triads(tt), E.esc_server_triads(sv, g, tt, delta)))
+        E.esc_server_destroy(sv)
         alone.close()
-    E.esc_group_destroy(grp)
-    cont = runs["continuous"]["overload"]
+    for grp in groups:
+        E.esc_group_destroy(grp)
+    cont = runs["continuous"]["own_capacity"]
+    one = runs["one_per_call"]["own_capacity"]
+    eq = [(a["updates_per_s"], b["updates_per_s"], a["p50_ms"], b["p50_ms"], a["p99_ms"], b["p99_ms"])
+          for a, b in zip(runs["continuous"]["equal_offered_load"], runs["one_per_call"]["equal_offered_load"])]
     print(json.dumps({
         "metric": METRIC, "value": cont["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1201,14 +1257,23 @@ def run_serving(args):
                                 f"log-uniform [1e3, {1e6 * args.scale:.0e}], vertices = hyperedges/2, cardinality "
                                 "Zipf(2.0) in [2,256]); Poisson arrivals, uniform graph, sizes log-uniform "
                                 "[10, 1e4], 1:1 insert/delete; hyperedge + temporal families"),
-                   "offered_per_s": args.rate, "seconds_per_run": args.duration, "queue_updates": max_pending,
-                   "load_s": round(t_load, 1), "hyperedges": int(sum(st.initial.n for st in streams)),
+                   "groups": len(groups), "groups_admitted_under_load": admitted_under_load,
+                   "graphs_refused": refused, "offered_per_s": args.rate, "seconds_per_run": args.duration,
+                   "queue_updates": max_pending, "load_s": round(t_load, 1),
+                   "hyperedges": int(sum(st.initial.n for st in streams)), "group_bytes": int(used),
                    "graph_launch": not args.no_graph_launch},
+        "headline": ("each policy at an offered load equal to its own capacity: continuous batching "
+                     f"{cont['updates_per_s']:.0f} vs one request per call {one['updates_per_s']:.0f} updates/s"),
         "p50_ms": cont["p50_ms"], "p99_ms": cont["p99_ms"],
+        "continuous_over_one_per_call_at_own_capacity": cont["updates_per_s"] / max(one["updates_per_s"], 1e-9),
+        "equal_offered_load": [dict(fraction=f, continuous_updates_per_s=a, one_per_call_updates_per_s=b,
+                                    continuous_p50_ms=c, one_per_call_p50_ms=d, continuous_p99_ms=e,
+                                    one_per_call_p99_ms=h)
+                               for f, (a, b, c, d, e, h) in zip((0.25, 0.5, 1.0), eq)],
         "runs": runs,
-        "continuous_over_one_per_call": cont["updates_per_s"] / max(runs["one_per_call"]["overload"]["updates_per_s"], 1e-9),
         "alone_equals_served": same,
-        "ids_ok": all(r["ids_ok"] for p in runs.values() for r in [p["overload"]] + p["curve"]),
+        "ids_ok": all(r["ids_ok"] for p in runs.values()
+                      for r in [p["overload"], p["own_capacity"]] + p["equal_offered_load"]),
     }))
 
 
@@ -1239,6 +1304,7 @@ def main():
     ap.add_argument("--rate", type=float, default=5e4, help="serving: offered requests/s")
     ap.add_argument("--duration", type=float, default=8.0, help="serving: seconds per run")
     ap.add_argument("--queue", type=int, default=1 << 20, help="serving: queued updates admitted")
+    ap.add_argument("--shards", type=int, default=4, help="serving: groups of graphs, each with its own stream")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--batch", type=int, default=100_000)
     ap.add_argument("--seed", type=int, default=2)

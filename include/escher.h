@@ -384,12 +384,18 @@ int64_t esc_group_launch_count(const esc_group* grp);
  * Serving loop over a group's resident graphs.  The paper applies one batch
  * at a time (Alg. 3); the server adds the request layer around that step:
  * update requests (one batch for one graph) are queued as they arrive, and
- * one worker thread applies them by continuous batching -- each call takes
- * the oldest pending request of as many distinct graphs as fit the group's
- * max_batch_hyperedges / max_batch_incidences (and max_batches_per_call
- * when > 0), so that requests arriving during a call join the next one.
- * Requests of one graph are applied in submission order, so a graph's IDs
- * and counts are those of its batches applied one by one with esc_group_apply.
+ * a worker thread per group applies them by continuous batching -- each call
+ * takes the oldest pending request of as many distinct graphs of the group
+ * as fit its max_batch_hyperedges / max_batch_incidences (and
+ * max_batches_per_call when > 0), so that requests arriving during a call
+ * join the next one.  Requests of one graph are applied in submission order,
+ * so a graph's IDs and counts are those of its batches applied one by one
+ * with esc_group_apply.  A server starts with one group and takes more while
+ * it runs (esc_server_add_group); the workers of different groups make their
+ * calls at the same time, each on its own group's stream, so that one
+ * group's ingest, store update and counting overlap another's on the device.
+ * Graphs are numbered server-wide: the graphs of the first group, then those
+ * of each group added, in the order added.
  * ------------------------------------------------------------------------ */
 typedef struct esc_server esc_server;
 
@@ -417,6 +423,21 @@ typedef struct {
 esc_status esc_server_create(esc_group* grp, int64_t max_pending_updates, int32_t max_batches_per_call,
                              esc_server** out);
 
+/* Add a group of resident graphs (created and loaded by the caller) to a
+ * running server; its graphs become the server's graphs *first_graph ..
+ * *first_graph + n_graphs - 1 (first_graph may be NULL).  From then on the
+ * group must only be used through the server.  For calls that overlap on
+ * the device, create each group on its own stream.  Errors: INVALID_ARG
+ * (the group is already served, or the server is stopping). */
+esc_status esc_server_add_group(esc_server* srv, esc_group* grp, int32_t* first_graph);
+
+/* Admission by free device memory: *fits = 1 when a group of the given
+ * configuration (esc_group_bytes) fits in the current device's free memory
+ * (cudaMemGetInfo) less reserve_bytes, else 0.  Nothing is allocated.
+ * Errors: INVALID_ARG, CUDA. */
+esc_status esc_group_fits(const esc_config* shared_cfg, int32_t n_graphs, const esc_config* graph_cfg,
+                          int64_t reserve_bytes, int32_t* fits);
+
 /* Queue one request.  All pointers are host memory and are copied before
  * the call returns, except out_ins_ids (host int32[n_ins] or NULL), which
  * receives the inserted IDs before the request is reported done and must
@@ -436,14 +457,15 @@ esc_status esc_server_wait(esc_server* srv, int64_t ticket, esc_request_info* in
 /* Block until every submitted request is done. */
 esc_status esc_server_drain(esc_server* srv);
 
-/* esc_group_triads through the server (serialised with the worker's calls). */
+/* esc_group_triads of a server graph, through the server (serialised with
+ * the calls of that graph's worker). */
 esc_status esc_server_triads(esc_server* srv, int32_t graph, esc_triad_type type, int64_t window,
                              uint64_t* out, int32_t n_out);
 
 esc_status esc_server_get_stats(esc_server* srv, esc_server_stats* out);
 
-/* Finish every queued request, stop the worker and free the server (not the
- * group). */
+/* Finish every queued request, stop the workers and free the server (not
+ * the groups). */
 esc_status esc_server_destroy(esc_server* srv);
 
 /* Allocation-free counting.  The paper has no counterpart of this call; it

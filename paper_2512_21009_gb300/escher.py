@@ -40,7 +40,7 @@ EXPORTED = [
     "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members", "esc_group_update_members",
     "esc_version", "esc_count_static_noalloc", "esc_insert_with_ids", "esc_restore",
     "esc_group_insert_with_ids", "esc_group_export_sizes", "esc_group_export", "esc_export_h2h",
-    "esc_group_export_h2h", "esc_set_split", "esc_group_set_split",
+    "esc_group_export_h2h", "esc_set_split", "esc_group_set_split", "esc_server_add_group", "esc_group_fits",
 ]
 
 
@@ -136,6 +136,8 @@ def load(path: str = LIB_PATH):
     L.esc_autotune.argtypes = [vp, i64, vp, i32, C.POINTER(esc_tune_result)]
     L.esc_set_graph_launch.argtypes = [vp, i32]
     L.esc_set_split.argtypes = [vp, i32, i32]
+    L.esc_server_add_group.argtypes = [vp, vp, C.POINTER(i32)]
+    L.esc_group_fits.argtypes = [C.POINTER(esc_config), i32, C.POINTER(esc_config), i64, C.POINTER(i32)]
     L.esc_group_set_split.argtypes = [vp, i32, i32]
     L.esc_update_members.argtypes = [vp, i64, vp, vp, vp]
     L.esc_group_update_members.argtypes = [vp, i32, i64, vp, vp, vp]
@@ -160,7 +162,7 @@ def load(path: str = LIB_PATH):
                  "esc_set_graph_launch", "esc_group_set_graph_launch", "esc_update_members",
                  "esc_group_update_members", "esc_insert_with_ids", "esc_restore", "esc_group_insert_with_ids",
                  "esc_group_export_sizes", "esc_group_export", "esc_export_h2h", "esc_group_export_h2h",
-                 "esc_set_split", "esc_group_set_split"):
+                 "esc_set_split", "esc_group_set_split", "esc_server_add_group", "esc_group_fits"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -570,6 +572,28 @@ def esc_server_get_stats(srv: int) -> dict:
     s = esc_server_stats()
     L.esc_server_get_stats(srv, C.byref(s))
     return {k: getattr(s, k) for k, _ in esc_server_stats._fields_}
+
+
+def esc_server_add_group(srv: int, grp: int) -> int:
+    """Serve another group; returns the server-wide index of its graph 0."""
+    L = load()
+    first = C.c_int32(-1)
+    rc = L.esc_server_add_group(srv, grp, C.byref(first))
+    if rc != 0:
+        raise EscError(rc, "esc_server_add_group failed")
+    return int(first.value)
+
+
+def esc_group_fits(shared: esc_config, graph_cfgs: Sequence[esc_config], reserve_bytes: int) -> bool:
+    """Whether a group of this configuration fits the current device's free
+    memory less reserve_bytes (nothing is allocated)."""
+    L = load()
+    arr = (esc_config * len(graph_cfgs))(*graph_cfgs)
+    fits = C.c_int32(0)
+    rc = L.esc_group_fits(C.byref(shared), len(graph_cfgs), arr, int(reserve_bytes), C.byref(fits))
+    if rc != 0:
+        raise EscError(rc, "esc_group_fits failed")
+    return bool(fits.value)
 
 
 def esc_server_destroy(srv: int) -> None:

@@ -170,3 +170,78 @@ def test_group_bytes_covers_the_allocation(E):
         assert used - slack <= est <= used + slack, (est, used)
     finally:
         E.esc_group_destroy(grp)
+
+
+def test_groups_added_while_serving_overlap_and_match_alone(E):
+    """A server starts with one group and takes two more while it runs; the
+    groups live on their own streams, so their workers' calls overlap on the
+    device.  Requests for all of them are interleaved from this thread.  Each
+    graph's IDs and counts must equal those of the oracle applying that
+    graph's requests alone, and the call records must show calls of
+    different groups overlapping in time."""
+    import torch
+    streams3 = [_streams()[2 * k:2 * k + 2] for k in range(3)]
+    cuda_streams = [torch.cuda.Stream() for _ in range(3)]
+    shared = E.make_config(1, 1, 1, 4000, 40000, ALL, DELTA)
+    groups, ogs, firsts = [], [], []
+
+    def make(k):
+        sts = streams3[k]
+        cfgs = [E.make_config(s.n_vertices, 1200, 12000, 0, 0, ALL, DELTA) for s in sts]
+        assert E.esc_group_fits(shared, cfgs, 0)
+        grp = E.esc_group_create(shared, cfgs, stream=cuda_streams[k])
+        E.esc_group_apply(grp, [dict(graph=i, ins_offsets=s.initial.offsets, ins_members=s.initial.members,
+                                     ins_timestamps=s.initial.timestamps, del_ids=None) for i, s in enumerate(sts)])
+        groups.append(grp)
+        ogs.extend(OracleHypergraph(s.n_vertices, s.initial.offsets, s.initial.members, s.initial.timestamps)
+                   for s in sts)
+        return grp
+
+    srv = E.esc_server_create(make(0), max_pending_updates=1 << 22, max_batches_per_call=0)
+    firsts.append(0)
+    try:
+        rng = np.random.default_rng(17)
+        sub, t0 = [], 90_000
+        for phase in range(3):
+            if phase > 0:
+                firsts.append(E.esc_server_add_group(srv, make(phase)))
+                assert firsts[-1] == 2 * phase
+            # the phase's requests are prepared (and applied to the oracle)
+            # first, then submitted in one burst
+            reqs = []
+            for r in range(60):
+                g = int(rng.integers(0, 2 * (phase + 1)))
+                off, mem, ts, dels = _request(rng, ogs[g], int(rng.integers(10, 30)), int(rng.integers(10, 30)), t0)
+                t0 += 100
+                reqs.append((g, off, mem, ts, dels, ogs[g].apply_batch(off, mem, ts, dels)))
+            for g, off, mem, ts, dels, want_ids in reqs:
+                out = np.full(max(len(off) - 1, 1), -1, np.int32)
+                t = E.esc_server_submit(srv, g, off, mem, ts, dels.astype(np.int32), out)
+                assert t >= 0
+                sub.append((g, t, out, want_ids))
+        E.esc_server_drain(srv)
+        spans = []
+        for g, t, out, want_ids in sub:
+            info = E.esc_server_wait(srv, t)
+            assert info["status"] == 0
+            assert np.array_equal(out[:len(want_ids)], want_ids), g
+            spans.append((g // 2, info["t_start_ns"], info["t_done_ns"]))
+        for i, og in enumerate(ogs):
+            want = O.counts(og, ALL, DELTA)
+            assert np.array_equal(E.esc_server_triads(srv, i, 0), want["hyperedge"]), i
+            assert np.array_equal(E.esc_server_triads(srv, i, 1), want["vertex"]), i
+            assert np.array_equal(E.esc_server_triads(srv, i, 2, DELTA), want["temporal"]), i
+        # some call of one group ran while a call of another group ran
+        overlap = any(a[0] != b[0] and a[1] < b[2] and b[1] < a[2] for a in spans for b in spans)
+        assert overlap
+    finally:
+        E.esc_server_destroy(srv)
+        for grp in groups:
+            E.esc_group_destroy(grp)
+    with pytest.raises(E.EscError):
+        s2 = E.esc_server_create(make(0), max_pending_updates=16)
+        try:
+            E.esc_server_add_group(s2, groups[-1])   # already served by s2
+        finally:
+            E.esc_server_destroy(s2)
+            E.esc_group_destroy(groups[-1])
