@@ -404,6 +404,137 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# the large workload as specified: Zipf(1.1) vertex popularity
+# ---------------------------------------------------------------------------
+
+def run_large_zipf(args):
+    """1M vertices, 2M hyperedges, cardinality Zipf(2.0) in [2,1000], vertex
+    popularity Zipf(1.1) (a vertex in ~44% of the hyperedges), batches of 5e4
+    inserts + 5e4 deletes: the store update and incident-vertex types 1 and 2
+    from vertex-pair statistics (ESC_FAMILY_VERTEX12).  The hyperedge family
+    and type 3 would need every neighbourhood of a hub-holding hyperedge
+    (~1e6 entries each) and are not kept here."""
+    import torch
+    from paper_2512_21009_gb300 import escher as E
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    nb = args.warmup + 2 * args.steps
+    s = gen.large(seed=args.seed, membership="zipf", scale=args.scale, n_batches=nb, batch_updates=args.batch)
+    init = s.initial
+    fam = 8
+    sizes_init = np.diff(init.offsets).astype(np.int64)
+    pairs_all = int((sizes_init * (sizes_init - 1) // 2).sum())
+    for b in s.batches[:nb]:
+        k = np.diff(b.inserts.offsets).astype(np.int64)
+        pairs_all += int((k * (k - 1) // 2).sum())
+    max_bh = max(args.batch, min(init.n, 100_000))
+    max_bi = max(max(b.inserts.nnz for b in s.batches), 4 * max_bh * 16)
+    todev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)  # noqa: E731
+    t0 = time.time()
+    g = E.Graph(s.n_vertices, todev(init.offsets, np.int64), todev(init.members, np.int32),
+                todev(init.timestamps, np.int64), capacity_hyperedges=init.n + args.batch + 64,
+                capacity_incidences=int(init.nnz * 1.6) + 4 * max(b.inserts.nnz for b in s.batches),
+                max_batch_hyperedges=max_bh, max_batch_incidences=max_bi, families=fam,
+                capacity_vertex_pairs=pairs_all, stream=torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    t_create = time.time() - t0
+    model = _LiveRule(init.n)
+    size_of = np.zeros(init.n + args.batch * nb + 64, np.int64)
+    size_of[:init.n] = sizes_init
+    predicted, dev_batches, host_batches, pair_ops = [], [], [], []
+    for b in s.batches[:nb]:
+        dels, ids = model.step(b.del_ranks, b.inserts.n)
+        kd = size_of[dels]
+        ki = np.diff(b.inserts.offsets).astype(np.int64)
+        pair_ops.append(int((kd * (kd - 1) // 2).sum() + (ki * (ki - 1) // 2).sum()))
+        size_of[ids] = ki
+        predicted.append(ids)
+        d32 = dels.astype(np.int32)
+        dev_batches.append((todev(b.inserts.offsets, np.int64), todev(b.inserts.members, np.int32),
+                            todev(b.inserts.timestamps, np.int64), todev(d32, np.int32)))
+        pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
+        host_batches.append((pin(b.inserts.offsets, np.int64), pin(b.inserts.members, np.int32),
+                             pin(b.inserts.timestamps, np.int64), pin(d32, np.int32)))
+    returned = []
+    g.set_profiling(True)
+
+    def step(bt):
+        out = np.zeros(bt[0].numel() - 1, np.int32)
+        E.esc_apply_batch(g.h, bt[0], bt[1], bt[2], bt[3], out)
+        returned.append(out)
+
+    st = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        step(dev_batches[k])
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = g.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, pair_ms = [], []
+    e0.record(st)
+    for k in range(args.warmup, args.warmup + args.steps):
+        ts0 = time.perf_counter()
+        step(dev_batches[k])
+        lat.append((time.perf_counter() - ts0) * 1e3)
+        pair_ms.append(g.stats()["ms_count_del"])
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    launches = g.launch_count() - l0
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    lat_e2e, h2d, d2h = [], 0, 0
+    te0 = time.perf_counter()
+    for k in range(args.warmup + args.steps, nb):
+        hb = host_batches[k]
+        t1 = time.perf_counter()
+        out = np.zeros(hb[0].numel() - 1, np.int32)
+        E.esc_apply_batch(g.h, hb[0].numpy(), hb[1].numpy(), hb[2].numpy(), hb[3].numpy(), out)
+        returned.append(out)
+        c = g.counts()
+        lat_e2e.append((time.perf_counter() - t1) * 1e3)
+        h2d += sum(t.numel() * t.element_size() for t in hb)
+        d2h += sum(v.nbytes for v in c.values())
+    te = time.perf_counter() - te0
+    for k, out in enumerate(returned):
+        if not np.array_equal(out, predicted[k]):
+            raise SystemExit(f"bench: batch {k}: the library's IDs differ from the ID rule's prediction")
+    v = g.counts()["vertex"]
+    g.close()
+    n_upd = [b.inserts.n + len(b.del_ranks) for b in s.batches[:nb]]
+    upd = sum(n_upd[args.warmup:args.warmup + args.steps])
+    upd_e2e = sum(n_upd[args.warmup + args.steps:nb])
+    hbm, kind = peaks()
+    ops = sum(pair_ops[args.warmup:args.warmup + args.steps])
+    pair_s = sum(pair_ms) / 1e3
+    # algorithmic bytes of the pair kernel: per (changed hyperedge, member
+    # pair), the pair's key (8 B) and its packed word (8 B read, 8 B written)
+    achieved = 24.0 * ops / pair_s / 1e9 if pair_s > 0 else 0.0
+    print(json.dumps({
+        "metric": METRIC, "value": upd / elapsed, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 ids / uint64 counts", "data": "synthetic",
+        "config": {"workload": (f"large, Zipf(1.1) vertex popularity as specified: {s.n_vertices:,} vertices, "
+                                f"{init.n:,} hyperedges, cardinality Zipf(2.0) in [2,{s.meta['kmax']}], batches of "
+                                f"{args.batch // 2:,} inserts + {args.batch - args.batch // 2:,} deletes"),
+                   "families": "incident-vertex types 1 and 2 (ESC_FAMILY_VERTEX12: vertex-pair statistics)",
+                   "max_vertex_degree": int(np.bincount(init.members).max()),
+                   "vertex_pairs_capacity": pairs_all, "create_s": round(t_create, 2)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "pair_updates_per_step": ops / args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": kind, "kernel": "k_pairs (vertex-pair statistics)",
+                     "bytes": "24 B per (changed hyperedge, member pair): the pair's key and its packed word "
+                              "read and written",
+                     "ms_per_step": pair_s * 1e3 / args.steps},
+        "e2e": {"value": upd_e2e / te, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps, "steps": args.steps},
+        "gpu_launches": int(launches), "clocks": clk,
+        "vertex_types_final": [int(x) for x in v],
+    }))
+
+
+# ---------------------------------------------------------------------------
 # DRAM traffic of the centre kernel, from the committed ncu summary
 # ---------------------------------------------------------------------------
 
@@ -1293,7 +1424,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large_uniform",
-                    choices=["large_uniform", "tiny", "batched", "temporal", "serving", "horizontal", "sweep"])
+                    choices=["large_uniform", "large_zipf", "tiny", "batched", "temporal", "serving", "horizontal",
+                             "sweep"])
     ap.add_argument("--sweep", default="batch", choices=["batch", "delete", "card", "size", "spread"],
                     help="sweep workload: which parameter varies")
     ap.add_argument("--size-scale", type=float, default=0.05, help="size sweep: fraction of 20M-55M hyperedges")
@@ -1320,6 +1452,8 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "large_zipf":
+        run_large_zipf(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "temporal":

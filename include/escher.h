@@ -116,6 +116,17 @@ typedef enum {
 #define ESC_FAMILY_HYPEREDGE 1u
 #define ESC_FAMILY_VERTEX 2u
 #define ESC_FAMILY_TEMPORAL 4u
+/* Incident-vertex types 1 and 2 only, kept from vertex-pair statistics
+ * (type 3 is not maintained and reads 0; esc_triads(ESC_TRIAD_VERTEX) gives
+ * the three values).  With m_uv the number of hyperedges holding the vertex
+ * pair {u, v} and S_uv the sum of their sizes, type 1 = sum over hyperedges
+ * of C(|h|, 3) and type 2 = sum over vertex pairs of
+ * (m_uv - 1) S_uv - 4 C(m_uv, 2) (Sec. II's types, this library's reading of
+ * them); a batch costs the sum over its hyperedges of C(|h|, 2), whatever the
+ * vertex degrees, so graphs with hub vertices stay cheap.  Needs
+ * capacity_vertex_pairs > 0 and at most 2^24 hyperedge IDs; excludes
+ * ESC_FAMILY_VERTEX.  esc_local_triads does not report it. */
+#define ESC_FAMILY_VERTEX12 8u
 
 #define ESC_N_HYPEREDGE_CLASSES 30
 #define ESC_N_VERTEX_TYPES 3
@@ -137,6 +148,11 @@ typedef struct {
     uint32_t families;              /* ESC_FAMILY_* bits of the families to keep   */
     int64_t delta;                  /* temporal window (timestamp units)           */
     int32_t debug;                  /* 0; reserved                                  */
+    int64_t capacity_vertex_pairs;  /* ESC_FAMILY_VERTEX12: distinct vertex pairs
+                                       (pairs of members of one hyperedge) the
+                                       graph may hold at once; 0 otherwise.  A
+                                       batch whose inserted hyperedges could
+                                       exceed it fails with OUT_OF_MEMORY        */
 } esc_config;
 
 typedef struct esc_graph esc_graph;

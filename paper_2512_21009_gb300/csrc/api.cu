@@ -74,6 +74,7 @@ struct Engine {
     int32_t* st_pin = nullptr;
     CountScratch cs{};
     int64_t max_u = 0;
+    PairTable pairs{};                 // vertex-pair statistics (ESC_FAMILY_VERTEX12)
     // pinned host copies of host-pointer inputs, grown on demand, so that a
     // call with many batches moves each input array with one copy
     struct Pinned {
@@ -159,7 +160,8 @@ static esc_status check_cfg(const esc_config* c, bool per_graph_only) {
     if (per_graph_only) return ESC_OK;
     if (c->max_batch_hyperedges <= 0 || c->max_batch_incidences <= 0) return ESC_ERR_INVALID_ARG;
     if (c->max_batch_incidences > 0x7fffffffLL) return ESC_ERR_UNSUPPORTED;
-    if (c->families == 0 || (c->families & ~7u)) return ESC_ERR_INVALID_ARG;
+    if (c->families == 0 || (c->families & ~15u)) return ESC_ERR_INVALID_ARG;
+    if ((c->families & kFamV) && (c->families & kFamV12)) return ESC_ERR_INVALID_ARG;
     if (c->delta < 0) return ESC_ERR_INVALID_ARG;
     return ESC_OK;
 }
@@ -206,6 +208,14 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
         inc += per[g].capacity_incidences;
     }
     if (V > 0x7fffffffLL || Ecap > 0x7fffffffLL) return E->fail(ESC_ERR_UNSUPPORTED, "ID spaces exceed int32");
+    int64_t pair_cap = 0;
+    for (int g = 0; g < G; ++g) pair_cap += per[g].capacity_vertex_pairs;
+    if (shared.families & kFamV12) {
+        if (pair_cap <= 0) return E->fail(ESC_ERR_INVALID_ARG, "ESC_FAMILY_VERTEX12 needs capacity_vertex_pairs");
+        // a pair's hyperedge count and size sum share one 64-bit word (24 + 40 bits)
+        if (Ecap >= (int64_t(1) << 24))
+            return E->fail(ESC_ERR_UNSUPPORTED, "ESC_FAMILY_VERTEX12 holds at most 2^24 hyperedge IDs");
+    }
     E->inc_cap = inc;
     Store& S = E->S;
     S.n_graphs = G;
@@ -345,6 +355,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     }
     if (dry) {
         E->dry_bytes += int64_t(count_scratch_bytes(sh));
+        if (shared.families & kFamV12) E->dry_bytes += int64_t(pair_table_bytes(pair_cap));
         return ESC_OK;
     }
     void* csmem = nullptr;
@@ -375,6 +386,12 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
         long long v = atoll(env);
         if (v >= 64 && (v & (v - 1)) == 0) E->cs.smem_slots = v;
+    }
+    if (shared.families & kFamV12) {
+        void* pm = nullptr;
+        ESC_CU(cudaMalloc(&pm, pair_table_bytes(pair_cap)), "alloc pair table");
+        E->allocs.push_back(pm);
+        ESC_CU(pair_table_init(&E->pairs, pm, pair_cap, st), "pair table init");
     }
     ESC_CU(upload_tables(st), "tables");
     for (auto& e : E->ev) ESC_CU(cudaEventCreate(&e), "event");
@@ -498,17 +515,26 @@ static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStr
                                    bool prof = false) {
     const Store& S = E->S;
     cudaError_t e;
+    const bool nbh = (S.fam & (kFamH | kFamV | kFamT)) != 0;  // a family counted from neighbourhoods
+    const bool pairs = (S.fam & kFamV12) != 0;
     {
         Range r("escher: ingest");
-        if ((e = store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, E->max_u, E->sm_count, st, lc))) return e;
+        // the neighbourhood-size limit binds only the families counted from
+        // neighbourhoods
+        if ((e = store_ingest(S, C, E->d_bins_lo, E->d_bdel_lo, nbh ? E->max_u : INT64_MAX, E->sm_count, st, lc)))
+            return e;
+        if (pairs) {
+            if ((e = pairs_check(E->pairs, C, st, lc))) return e;
+            if ((e = store_latch(C, st, lc))) return e;
+        }
     }
-    if (fixed) {
+    if (fixed && nbh) {
         // the inserted side's runs must fit the sequence before anything changes
         if ((e = count_precheck_fixed(S, C, E->cs, E->max_u, kFixedRuns, st, lc))) return e;
         if ((e = store_latch(C, st, lc))) return e;
     }
     if (prof) cudaEventRecord(E->ev[1], st);
-    {
+    if (nbh) {
         Range r("escher: count, deleted side");
         if (fixed)
             e = count_launch_fixed(S, C.sc, C.del, C.del_g, S.delb, C.dims + 2, 0, S.dcounts, E->cs, E->max_u,
@@ -521,6 +547,13 @@ static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStr
         // a failed count (the retry status) must leave the store unchanged
         if ((e = store_latch(C, st, lc))) return e;
     }
+    if (pairs) {
+        // vertex-pair statistics: the deleted hyperedges leave (their members
+        // are still in the store), then the inserted ones arrive
+        Range r("escher: vertex pairs");
+        if ((e = pairs_update(S, C, E->pairs, 0, E->sm_count, st, lc))) return e;
+        if ((e = pairs_update(S, C, E->pairs, 1, E->sm_count, st, lc))) return e;
+    }
     if (prof) cudaEventRecord(E->ev[2], st);
     {
         Range r("escher: store update");
@@ -529,7 +562,7 @@ static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStr
     }
     if (prof) cudaEventRecord(E->ev[3], st);
     uint64_t* dins = S.dcounts + int64_t(S.n_graphs) * kCStride;
-    {
+    if (nbh) {
         Range r("escher: count, inserted side");
         if (fixed)
             e = count_launch_fixed(S, C.sc, C.ids, C.ins_g, S.insb, C.dims + 1, 1, dins, E->cs, E->max_u,
@@ -946,7 +979,7 @@ static esc_status read_counts(Engine* E, int32_t g, esc_triad_type type, int64_t
     uint32_t fam;
     switch (type) {
         case ESC_TRIAD_HYPEREDGE: off = 0; len = kNH; fam = kFamH; break;
-        case ESC_TRIAD_VERTEX: off = kOffV; len = kNV; fam = kFamV; break;
+        case ESC_TRIAD_VERTEX: off = kOffV; len = kNV; fam = kFamV | kFamV12; break;
         case ESC_TRIAD_TEMPORAL: off = kOffT; len = kNT; fam = kFamT; break;
         default: return E->fail(ESC_ERR_INVALID_ARG, "bad triad type");
     }

@@ -32,7 +32,7 @@ constexpr int kOffT = kNH + kNV;
 constexpr int kNCount = kNH + kNV + kNT; // 129
 constexpr int kCStride = 136;            // counters per graph, padded
 
-constexpr uint32_t kFamH = 1u, kFamV = 2u, kFamT = 4u;
+constexpr uint32_t kFamH = 1u, kFamV = 2u, kFamT = 4u, kFamV12 = 8u;
 
 // status codes, identical to esc_status
 constexpr int kOk = 0, kErrInvalid = 1, kErrNotFound = 2, kErrNoMem = 3, kErrUnsupported = 4,

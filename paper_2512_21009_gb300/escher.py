@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libescher.so")
 FAMILY_HYPEREDGE = 1
 FAMILY_VERTEX = 2
 FAMILY_TEMPORAL = 4
+FAMILY_VERTEX12 = 8
 TRIAD_HYPEREDGE, TRIAD_VERTEX, TRIAD_TEMPORAL = 0, 1, 2
 N_CLASSES = {TRIAD_HYPEREDGE: 30, TRIAD_VERTEX: 3, TRIAD_TEMPORAL: 96}
 STATUS = {0: "ESC_OK", 1: "ESC_ERR_INVALID_ARG", 2: "ESC_ERR_NOT_FOUND", 3: "ESC_ERR_OUT_OF_MEMORY",
@@ -54,7 +55,7 @@ class esc_config(C.Structure):
     _fields_ = [("n_vertices", C.c_int32), ("capacity_hyperedges", C.c_int64),
                 ("capacity_incidences", C.c_int64), ("max_batch_hyperedges", C.c_int64),
                 ("max_batch_incidences", C.c_int64), ("families", C.c_uint32), ("delta", C.c_int64),
-                ("debug", C.c_int32)]
+                ("debug", C.c_int32), ("capacity_vertex_pairs", C.c_int64)]
 
 
 class esc_batch_stats(C.Structure):
@@ -637,9 +638,10 @@ def esc_count_static_noalloc(n_vertices: int, offsets, members, timestamps, fami
 
 def make_config(n_vertices: int, capacity_hyperedges: int, capacity_incidences: int,
                 max_batch_hyperedges: int, max_batch_incidences: int, families: int,
-                delta: int = 0) -> esc_config:
+                delta: int = 0, capacity_vertex_pairs: int = 0) -> esc_config:
     return esc_config(int(n_vertices), int(capacity_hyperedges), int(capacity_incidences),
-                      int(max_batch_hyperedges), int(max_batch_incidences), int(families), int(delta), 0)
+                      int(max_batch_hyperedges), int(max_batch_incidences), int(families), int(delta), 0,
+                      int(capacity_vertex_pairs))
 
 
 class Graph:
@@ -647,12 +649,13 @@ class Graph:
 
     def __init__(self, n_vertices: int, offsets=None, members=None, timestamps=None, *,
                  capacity_hyperedges: int, capacity_incidences: int, max_batch_hyperedges: int,
-                 max_batch_incidences: int, families: int, delta: int = 0, stream=None):
+                 max_batch_incidences: int, families: int, delta: int = 0, stream=None,
+                 capacity_vertex_pairs: int = 0):
         self.n_vertices = int(n_vertices)
         self.families = families
         self.delta = int(delta)
         self.cfg = make_config(n_vertices, capacity_hyperedges, capacity_incidences, max_batch_hyperedges,
-                               max_batch_incidences, families, delta)
+                               max_batch_incidences, families, delta, capacity_vertex_pairs)
         if offsets is None:
             offsets = np.zeros(1, np.int64)
             members = np.zeros(0, np.int32)
@@ -694,7 +697,7 @@ class Graph:
         out = {}
         if self.families & FAMILY_HYPEREDGE:
             out["hyperedge"] = self.triads(TRIAD_HYPEREDGE)
-        if self.families & FAMILY_VERTEX:
+        if self.families & (FAMILY_VERTEX | FAMILY_VERTEX12):
             out["vertex"] = self.triads(TRIAD_VERTEX)
         if self.families & FAMILY_TEMPORAL:
             out["temporal"] = self.triads(TRIAD_TEMPORAL)

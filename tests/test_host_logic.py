@@ -94,3 +94,55 @@ def test_restored_oracle_graph_hands_out_the_same_ids():
                 assert np.array_equal(a, b)
             for x, y in zip(og.csr(), r.csr()):
                 assert np.array_equal(x, y)
+
+
+def _pair_stats(E):
+    """m_uv and S_uv over all vertex pairs of the hyperedges E."""
+    import itertools
+    st = {}
+    for e in E:
+        for u, v in itertools.combinations(sorted(set(e)), 2):
+            m, s = st.get((u, v), (0, 0))
+            st[(u, v)] = (m + 1, s + len(set(e)))
+    return st
+
+
+def test_vertex_types_1_2_from_pair_statistics_match_the_oracle():
+    """The vertex-pair form the GPU's ESC_FAMILY_VERTEX12 keeps: type 1 =
+    sum C(|h|,3), type 2 = sum over vertex pairs of (m-1) S - 4 C(m,2), and
+    the per-step changes S + m (k - 4) (add) / (S - k) + (m - 1)(k - 4)
+    (remove) telescoping to the recount -- checked against the oracle's
+    per-triple and literal counts on random hypergraphs with repeated sets."""
+    import itertools
+    import math
+    from oracle import oracle as O
+    rng = np.random.default_rng(8)
+    for trial in range(6):
+        nv = 12
+        E = [sorted(rng.choice(nv, size=int(rng.integers(2, 7)), replace=False).tolist()) for _ in range(14)]
+        E += [list(E[int(rng.integers(0, len(E)))]) for _ in range(3)]   # identical sets
+        off = np.concatenate([[0], np.cumsum([len(e) for e in E])]).astype(np.int64)
+        mem = np.concatenate([np.array(e, np.int32) for e in E])
+        want = O.count_vertex(off, mem, nv, "literal")
+        t1 = sum(math.comb(len(e), 3) for e in E)
+        t2 = sum((m - 1) * s - 4 * math.comb(m, 2) for m, s in _pair_stats(E).values())
+        assert [t1, t2] == [int(want[0]), int(want[1])], trial
+        # incremental: add the hyperedges one by one, then remove some
+        st, acc = {}, 0
+        for e in E:
+            k = len(e)
+            for p in itertools.combinations(e, 2):
+                m, s = st.get(p, (0, 0))
+                acc += s + m * (k - 4)
+                st[p] = (m + 1, s + k)
+        assert acc == t2
+        keep = E[5:]
+        for e in E[:5]:
+            k = len(e)
+            for p in itertools.combinations(e, 2):
+                m, s = st[p]
+                acc -= (s - k) + (m - 1) * (k - 4)
+                st[p] = (m - 1, s - k)
+        off2 = np.concatenate([[0], np.cumsum([len(e) for e in keep])]).astype(np.int64)
+        mem2 = np.concatenate([np.array(e, np.int32) for e in keep])
+        assert acc == int(O.count_vertex(off2, mem2, nv, "literal")[1])
