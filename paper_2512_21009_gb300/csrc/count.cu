@@ -1587,7 +1587,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// 3b. oriented centre kernel (hyperedge and incident-vertex families)
+// 3b. oriented centre kernel (all neighbourhood families)
 // ---------------------------------------------------------------------------
 //
 // Without the temporal family every open triad is counted in aggregate, so
@@ -1607,6 +1607,19 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
 // class.  The changed f < h of N(g1) are left out of h's aggregate at g1
 // whether or not they lie in N(h): their triads belong to f.  So no mark of
 // N(h) inside N(g1) is kept, and every closed triad is classified once.
+//
+// With the temporal family (TEMP) an open triad's class also depends on the
+// time order of its three hyperedges and on the window, which no aggregate
+// over N(g1) or N'(h) keeps.  The pair pass then visits every g2 of N'(h)
+// above g1 (modes 0 and 3; the plus list is not used): a g2 outside N(g1)
+// is an open triad centred at h, classified on the spot, a g2 inside it a
+// closed pair, queued as before.  Open triads centred at g1 are counted per
+// h by a warp over N(g1), bucketed by the static class bits and by where f
+// falls in time against h and g1 (a constant number of counters per h).  A
+// closed triad takes back the two open classes the warp pass gave it (at g1
+// with f = g2, at g2 with f = g1), static and temporal, and adds its closed
+// class; open triads at h need no taking back, since only open pairs were
+// classified as such.
 
 constexpr int kG1M = 1024;  // members of g1 kept in shared memory, at most
 
@@ -1642,9 +1655,22 @@ struct SmemCO {
     uint32_t vals[T1_S];
     int32_t list[T1_S / 2];
     int32_t lk[T1_S / 2];        // |f|, bit 31: f is changed
-    int32_t pf[T1_S / 2];        // plus list: f above g1 ...
-    uint32_t pm[T1_S / 2];       // ... and |g1 & f| | |f| << 16 | changed << 31
-    long long cl[T1_S / 2];      // changed f: f | |g1 & f| << 31 | |f| << 46
+    union {
+        struct {
+            int32_t pf[T1_S / 2];    // plus list: f above g1 ...
+            uint32_t pm[T1_S / 2];   // ... and |g1 & f| | |f| << 16 | changed << 31
+        } p;
+        int64_t lts[T1_S / 2];       // with the temporal family: the timestamp of every f
+    } u1;
+    union {
+        long long cl[T1_S / 2];      // changed f: f | |g1 & f| << 31 | |f| << 46
+        struct {                     // with the temporal family:
+            uint32_t th[NW_C][kNT];  //   temporal class bins per warp
+            uint32_t tn[kNT];        //   temporal classes taken back for closed triads
+            unsigned long long tacc[kNT];
+            int64_t hts[LCH];        //   timestamps of the chunk's h
+        } t;
+    } u2;
     int64_t seg_off[NT_C];
     int32_t seg_pre[NT_C + 1];
     int warp_tmp[32];
@@ -1677,7 +1703,23 @@ __device__ __forceinline__ unsigned long long order_key(int k, int32_t g) {
     return (uint64_t(uint32_t(k)) << 32) | uint64_t(uint32_t(g));
 }
 
-template <int NT_C, int T1_S, int MINB>
+// Temporal class of the triple with labels a, b, c (7-bit mask m under those
+// labels), timestamps ta, tb, tc and IDs ia, ib, ic: the labels ordered by
+// (timestamp, ID), the mask read in that order; -1 outside the window.
+__device__ __forceinline__ int temporal_class(const Tables& tbl, int m, int64_t ta, int64_t tb, int64_t tc,
+                                              int32_t ia, int32_t ib, int32_t ic, int64_t delta) {
+    const int64_t T[3] = {ta, tb, tc};
+    const int32_t I[3] = {ia, ib, ic};
+    int o0 = 0, o1 = 1, o2 = 2, tmp;
+#define ESC_BEFORE(x, y) (T[x] < T[y] || (T[x] == T[y] && I[x] < I[y]))
+    if (ESC_BEFORE(o1, o0)) { tmp = o0; o0 = o1; o1 = tmp; }
+    if (ESC_BEFORE(o2, o1)) { tmp = o1; o1 = o2; o2 = tmp; }
+    if (ESC_BEFORE(o1, o0)) { tmp = o0; o0 = o1; o1 = tmp; }
+#undef ESC_BEFORE
+    return T[o2] - T[o0] <= delta ? tbl.cls96[tbl.perm[perm_index(o0, o1)][m]] : -1;
+}
+
+template <int NT_C, int T1_S, int MINB, bool TEMP>
 __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
     constexpr int NW_C = NT_C / 32;
     using Sm = SmemCO<NT_C, T1_S>;
@@ -1689,7 +1731,12 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
     const int lane = lane_id();
     const int wid = warp_id();
     const uint32_t fam = S.fam;
-    const bool agg = (fam & kFamH) != 0;   // the open triads, in aggregate
+    const bool want_h = (fam & kFamH) != 0;
+    // without the temporal family the open triads are counted in aggregate;
+    // with it (TEMP) the open triads centred at h are enumerated from the
+    // suffixes of N(h) and those centred at g1 counted per h by time position
+    const bool agg = want_h && !TEMP;
+    const int64_t delta = S.delta;
     const CountScratch& cs = A.cs;
     const RunRange R = run_of(A);
     const int32_t* v2h = S.vp.arena;
@@ -1700,6 +1747,13 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
         s.hneg[i / 32][i % 32] = 0;
     }
     for (int i = tid; i < 32; i += NT_C) s.acc[i] = 0;
+    if constexpr (TEMP) {
+        for (int i = tid; i < NW_C * kNT; i += NT_C) s.u2.t.th[i / kNT][i % kNT] = 0;
+        for (int i = tid; i < kNT; i += NT_C) {
+            s.u2.t.tn[i] = 0;
+            s.u2.t.tacc[i] = 0;
+        }
+    }
     for (int i = tid; i < T1_S; i += NT_C) {
         s.keys[i] = EMPTY;
         s.vals[i] = 0;
@@ -1723,6 +1777,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
     int32_t* g_pf = cs.oc_pf + blockIdx.x * (gs / 2);
     uint32_t* g_pm = cs.oc_pm + blockIdx.x * (gs / 2);
     long long* g_cl = reinterpret_cast<long long*>(cs.oc_lts) + blockIdx.x * (gs / 2);
+    int64_t* g_lts = cs.oc_lts + blockIdx.x * (gs / 2);
     uint32_t* hist = s.hist[wid];
     uint32_t* hneg = s.hneg[wid];
     Accum acc = {0, 0, 0, 0, 0, 0, 0, 0, {0, 0, 0, 0, 0, 0}, 0, 0, 0, 0, 0};
@@ -1752,6 +1807,14 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(cur_g) * kCStride + b]), v);
                     s.acc[b] = 0;
                 }
+                if constexpr (TEMP)
+                    for (int b = tid; b < kNT; b += NT_C) {
+                        unsigned long long v = s.u2.t.tacc[b];
+                        if (v)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(
+                                          &A.dc[int64_t(cur_g) * kCStride + kOffT + b]), v);
+                        s.u2.t.tacc[b] = 0;
+                    }
                 flush<NT_C>(A, nullptr, nullptr, 0, cur_g, acc, s.red);
             }
             cur_g = g;
@@ -1764,6 +1827,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
             for (int t = tid; t < k1; t += NT_C) s.g1m[t] = g1mem[t];
         const int32_t* g1s = k1 <= kG1M ? s.g1m : g1mem;
         const unsigned long long key1 = order_key(k1, g1);
+        const int64_t ts1 = TEMP ? S.h_ts[g1] : 0;
         const long long u1 = cs.d_u1[j];
         acc.n_h2v += (tid < k1) ? (k1 - tid + NT_C - 1) / NT_C : 0;
         if (tid == 0) {
@@ -1777,20 +1841,23 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
         int32_t* pf;
         uint32_t* pm;
         long long* cl;
+        int64_t* lts;
         int P = 1;
         const uint32_t t1_cap = pow2_at_least(2 * u1);
         if (t1_cap <= min(A.c_smem_cap, uint32_t(T1_S))) {
             T1 = Tab{s.keys, s.vals, nullptr, s.list, &s.n_list, t1_cap - 1, T1_S / 2};
             lk = s.lk;
-            pf = s.pf;
-            pm = s.pm;
-            cl = s.cl;
+            pf = s.u1.p.pf;
+            pm = s.u1.p.pm;
+            cl = s.u2.cl;
+            lts = s.u1.lts;
         } else {
             T1 = Tab{g_keys, g_vals, nullptr, g_list, &s.n_list, uint32_t(gs - 1), int(gs / 2)};
             lk = g_lk;
             pf = g_pf;
             pm = g_pm;
             cl = g_cl;
+            lts = g_lts;
             if ((int64_t)t1_cap <= gs) T1.mask = t1_cap - 1;
             else P = int((4 * u1 + gs - 1) / gs);
         }
@@ -1859,7 +1926,8 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     lk[q] = kf | (changed_f ? int32_t(0x80000000u) : 0);
                     const uint32_t bb = bloom_bit(f, bw);
                     atomicOr(&s.bloom[bb >> 5], 1u << (bb & 31));
-                    if (order_key(kf, f) > key1) {
+                    if (TEMP) lts[q] = S.h_ts[f];
+                    if (!TEMP && order_key(kf, f) > key1) {
                         const int c = atomicAdd(&s.n_plus, 1);
                         pf[c] = f;
                         pm[c] = uint32_t(x) | (uint32_t(kf) << 16) | (changed_f ? 0x80000000u : 0u);
@@ -1918,17 +1986,19 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         s.htoff[l] = cs.nh_toff[li];
                         s.hpos[l] = hpos;
                         s.hIn[l] = 0;
+                        if (TEMP) s.u2.t.hts[l] = S.h_ts[h];
                         int mode;
                         if (hpos >= 0) {
                             const int sfx = hnn - hpos - 1;
-                            if (htcap > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
+                            // with the temporal family every pair above g1 is visited
+                            if (!TEMP && htcap > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
                                 mode = 1;
                                 work = n_plus;
                             } else {
                                 mode = 0;
                                 work = sfx;
                             }
-                        } else if (htcap > 0) {
+                        } else if (!TEMP && htcap > 0) {
                             mode = 1;
                             work = n_plus;
                         } else {
@@ -2005,23 +2075,37 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                                                 kh, s.hI[l], s.hIn[l], acc.w[4]);
                     acc.n_meta += 1;
                     acc.n_closed += (unsigned long long)min(k1, k2);  // closed pairs: min(|g1|, |g2|) entries
-                    if (agg) {
-                        const int ra = kh - xh1 - xh2 + t, rb = k1 - xh1 - x12 + t, rc = k2 - x12 - xh2 + t;
-                        const int mk = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xh1 - t > 0) << 3) |
-                                       ((x12 - t > 0) << 4) | ((xh2 - t > 0) << 5) | ((t > 0) << 6);
-                        ++acc.n_tri;
+                    const int ra = kh - xh1 - xh2 + t, rb = k1 - xh1 - x12 + t, rc = k2 - x12 - xh2 + t;
+                    const int mk = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((xh1 - t > 0) << 3) |
+                                   ((x12 - t > 0) << 4) | ((xh2 - t > 0) << 5) | ((t > 0) << 6);
+                    // the open classes the open-triad counts gave this triple:
+                    // centred at g1 (f = g2) and at g2 (f = g1), and, when
+                    // those at h are counted in aggregate, centred at h
+                    const int m1 = (kh > xh1 ? 1 : 0) | (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 4 : 0) | 8 | 16;
+                    const int m2 = (kh > xh2 ? 1 : 0) | (x12 != k2 - xh2 ? 2 : 0) | (k1 > x12 ? 4 : 0) | 8 | 16;
+                    ++acc.n_tri;
+                    if (want_h) {
                         // every mask formed here is a valid triad (its pairwise
                         // intersections are non-empty), so each class is >= 0
                         const int cc = s.tb.cls30[mk];
-                        // the open classes the aggregates gave this triple
-                        const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
-                        const int m1 = (kh > xh1 ? 1 : 0) | (x12 != k1 - xh1 ? 2 : 0) | (k2 > x12 ? 4 : 0) | 8 | 16;
-                        const int m2 = (kh > xh2 ? 1 : 0) | (x12 != k2 - xh2 ? 2 : 0) | (k1 > x12 ? 4 : 0) | 8 | 16;
                         const int c1 = s.tb.cls30[m1], c2 = s.tb.cls30[m2];
                         if (cc >= 0) atomicAdd(&hist[cc], 1u);
-                        if (ch >= 0) atomicAdd(&hneg[ch], 1u);
+                        if (!TEMP) {
+                            const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
+                            if (ch >= 0) atomicAdd(&hneg[ch], 1u);
+                        }
                         if (c1 >= 0) atomicAdd(&hneg[c1], 1u);
                         if (c2 >= 0) atomicAdd(&hneg[c2], 1u);
+                    }
+                    if constexpr (TEMP) {
+                        const int32_t h = s.hh[l];
+                        const int64_t th = s.u2.t.hts[l], t2 = S.h_ts[g2];
+                        const int cc = temporal_class(s.tb, mk, th, ts1, t2, h, g1, g2, delta);
+                        const int p1 = temporal_class(s.tb, m1, th, ts1, t2, h, g1, g2, delta);
+                        const int p2 = temporal_class(s.tb, m2, th, t2, ts1, h, g2, g1, delta);
+                        if (cc >= 0) atomicAdd(&s.u2.t.th[wid][cc], 1u);
+                        if (p1 >= 0) atomicAdd(&s.u2.t.tn[p1], 1u);
+                        if (p2 >= 0) atomicAdd(&s.u2.t.tn[p2], 1u);
                     }
                     if (fam & kFamV)
                         acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
@@ -2064,6 +2148,34 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         chg2 = (m >> 31) != 0;
                         xh2 = int(uint32_t(xv2) & kXMask);
                         vf2 = int32_t(uint32_t(xv2 >> 32));
+                    } else if constexpr (TEMP) {
+                        // every g2 of N'(h) above g1: closed pairs queued, open
+                        // ones (centred at h) classified here
+                        const int64_t at = s.hnb[l] + (mode == 0 ? s.hpos[l] + 1 + q : q);
+                        g2 = cs.nh_g[at];
+                        const uint64_t xv2 = cs.nh_xv[at];
+                        k2 = int((xv2 >> 16) & 0x7fffu);
+                        if (mode == 3 && order_key(k2, g2) <= key1) break;
+                        chg2 = ((xv2 >> 31) & 1u) != 0;
+                        const int32_t h = s.hh[l];
+                        if (g2 < h && chg2) break;  // the triple belongs to g2 (or a smaller changed member)
+                        if (P > 1 && part_of(g2, P) != p) break;
+                        xh2 = int(xv2 & kXMask);
+                        vf2 = int32_t(uint32_t(xv2 >> 32));
+                        const uint32_t bb = bloom_bit(g2, bw);
+                        const int sl = ((s.bloom[bb >> 5] >> (bb & 31)) & 1u) ? tab_find(T1, g2) : -1;
+                        if (sl < 0) {
+                            const int m = open_at_h_mask(s.hk[l], s.hx[l], xh2, k1, k2);
+                            ++acc.n_tri;
+                            if (want_h) {
+                                const int c = s.tb.cls30[m];
+                                if (c >= 0) atomicAdd(&hist[c], 1u);
+                            }
+                            const int c96 = temporal_class(s.tb, m, s.u2.t.hts[l], ts1, cs.nh_ts[at], h, g1, g2, delta);
+                            if (c96 >= 0) atomicAdd(&s.u2.t.th[wid][c96], 1u);
+                            break;
+                        }
+                        x12 = int(T1.vals[sl]);
                     } else {
                         const int64_t at = s.hnb[l] + (mode == 0 ? s.hpos[l] + 1 + q : q);
                         g2 = cs.nh_g[at];
@@ -2110,6 +2222,73 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                 __syncwarp();
                 if (lane < qn) classify(lane);
                 __syncthreads();
+                if constexpr (TEMP) {
+                    // open triads {h, g1, f} centred at g1: f in N(g1), f != h,
+                    // f not a changed hyperedge of smaller ID than h (its triads
+                    // belong to f).  Their class is set by A = [h not inside g1],
+                    // the bucket 2B + C of f (B = [|g1&f| != |g1| - |h&g1|],
+                    // C = [f not inside g1]) and, for the temporal family, by
+                    // where f falls in time against h and g1 and whether the
+                    // triple fits the window; a warp per h counts its f by
+                    // (position, bucket).  Those f that meet h (closed triples)
+                    // are taken back when their closed pair is classified.
+                    for (int l = wid; l < nh; l += NW_C) {
+                        const int32_t h = s.hh[l];
+                        const int xh1 = s.hx[l], xstar = k1 - xh1;
+                        const int64_t th = s.u2.t.hts[l];
+                        const bool h_first = th < ts1 || (th == ts1 && h < g1);
+                        const int64_t tp = h_first ? th : ts1, tq = h_first ? ts1 : th;
+                        const int32_t ip = h_first ? h : g1, iq = h_first ? g1 : h;
+                        uint32_t cst[4] = {0, 0, 0, 0};
+                        uint32_t ctm[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+                        for (int q = lane; q < n1; q += 32) {
+                            const int sl = T1.list[q];
+                            const int32_t f = T1.keys[sl];
+                            if (f == h) continue;
+                            const int32_t meta = lk[q];
+                            if (meta < 0 && f < h) continue;
+                            const int x = int(T1.vals[sl]);
+                            const int b = (x != xstar ? 2 : 0) | ((meta & 0x7fffffff) > x ? 1 : 0);
+                            const int64_t tf = lts[q];
+                            int r;  // position in time, -1: outside the window
+                            if (tf < tp || (tf == tp && f < ip)) r = tq - tf <= delta ? 0 : -1;
+                            else if (tf < tq || (tf == tq && f < iq)) r = tq - tp <= delta ? 1 : -1;
+                            else r = tf - tp <= delta ? 2 : -1;
+                            // constant indices keep the counters in registers
+#pragma unroll
+                            for (int bb = 0; bb < 4; ++bb) {
+                                cst[bb] += b == bb ? 1u : 0u;
+#pragma unroll
+                                for (int rr = 0; rr < 3; ++rr) ctm[rr][bb] += (b == bb && r == rr) ? 1u : 0u;
+                            }
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                            for (int b = 0; b < 4; ++b) {
+                                cst[b] += __shfl_xor_sync(0xffffffffu, cst[b], o);
+#pragma unroll
+                                for (int r = 0; r < 3; ++r) ctm[r][b] += __shfl_xor_sync(0xffffffffu, ctm[r][b], o);
+                            }
+                        }
+                        if (lane == 0) {
+                            const int A_bit = s.hk[l] > xh1 ? 1 : 0;
+                            // labels 0 = h, 1 = g1, 2 = f; p and q are h and g1 in time order
+                            const int lp = h_first ? 0 : 1, lq = h_first ? 1 : 0;
+                            for (int b = 0; b < 4; ++b) {
+                                const int m = A_bit | ((b >> 1) << 1) | ((b & 1) << 2) | (1 << 3) | (1 << 4);
+                                acc.n_tri += cst[b];
+                                if (want_h && cst[b] && s.tb.cls30[m] >= 0) atomicAdd(&hist[s.tb.cls30[m]], cst[b]);
+                                for (int r = 0; r < 3; ++r) {
+                                    if (!ctm[r][b]) continue;
+                                    const int o0 = r == 0 ? 2 : lp, o1 = r == 0 ? lp : (r == 1 ? 2 : lq);
+                                    const int c = s.tb.cls96[s.tb.perm[perm_index(o0, o1)][m]];
+                                    if (c >= 0) atomicAdd(&s.u2.t.th[wid][c], ctm[r][b]);
+                                }
+                            }
+                        }
+                    }
+                }
                 if (agg) {
                     // open triads {h, g1, f} centred at g1, in aggregate: the
                     // class is set by A = [h not inside g1] and the bucket
@@ -2193,6 +2372,17 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
             }
             s.acc[b] += v;
         }
+        if constexpr (TEMP)
+            for (int b = tid; b < kNT; b += NT_C) {
+                unsigned long long v = 0;
+                for (int w = 0; w < NW_C; ++w) {
+                    v += s.u2.t.th[w][b];
+                    s.u2.t.th[w][b] = 0;
+                }
+                v -= s.u2.t.tn[b];
+                s.u2.t.tn[b] = 0;
+                s.u2.t.tacc[b] += v;
+            }
     }
     __syncthreads();
     if (cur_g >= 0) {
@@ -2201,6 +2391,12 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
             if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(cur_g) * kCStride + b]), v);
             s.acc[b] = 0;
         }
+        if constexpr (TEMP)
+            for (int b = tid; b < kNT; b += NT_C) {
+                unsigned long long v = s.u2.t.tacc[b];
+                if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(cur_g) * kCStride + kOffT + b]), v);
+                s.u2.t.tacc[b] = 0;
+            }
         flush<NT_C>(A, nullptr, nullptr, 0, cur_g, acc, s.red);
     }
     flush_stats<NT_C>(A, acc, s.red);
@@ -2438,14 +2634,16 @@ void count_prepare() {
                          int(sizeof(SmemC<512, 4096>)));
     cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(SmemC<256, 2048>)));
-    cudaFuncSetAttribute(k_center_o<512, 8192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sizeof(SmemCO<512, 8192>)));
-    cudaFuncSetAttribute(k_center_o<256, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sizeof(SmemCO<256, 4096>)));
-    cudaFuncSetAttribute(k_center_o<512, 4096, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sizeof(SmemCO<512, 4096>)));
-    cudaFuncSetAttribute(k_center_o<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sizeof(SmemCO<256, 2048>)));
+#define ESC_CO_ATTR(NT, TS, MB)                                                                          \
+    cudaFuncSetAttribute(k_center_o<NT, TS, MB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                         int(sizeof(SmemCO<NT, TS>)));                                                      \
+    cudaFuncSetAttribute(k_center_o<NT, TS, MB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                         int(sizeof(SmemCO<NT, TS>)));
+    ESC_CO_ATTR(512, 8192, 1)
+    ESC_CO_ATTR(256, 4096, 2)
+    ESC_CO_ATTR(512, 4096, 2)
+    ESC_CO_ATTR(256, 2048, 3)
+#undef ESC_CO_ATTR
     });
 }
 
@@ -2454,9 +2652,10 @@ void count_prepare() {
 static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed, const int32_t* changed_g,
                              const uint32_t* chg_bits, int64_t lo, int64_t n, bool dev, int side,
                              uint64_t* dcounts_side, const CountScratch& cs, cudaStream_t st, LaunchCounter& lc) {
-    // without the temporal family (and without restricted lists) closed pairs
-    // are searched in (|g|, g) order by k_center_o
-    const bool orient = cs.orient && !(S.fam & kFamT) && cs.r_cap == 0;
+    // without restricted lists closed pairs are searched in (|g|, g) order by
+    // k_center_o (its temporal variant when the temporal family is kept)
+    const bool orient = cs.orient && cs.r_cap == 0;
+    const bool temp = (S.fam & kFamT) != 0;
     CountArgs A{S, sc, changed, changed_g, chg_bits, lo, n, side, dcounts_side, cs,
                 uint32_t(cs.smem_slots < NH_S ? cs.smem_slots : NH_S),
                 uint32_t(std::min<int64_t>(cs.smem_slots, cs.center_small == 0 ? 8192 : 4096)), dev, orient};
@@ -2492,12 +2691,16 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     // three blocks per SM need the tables sized for them
     const int shape = cs.center_small == 3 && cs.c_per_sm < 3 ? 1 : cs.center_small;
     if (orient) {
+#define ESC_CO_LAUNCH(NT, TS, MB, GRID)                                                            \
+    (temp ? k_center_o<NT, TS, MB, true><<<GRID, NT, sizeof(SmemCO<NT, TS>), st>>>(A)             \
+          : k_center_o<NT, TS, MB, false><<<GRID, NT, sizeof(SmemCO<NT, TS>), st>>>(A))
         switch (shape) {
-            case 0: k_center_o<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemCO<512, 8192>), st>>>(A); break;
-            case 2: k_center_o<512, 4096, 2><<<cs.n_cta_c * 2, 512, sizeof(SmemCO<512, 4096>), st>>>(A); break;
-            case 3: k_center_o<256, 2048, 3><<<cs.n_cta_c * 3, 256, sizeof(SmemCO<256, 2048>), st>>>(A); break;
-            default: k_center_o<256, 4096, 2><<<cs.n_cta_c * 2, 256, sizeof(SmemCO<256, 4096>), st>>>(A); break;
+            case 0: ESC_CO_LAUNCH(512, 8192, 1, cs.n_cta_c); break;
+            case 2: ESC_CO_LAUNCH(512, 4096, 2, cs.n_cta_c * 2); break;
+            case 3: ESC_CO_LAUNCH(256, 2048, 3, cs.n_cta_c * 3); break;
+            default: ESC_CO_LAUNCH(256, 4096, 2, cs.n_cta_c * 2); break;
         }
+#undef ESC_CO_LAUNCH
     } else {
         switch (shape) {
             case 0: k_center<512, 8192, 1><<<cs.n_cta_c, 512, sizeof(SmemC<512, 8192>), st>>>(A); break;

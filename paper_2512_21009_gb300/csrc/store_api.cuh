@@ -92,7 +92,7 @@ struct CountScratch {
     int64_t m1_pct = 100;            // visit N(g1) instead of N(h) when |N(g1)| * 100 < |N(h)| * m1_pct
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 3 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
-    bool orient = true;              // search closed pairs in (|g|, g) order (no temporal family, no restricted lists)
+    bool orient = true;              // search closed pairs in (|g|, g) order (not with restricted lists)
     // work split of one hypergraph across ranks: count_launch counts only
     // this rank's contiguous share (by neighbourhood size) of a side
     int split_rank = 0, split_world = 1;

@@ -206,7 +206,25 @@ def test_both_centre_kernels_without_temporal(E, monkeypatch, orient):
     run_stream(E, s, 3, 0)
 
 
-def test_unsorted_neighbourhood_without_table(E, monkeypatch):
+@pytest.mark.parametrize("orient,coarse", [("0", 1), ("1", 1), ("1", 2000)])
+def test_both_centre_kernels_with_temporal(E, monkeypatch, orient, coarse):
+    """All three families through both centre kernels.  The oriented one
+    classifies the open triads centred at h as it visits N'(h) and counts
+    those centred at g1 per h by their place in time; closed triads take
+    back what those counts gave them.  Timestamps divided by `coarse` make
+    many ties (ordered by ID), and the window cuts part of the triads."""
+    monkeypatch.setenv("ESC_COUNT_ORIENT", orient)
+    s = gen.random_small(31, 400, 600, 2, 30, n_batches=3, n_ins=60, n_del=60, membership="zipf", card="zipf")
+    if coarse > 1:
+        s.initial.timestamps[:] //= coarse
+        for b in s.batches:
+            b.inserts.timestamps[:] //= coarse
+    span = int(s.initial.timestamps[-1] - s.initial.timestamps[0])
+    run_stream(E, s, ALL, max(span // 5, 1))
+
+
+@pytest.mark.parametrize("families", [3, ALL])
+def test_unsorted_neighbourhood_without_table(E, monkeypatch, families):
     """A changed hyperedge with more than 4096 distinct neighbours (too many
     to sort) and, with ESC_COUNT_BIGNH raised, no hash table: the centre
     kernel visits its whole N(h), testing the (|g|, g) order per entry."""
@@ -219,19 +237,20 @@ def test_unsorted_neighbourhood_without_table(E, monkeypatch):
     mem = np.array([v for e in edges for v in e], np.int32)
     ts = np.arange(len(edges), dtype=np.int64)
     og = OracleHypergraph(nv, off, mem, ts)
-    g = E.Graph(nv, off, mem, ts, families=3, **caps_for(nv, 10000, 40000, 2000, 20000))
-    assert_counts_equal(g.counts(), O.counts(og, 3), "initial")
+    delta = 1500  # the initial timestamps run 0..4499: the window cuts part of the triads
+    g = E.Graph(nv, off, mem, ts, families=families, delta=delta, **caps_for(nv, 10000, 40000, 2000, 20000))
+    assert_counts_equal(g.counts(), O.counts(og, families, delta), "initial")
     big = sorted(rng.choice(nv, size=150, replace=False).tolist())
     # the initial hyperedges hold IDs 0..n-1 on both sides: delete five of them
     ids_o = og.apply_batch(np.array([0, 150]), np.array(big), np.array([9000]), np.arange(5))
     ids_g = g.apply_batch(np.array([0, 150]), np.array(big, np.int32), np.array([9000]), np.arange(5, dtype=np.int32))
     assert np.array_equal(ids_g, ids_o)
-    assert_counts_equal(g.counts(), O.counts(og, 3), "after insert")
+    assert_counts_equal(g.counts(), O.counts(og, families, delta), "after insert")
     ids_o2 = og.apply_batch(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64), ids_o)
     ids_g2 = g.apply_batch(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int64),
                            np.asarray(ids_g, np.int32))
     assert ids_o2.size == 0 and len(ids_g2) == 0
-    assert_counts_equal(g.counts(), O.counts(og, 3), "after delete")
+    assert_counts_equal(g.counts(), O.counts(og, families, delta), "after delete")
 
 
 @pytest.mark.parametrize("families", [1, 2, 4, 3, 5, 6])
