@@ -471,13 +471,17 @@ def run_large_zipf(args):
     clocks.start()
     l0 = g.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat, pair_ms = [], []
+    lat, pair_ms, stage = [], [], {"ingest": 0.0, "pairs": 0.0, "store": 0.0, "count_ins": 0.0}
     e0.record(st)
     for k in range(args.warmup, args.warmup + args.steps):
         ts0 = time.perf_counter()
         step(dev_batches[k])
         lat.append((time.perf_counter() - ts0) * 1e3)
-        pair_ms.append(g.stats()["ms_count_del"])
+        sts = g.stats()
+        pair_ms.append(sts["ms_count_del"])
+        for name, key in (("ingest", "ms_ingest"), ("pairs", "ms_count_del"), ("store", "ms_store"),
+                          ("count_ins", "ms_count_ins")):
+            stage[name] += sts[key] / args.steps
     e1.record(st)
     torch.cuda.synchronize(dev)
     launches = g.launch_count() - l0
@@ -522,11 +526,14 @@ def run_large_zipf(args):
                    "vertex_pairs_capacity": pairs_all, "create_s": round(t_create, 2)},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "pair_updates_per_step": ops / args.steps,
+        "stage_ms_per_step": stage,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": kind, "kernel": "k_pairs (vertex-pair statistics)",
+                     "traffic": None, "peak_kind": kind,
+                     "kernel": "k_pairs (vertex-pair statistics; timed with its prefix-scan kernels)",
                      "bytes": "24 B per (changed hyperedge, member pair): the pair's key and its packed word "
                               "read and written",
-                     "ms_per_step": pair_s * 1e3 / args.steps},
+                     "ms_per_step": pair_s * 1e3 / args.steps,
+                     "pair_ops_per_s": ops / pair_s if pair_s > 0 else 0.0},
         "e2e": {"value": upd_e2e / te, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps, "steps": args.steps},
         "gpu_launches": int(launches), "clocks": clk,

@@ -260,6 +260,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     ESC_CU(E->alloc(&S.v_newoff, V), "alloc");
     ESC_CU(E->alloc(&S.v_newcap, V), "alloc");
     ESC_CU(E->alloc(&S.realloc_v, V), "alloc");
+    ESC_CU(E->alloc(&S.vbig, V), "alloc");
     // slab arenas: power-of-two classes at most double a list, plus the
     // smallest slab per hyperedge / vertex; v2h gets extra room because a
     // vertex that outgrows its slab leaves the old one on a free stack
@@ -355,7 +356,7 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     }
     if (dry) {
         E->dry_bytes += int64_t(count_scratch_bytes(sh));
-        if (shared.families & kFamV12) E->dry_bytes += int64_t(pair_table_bytes(pair_cap));
+        if (shared.families & kFamV12) E->dry_bytes += int64_t(pair_table_bytes(pair_cap, E->max_ins));
         return ESC_OK;
     }
     void* csmem = nullptr;
@@ -389,9 +390,9 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     }
     if (shared.families & kFamV12) {
         void* pm = nullptr;
-        ESC_CU(cudaMalloc(&pm, pair_table_bytes(pair_cap)), "alloc pair table");
+        ESC_CU(cudaMalloc(&pm, pair_table_bytes(pair_cap, E->max_ins)), "alloc pair table");
         E->allocs.push_back(pm);
-        ESC_CU(pair_table_init(&E->pairs, pm, pair_cap, st), "pair table init");
+        ESC_CU(pair_table_init(&E->pairs, pm, pair_cap, E->max_ins, st), "pair table init");
     }
     ESC_CU(upload_tables(st), "tables");
     for (auto& e : E->ev) ESC_CU(cudaEventCreate(&e), "event");
@@ -549,10 +550,9 @@ static cudaError_t launch_sequence(Engine* E, const Call& C, bool fixed, cudaStr
     }
     if (pairs) {
         // vertex-pair statistics: the deleted hyperedges leave (their members
-        // are still in the store), then the inserted ones arrive
+        // are still in the store) and the inserted ones arrive, in one pass
         Range r("escher: vertex pairs");
-        if ((e = pairs_update(S, C, E->pairs, 0, E->sm_count, st, lc))) return e;
-        if ((e = pairs_update(S, C, E->pairs, 1, E->sm_count, st, lc))) return e;
+        if ((e = pairs_update(S, C, E->pairs, E->sm_count, st, lc))) return e;
     }
     if (prof) cudaEventRecord(E->ev[2], st);
     {

@@ -2232,6 +2232,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     // triple fits the window; a warp per h counts its f by
                     // (position, bucket).  Those f that meet h (closed triples)
                     // are taken back when their closed pair is classified.
+                    if (tid == 0) acc.w[5] += (unsigned long long)nh * n1;
                     for (int l = wid; l < nh; l += NW_C) {
                         const int32_t h = s.hh[l];
                         const int xh1 = s.hx[l], xstar = k1 - xh1;

@@ -68,6 +68,7 @@ struct Scalars {
     int32_t n_touched;    // touched vertices
     int32_t n_big;        // inserted hyperedges sorted by the block sorter
     int32_t n_realloc;    // vertices whose v2h slab moves
+    int32_t n_vbig;       // touched vertices whose v2h list is rewritten by a whole block
     int32_t max_u;        // largest neighbour-entry count of a changed hyperedge
     int32_t need_h[kNumClasses];
     int32_t freed_h[kNumClasses];
@@ -117,6 +118,7 @@ struct Store {
     int64_t* v_newoff;
     int32_t* v_newcap;
     int32_t* realloc_v;     // vertices whose slab moves this call
+    int32_t* vbig;          // touched vertices of degree >= kVBig this call (their v2h lists are long)
     SlabPool hp, vp;
 };
 

@@ -504,7 +504,27 @@ __global__ void k_valloc(Store S, Call C) {
 
 // Rewrite the v2h list of every touched vertex: drop the deleted IDs (kept
 // order, compacted by warp ballot, in place when the slab still fits) and
-// leave room for the appended IDs.
+// leave room for the appended IDs.  A vertex of degree >= kVBig (a hub under
+// skewed popularity, in a large share of all hyperedges) is left to
+// k_vfilter_big: one warp walking its list 32 entries at a time would take
+// tens of thousands of dependent steps.
+constexpr int kVBig = 2048;
+
+// The new v2h metadata of v once `kept` entries remain at dst.
+__device__ __forceinline__ void vfilter_finish(const Store& S, const Call& C, int32_t v, int kept, int deg, int nd,
+                                               int newdeg, bool moved, int64_t off, int64_t dst, int cap) {
+    if (kept != deg - nd) set_error(C.sc, kErrCuda, -5, v, kept);
+    S.v_base[v] = kept;
+    S.v_deg[v] = newdeg;
+    if (moved) {
+        S.v_off[v] = dst;
+        int newcap = S.v_newcap[v];
+        S.v_newoff[v] = off;       // old slab, freed by k_vfree
+        S.v_newcap[v] = cap;
+        S.v_cap[v] = newcap;
+    }
+}
+
 __global__ void k_vfilter(Store S, Call C) {
     if (C.sc->gate) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) pool_clamp(S.vp);
@@ -515,6 +535,10 @@ __global__ void k_vfilter(Store S, Call C) {
     for (int64_t t = wid; t < nt; t += nw) {
         int32_t v = C.touched[t];
         int nd = S.v_ndel[v], ni = S.v_nins[v], deg = S.v_deg[v], cap = S.v_cap[v];
+        if (deg >= kVBig) {
+            if (lane == 0) S.vbig[atomicAdd(&C.sc->n_vbig, 1)] = v;
+            continue;
+        }
         int64_t off = S.v_off[v];
         int newdeg = deg - nd + ni;
         bool moved = newdeg > cap;
@@ -531,18 +555,81 @@ __global__ void k_vfilter(Store S, Call C) {
                 kept += __popc(bal);
             }
         }
-        if (lane == 0) {
-            if (kept != deg - nd) set_error(C.sc, kErrCuda, -5, v, kept);
-            S.v_base[v] = kept;
-            S.v_deg[v] = newdeg;
-            if (moved) {
-                S.v_off[v] = dst;
-                int newcap = S.v_newcap[v];
-                S.v_newoff[v] = off;       // old slab, freed by k_vfree
-                S.v_newcap[v] = cap;
-                S.v_cap[v] = newcap;
+        if (lane == 0) vfilter_finish(S, C, v, kept, deg, nd, newdeg, moved, off, dst, cap);
+    }
+}
+
+// The same for the vertices of degree >= kVBig, a block per vertex: the list
+// is compacted in chunks of kVChunk entries (kVPer consecutive ones per
+// thread), in order, by a block scan of the kept counts.  In place this is
+// safe: every thread has loaded its entries of a chunk before the scan's
+// barrier, and the chunk's writes land below the chunk's end.
+constexpr int kVNT = 512, kVPer = 8, kVChunk = kVNT * kVPer;
+
+__global__ void __launch_bounds__(kVNT) k_vfilter_big(Store S, Call C) {
+    __shared__ int wsum[kVNT / 32];
+    __shared__ int total_s;
+    if (C.sc->gate) return;
+    const int nb = C.sc->n_vbig;
+    const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        const int32_t v = S.vbig[b];
+        const int nd = S.v_ndel[v], ni = S.v_nins[v], deg = S.v_deg[v], cap = S.v_cap[v];
+        const int64_t off = S.v_off[v];
+        const int newdeg = deg - nd + ni;
+        const bool moved = newdeg > cap;
+        const int64_t dst = moved ? S.v_newoff[v] : off;
+        int kept = deg;
+        if (nd > 0 || moved) {
+            kept = 0;
+            for (int base = 0; base < deg; base += kVChunk) {
+                int32_t val[kVPer];
+                unsigned keep = 0;
+                int cnt = 0;
+#pragma unroll
+                for (int i = 0; i < kVPer; ++i) {
+                    const int e = base + tid * kVPer + i;
+                    val[i] = e < deg ? S.vp.arena[off + e] : 0;
+                }
+#pragma unroll
+                for (int i = 0; i < kVPer; ++i) {
+                    const int e = base + tid * kVPer + i;
+                    if (e < deg && !bit_test(S.delb, val[i])) {
+                        keep |= 1u << i;
+                        ++cnt;
+                    }
+                }
+                // block exclusive scan of the kept counts
+                int inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int x = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += x;
+                }
+                if (lane == 31) wsum[w] = inc;
+                __syncthreads();
+                if (w == 0) {
+                    int x = lane < kVNT / 32 ? wsum[lane] : 0;
+                    const int own = x;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (lane < kVNT / 32) wsum[lane] = x - own;
+                    if (lane == 31) total_s = x;
+                }
+                __syncthreads();
+                int pos = kept + wsum[w] + inc - cnt;
+#pragma unroll
+                for (int i = 0; i < kVPer; ++i)
+                    if (keep & (1u << i)) S.vp.arena[dst + pos++] = val[i];
+                kept += total_s;
+                __syncthreads();  // wsum and total_s are rewritten by the next chunk
             }
         }
+        if (tid == 0) vfilter_finish(S, C, v, kept, deg, nd, newdeg, moved, off, dst, cap);
+        __syncthreads();
     }
 }
 
@@ -690,6 +777,7 @@ cudaError_t store_insert(const Store& S, const Call& C, int sm_count, cudaStream
     }
     ESC_LAUNCH(lc, k_valloc<<<sm_count, kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_vfilter<<<sm_count * 8, kBlk, 0, st>>>(S, C));
+    ESC_LAUNCH(lc, k_vfilter_big<<<sm_count * 2, kVNT, 0, st>>>(S, C));
     if (any_i) ESC_LAUNCH(lc, k_ins_write<<<g_warp(gi, sm_count), kBlk, 0, st>>>(S, C));
     ESC_LAUNCH(lc, k_vfree<<<sm_count, kBlk, 0, st>>>(S, C));
     return cudaSuccess;

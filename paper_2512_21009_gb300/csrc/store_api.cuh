@@ -116,13 +116,16 @@ struct CountShape {
 };
 
 // pairs.cu: vertex-pair statistics for incident-vertex types 1 and 2
-constexpr unsigned long long kPairEmpty = ~0ull;
+constexpr unsigned long long kPairEmpty = 0;  // no pair key is 0 (u < v)
 struct PairTable {
-    unsigned long long* keys = nullptr;  // [mask+1] u << 32 | v (u < v), kPairEmpty when unused
-    unsigned long long* vals = nullptr;  // [mask+1] m << 40 | S (hyperedges holding the pair, their sizes)
+    unsigned long long* kv = nullptr;    // [2 (mask+1)] per slot: key u << 32 | v (u < v; 0 when unused)
+                                         // and word m << 40 | S (hyperedges holding the pair, their sizes)
     unsigned long long* used = nullptr;  // device: keys taken
+    int64_t* poff = nullptr;             // [n_cap+1] per call: first member pair of each changed hyperedge
+    int64_t* tsum = nullptr;             // scan tiles of poff
     uint64_t mask = 0;
     unsigned long long limit = 0;        // keys allowed (the configured capacity)
+    int64_t n_cap = 0;                   // changed hyperedges per call
 };
 // slots for `pairs` keys at a load of at most 0.8
 inline uint64_t pair_table_slots(int64_t pairs) {
@@ -130,12 +133,13 @@ inline uint64_t pair_table_slots(int64_t pairs) {
     while (s < uint64_t(pairs) + uint64_t(pairs) / 4) s <<= 1;
     return s;
 }
-size_t pair_table_bytes(int64_t pairs);
-cudaError_t pair_table_init(PairTable* P, void* mem, int64_t pairs, cudaStream_t st);
+size_t pair_table_bytes(int64_t pairs, int64_t n_cap);
+cudaError_t pair_table_init(PairTable* P, void* mem, int64_t pairs, int64_t n_cap, cudaStream_t st);
 // admission: the batch's inserted pairs must fit the table (status OUT_OF_MEMORY otherwise)
 cudaError_t pairs_check(const PairTable& P, const Call& C, cudaStream_t st, LaunchCounter& lc);
-// one side of a batch into the pair statistics and the type 1 / type 2 deltas
-cudaError_t pairs_update(const Store& S, const Call& C, const PairTable& P, int side, int sm_count, cudaStream_t st,
+// both sides of a batch into the pair statistics and the type 1 / type 2
+// terms of each side (run before the store deletes)
+cudaError_t pairs_update(const Store& S, const Call& C, const PairTable& P, int sm_count, cudaStream_t st,
                          LaunchCounter& lc);
 
 // Largest neighbour-entry count sum(deg) of a changed hyperedge the counter

@@ -167,3 +167,52 @@ def test_vertex12_has_no_neighbourhood_limit(E, monkeypatch):
     with pytest.raises(E.EscError) as ei:
         E.Graph(nv, off, mem, None, families=2, **caps)
     assert ei.value.status == 4
+
+
+def _csr(edges):
+    off = np.zeros(len(edges) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    mem = np.array([v for e in edges for v in e], np.int32)
+    return off, mem
+
+
+def test_vertex12_singletons_and_one_large_hyperedge(E):
+    """Runs of more than 32 single-member hyperedges (no member pairs, some
+    written as a repeated member) among ordinary ones, and one hyperedge of
+    800 members whose 319,600 member pairs are spread over the whole grid;
+    the next batch deletes it with part of the singletons while inserting
+    more of them."""
+    rng = np.random.default_rng(73)
+    nv = 3000
+    init = gen.random_small(73, nv, 500, 2, 20, membership="zipf").initial
+    og = OracleHypergraph(nv, init.offsets, init.members, init.timestamps)
+    caps = caps_for(nv, 4096, 40000, 4096, 40000)
+    g = E.Graph(nv, init.offsets, init.members, init.timestamps, families=V12,
+                capacity_vertex_pairs=int(np.sum(np.diff(init.offsets) ** 2)) + 800000, **caps)
+    _check(g, og, V12, 0, "initial")
+
+    def ordinary(n):
+        return [sorted(rng.choice(nv, size=int(rng.integers(2, 30)), replace=False).tolist()) for _ in range(n)]
+
+    def singles(n):
+        return [[int(v)] * int(rng.integers(1, 3)) for v in rng.integers(0, nv, size=n)]
+
+    large = sorted(rng.choice(nv, size=800, replace=False).tolist())
+    edges = ordinary(5) + singles(70) + [large] + singles(70) + ordinary(5)
+    off, mem = _csr(edges)
+    ts = np.arange(len(edges), dtype=np.int64) + 10_000
+    ids_o = og.apply_batch(off, mem, ts, np.zeros(0, np.int64))
+    ids_g = g.apply_batch(off, mem, ts, np.zeros(0, np.int32))
+    assert np.array_equal(ids_g, ids_o)
+    _check(g, og, V12, 0, "after the large insert")
+
+    # delete the large hyperedge, 50 singletons and three ordinary ones
+    dels = np.array([ids_o[75]] + list(ids_o[5:55]) + list(ids_o[-3:]), np.int64)
+    edges2 = singles(40) + ordinary(2)
+    off2, mem2 = _csr(edges2)
+    ts2 = np.arange(len(edges2), dtype=np.int64) + 20_000
+    ids_o2 = og.apply_batch(off2, mem2, ts2, dels)
+    ids_g2 = g.apply_batch(off2, mem2, ts2, dels.astype(np.int32))
+    assert np.array_equal(ids_g2, ids_o2)
+    _check(g, og, V12, 0, "after the delete")
+    g.close()
