@@ -78,6 +78,10 @@
  *   ESC_COUNT_M1PCT=p         weight (percent) of a visit of N(g1) against a
  *                             visit of N(h) in the per-pair choice of which
  *                             side to scan.
+ *   ESC_COUNT_OPEN_MAX=n      temporal family: longest N'(h) (0..8192) whose
+ *                             open triads centred at h are counted from its
+ *                             time order; longer ones have every pair
+ *                             classified by the centre kernel.
  *   ESC_CENTER_SMALL=s        centre-kernel launch shape, as
  *                             esc_tune_result.center_shape (0..3).
  *   ESC_CALL_GRAPH=1          graph launch on from creation (as

@@ -384,6 +384,10 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
         if (v >= 1) E->cs.r_min = v;
     }
     if (const char* env = getenv("ESC_COUNT_ORIENT")) E->cs.orient = atoi(env) != 0;
+    if (const char* env = getenv("ESC_COUNT_OPEN_MAX")) {
+        long long v = atoll(env);
+        if (v >= 0 && v <= 8192) E->cs.oh_max = int(v);
+    }
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
         long long v = atoll(env);
         if (v >= 64 && (v & (v - 1)) == 0) E->cs.smem_slots = v;

@@ -546,8 +546,10 @@ __global__ void __launch_bounds__(NT_NH) k_nh_build(CountArgs A) {
     for (int i = tid; i < 128; i += NT_NH) s.acc[i] = 0;
     for (int i = tid; i < 2 * (kHistSmem + 1); i += NT_NH) s.hx[i / (kHistSmem + 1)][i % (kHistSmem + 1)] = 0;
     if (tid == 0) s.n_list = 0;
-    // open-at-h triads are counted in aggregate unless the temporal family is kept
-    const bool agg = (fam & kFamH) && !(fam & kFamT);
+    // open-at-h triads are counted in aggregate (static classes); with the
+    // temporal family only for the oriented centre kernel (k_open_h counts
+    // their temporal classes), the earlier one classifies each of them
+    const bool agg = (fam & kFamH) && (!(fam & kFamT) || A.orient);
     // without the temporal family k_center may meet N(g1) and a large N(h)
     // through restricted lists
     const bool use_r = !(fam & kFamT) && cs.r_cap > 0;
@@ -1586,6 +1588,295 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center(CountArgs A) {
     flush_stats<NT_C>(A, acc, s.red);
 }
 
+// a + b and a - b for b >= 0, held within the int64 range
+__device__ __forceinline__ int64_t sat_add(int64_t a, int64_t b) { return a > INT64_MAX - b ? INT64_MAX : a + b; }
+__device__ __forceinline__ int64_t sat_sub(int64_t a, int64_t b) { return a < INT64_MIN + b ? INT64_MIN : a - b; }
+
+// ---------------------------------------------------------------------------
+// 3a. open triads centred at h, temporal classes (oriented counter)
+// ---------------------------------------------------------------------------
+//
+// Every unordered pair {a, b} of N'(h) (N(h) without the changed g < h) is
+// an open triad {h, a, b} centred at h unless a meets b; the centre kernel
+// finds the closed ones and takes back the class counted here.  With the
+// labels h, a (earlier in (t, ID) order), b (later), the class depends on
+// the mask bits [|h| != x_a + x_b], C_a = [a not inside h], C_b, and on
+// where h falls in time.  With N'(h) sorted by (t, ID) and h's place s:
+//   h last:   a, b both before h, within [t_h - delta, t_h]: one range;
+//   h first:  a, b both after h, within [t_h, t_h + delta]: one range;
+//   h middle: a before h, b after h with t_b - t_a <= delta: a range of b per a.
+// Pairs inside a range are counted per later member from prefix counts of C;
+// those with x_a + x_b = |h| from a second order by (x, place): the members
+// with x = |h| - x_b and places in [L, b) are one stretch of it.  Work per h
+// is O(n log n) (two bitonic sorts) instead of one visit per pair.  A list
+// longer than kOhMax (or the lower cs.oh_max) is left to the centre kernel,
+// which then classifies every pair of it (flag bit 1 of nh_flag).
+constexpr int kOhNT = 1024;
+constexpr int kOhMax = 8192;  // entries of N'(h) sorted in shared memory, at most
+
+struct SmemOH {
+    Tables tb;
+    int64_t t[kOhMax];         // timestamp of each entry (sorted with id and pay)
+    int32_t id[kOhMax];
+    int32_t pay[kOhMax];       // x | C << 15
+    int32_t key[kOhMax];       // x << 14 | place << 1 | C, sorted
+    uint16_t p1[kOhMax + 1];   // entries with C = 1 among the first i, in (t, ID) order
+    uint16_t pc[kOhMax + 1];   // the same in key order
+    unsigned long long cnt[24];
+    int wsum[kOhNT / 32];
+    long long item;
+    int n, s_pos, l0, r1;
+};
+
+// out[i] = number of the first i of n entries with bit(i) set, and out[n]
+template <typename F>
+__device__ __forceinline__ void oh_prefix(F bit, uint16_t* out, int n, int* wsum) {
+    constexpr int PER = kOhMax / kOhNT;
+    const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
+    const int q0 = tid * PER;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+        if (q0 + k < n) c += bit(q0 + k);
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int x = wsum[lane];  // kOhNT / 32 == 32 warps
+        const int own = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += v;
+        }
+        wsum[lane] = x - own;
+        if (lane == 31) out[n] = uint16_t(x);
+    }
+    __syncthreads();
+    int run = wsum[w] + inc - c;
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+        if (q0 + k < n) {
+            out[q0 + k] = uint16_t(run);
+            run += bit(q0 + k);
+        }
+    __syncthreads();
+}
+
+// The counts of one later member (or, in the middle case, of one earlier
+// member against a range of later ones): CE is that member's C bit.
+// Counter index: case * 8 + E * 4 + C_a * 2 + C_b.
+template <int CE>
+__device__ __forceinline__ void oh_add(unsigned (&c)[24], int cas, bool later, int tot, int t1, int e, int e1) {
+    // tot members in the range, t1 of them with C = 1; e with x_a + x_b = |h|,
+    // e1 of those with C = 1
+    const int k = cas * 8;
+    if (later) {  // the range holds the earlier members a; b is this one
+        c[k + 4 + 2 + CE] += unsigned(e1);
+        c[k + 4 + 0 + CE] += unsigned(e - e1);
+        c[k + 0 + 2 + CE] += unsigned(t1 - e1);
+        c[k + 0 + 0 + CE] += unsigned((tot - t1) - (e - e1));
+    } else {      // this one is a; the range holds the later members b
+        c[k + 4 + CE * 2 + 1] += unsigned(e1);
+        c[k + 4 + CE * 2 + 0] += unsigned(e - e1);
+        c[k + 0 + CE * 2 + 1] += unsigned(t1 - e1);
+        c[k + 0 + CE * 2 + 0] += unsigned((tot - t1) - (e - e1));
+    }
+}
+
+__global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemOH& s = *reinterpret_cast<SmemOH*>(smem_raw);
+    const Store& S = A.S;
+    if (A.sc->gate) return;
+    const CountScratch& cs = A.cs;
+    const int tid = threadIdx.x, lane = lane_id();
+    const int64_t delta = S.delta;
+    const RunRange R = run_of(A);
+    load_tables(s.tb, kOhNT);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s.item = (long long)atomicAdd(&A.sc->qoh[A.side], 1ull);
+            s.n = 0;
+        }
+        if (tid < 24) s.cnt[tid] = 0;
+        __syncthreads();
+        if (s.item >= R.n) break;
+        const int64_t i = cs.order[s.item];
+        const int nn = cs.nh_n[i];
+        if (nn < 2) continue;
+        const int32_t h = A.changed[A.lo + i];
+        const int g = A.changed_g ? A.changed_g[A.lo + i] : 0;
+        const int kh = S.h_card[h];
+        const int64_t th = S.h_ts[h];
+        const int64_t base = cs.nh_off[i] - R.base;
+        for (int q = tid; q < nn; q += kOhNT) {
+            const int32_t gg = cs.nh_g[base + q];
+            const uint64_t xv = cs.nh_xv[base + q];
+            if (gg < h && ((xv >> 31) & 1u)) continue;  // changed below h: its triads belong to gg
+            const int p = atomicAdd(&s.n, 1);
+            if (p < kOhMax) {
+                const int x = int(xv & kXMask), kg = int((xv >> 16) & 0x7fffu);
+                s.t[p] = cs.nh_ts[base + q];
+                s.id[p] = gg;
+                s.pay[p] = x | (kg > x ? 1 << 15 : 0);
+            }
+        }
+        __syncthreads();
+        const int n = s.n;
+        if (n > cs.oh_max) {  // left to the centre kernel
+            if (tid == 0) cs.nh_flag[i] |= 2;
+            continue;
+        }
+        if (n < 2) continue;
+        int n2 = 2;
+        while (n2 < n) n2 <<= 1;
+        for (int q = n + tid; q < n2; q += kOhNT) {
+            s.t[q] = INT64_MAX;
+            s.id[q] = INT_MAX;
+            s.pay[q] = 0;
+        }
+        __syncthreads();
+        // bitonic sort by (t, ID)
+        for (int k = 2; k <= n2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int u = tid; u < (n2 >> 1); u += kOhNT) {
+                    const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
+                    const int64_t ta = s.t[a], tb = s.t[b];
+                    const int32_t ia = s.id[a], ib = s.id[b];
+                    if ((ta > tb || (ta == tb && ia > ib)) == ((a & k) == 0)) {
+                        s.t[a] = tb;
+                        s.t[b] = ta;
+                        s.id[a] = ib;
+                        s.id[b] = ia;
+                        const int32_t pa = s.pay[a];
+                        s.pay[a] = s.pay[b];
+                        s.pay[b] = pa;
+                    }
+                }
+                __syncthreads();
+            }
+        for (int q = tid; q < n2; q += kOhNT)
+            s.key[q] = q < n ? ((s.pay[q] & 0x7fff) << 14) | (q << 1) | ((s.pay[q] >> 15) & 1) : INT_MAX;
+        oh_prefix([&](int q) { return (s.pay[q] >> 15) & 1; }, s.p1, n, s.wsum);
+        // bitonic sort of the keys
+        for (int k = 2; k <= n2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int u = tid; u < (n2 >> 1); u += kOhNT) {
+                    const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
+                    const int32_t ka = s.key[a], kb = s.key[b];
+                    if ((ka > kb) == ((a & k) == 0)) {
+                        s.key[a] = kb;
+                        s.key[b] = ka;
+                    }
+                }
+                __syncthreads();
+            }
+        oh_prefix([&](int q) { return s.key[q] & 1; }, s.pc, n, s.wsum);
+        if (tid == 0) {
+            // h's place, the first member within delta before it, the end of
+            // the members within delta after it
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s.t[mid] < th || (s.t[mid] == th && s.id[mid] < h)) lo = mid + 1;
+                else hi = mid;
+            }
+            const int sp = lo;
+            lo = 0;
+            hi = sp;
+            const int64_t tlo = sat_sub(th, delta), thi = sat_add(th, delta);
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s.t[mid] < tlo) lo = mid + 1;
+                else hi = mid;
+            }
+            s.l0 = lo;
+            lo = sp;
+            hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s.t[mid] <= thi) lo = mid + 1;
+                else hi = mid;
+            }
+            s.r1 = lo;
+            s.s_pos = sp;
+        }
+        __syncthreads();
+        const int sp = s.s_pos, l0 = s.l0, r1 = s.r1;
+        auto key_lb = [&](int32_t v) {
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s.key[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            return lo;
+        };
+        unsigned c[24];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) c[k] = 0;
+        for (int e = tid; e < n; e += kOhNT) {
+            const int xe = s.pay[e] & 0x7fff;
+            const int ce = (s.pay[e] >> 15) & 1;
+            const int xs = kh - xe;  // the x of a partner that completes h
+            // members in places [L, R) with x = xs: how many, and with C = 1
+            auto match = [&](int L, int Rr, int& m, int& m1) {
+                m = m1 = 0;
+                if (xs < 1 || L >= Rr) return;
+                // places are < kOhMax = 1 << 13, so (xs << 14) + (kOhMax << 1)
+                // is the first key of x = xs + 1
+                const int i0 = key_lb((xs << 14) + (L << 1)), i1 = key_lb((xs << 14) + (Rr << 1));
+                m = i1 - i0;
+                m1 = int(s.pc[i1]) - int(s.pc[i0]);
+            };
+            auto range = [&](int cas, bool later, int L, int Rr) {
+                if (L >= Rr) return;
+                int m, m1;
+                match(L, Rr, m, m1);
+                const int tot = Rr - L, t1 = int(s.p1[Rr]) - int(s.p1[L]);
+                if (ce) oh_add<1>(c, cas, later, tot, t1, m, m1);
+                else oh_add<0>(c, cas, later, tot, t1, m, m1);
+            };
+            if (e >= l0 && e < sp) range(0, true, l0, e);   // h last: a in [l0, e)
+            if (e >= sp && e < r1) range(1, true, sp, e);   // h first: a in [sp, e)
+            if (e < sp) {                                   // h middle: b after h within delta of e
+                const int64_t tb = sat_add(s.t[e], delta);
+                int lo = sp, hi = n;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s.t[mid] <= tb) lo = mid + 1;
+                    else hi = mid;
+                }
+                range(2, false, sp, lo);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            unsigned v = c[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v) atomicAdd(&s.cnt[k], (unsigned long long)v);
+        }
+        __syncthreads();
+        if (tid < 24 && s.cnt[tid]) {
+            const int cas = tid >> 3, E = (tid >> 2) & 1, ca = (tid >> 1) & 1, cb = tid & 1;
+            // labels 0 = h, 1 = a, 2 = b; order: h last (a, b, h), first (h, a, b), middle (a, h, b)
+            const int m = (E ? 0 : 1) | (ca ? 2 : 0) | (cb ? 4 : 0) | (1 << 3) | (1 << 5);
+            const int pi = cas == 0 ? perm_index(1, 2) : cas == 1 ? perm_index(0, 1) : perm_index(1, 0);
+            const int cl = s.tb.cls96[s.tb.perm[pi][m]];
+            if (cl >= 0)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(g) * kCStride + kOffT + cl]), s.cnt[tid]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 3b. oriented centre kernel (all neighbourhood families)
 // ---------------------------------------------------------------------------
@@ -1669,6 +1960,15 @@ struct SmemCO {
             uint32_t tn[kNT];        //   temporal classes taken back for closed triads
             unsigned long long tacc[kNT];
             int64_t hts[LCH];        //   timestamps of the chunk's h
+            // the sweep over N(g1): the chunk's h in (t, ID) order and in
+            // (|h & g1|, t, ID) order, the place of each h in both, and the
+            // range counts by (time position r, C) of each order (r = 3:
+            // every h, for the static classes)
+            int64_t ot_t[LCH], ox_t[LCH];
+            int32_t ot_i[LCH], ox_i[LCH], ox_x[LCH];
+            int32_t pt[LCH], px[LCH];
+            int32_t dT[8][LCH + 1], dX[8][LCH + 1];
+            int n_before;            //   the chunk's h before g1 in (t, ID) order
         } t;
     } u2;
     int64_t seg_off[NT_C];
@@ -1698,6 +1998,8 @@ struct SmemCO {
 };
 
 static_assert(sizeof(SmemCO<256, 2048>) + 1024 <= 233472 / 3, "three 256-thread oriented centre blocks per SM");
+
+constexpr int kSweepMin = 4;  // chunks with fewer h count the open triads at g1 per h
 
 __device__ __forceinline__ unsigned long long order_key(int k, int32_t g) {
     return (uint64_t(uint32_t(k)) << 32) | uint64_t(uint32_t(g));
@@ -1843,12 +2145,16 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
         long long* cl;
         int64_t* lts;
         int P = 1;
+        // with the temporal family the plus list lives in the block's global
+        // scratch (its shared-memory place holds the timestamps of N(g1))
+        bool plus_ok = true;
         const uint32_t t1_cap = pow2_at_least(2 * u1);
         if (t1_cap <= min(A.c_smem_cap, uint32_t(T1_S))) {
             T1 = Tab{s.keys, s.vals, nullptr, s.list, &s.n_list, t1_cap - 1, T1_S / 2};
             lk = s.lk;
-            pf = s.u1.p.pf;
-            pm = s.u1.p.pm;
+            pf = TEMP ? g_pf : s.u1.p.pf;
+            pm = TEMP ? g_pm : s.u1.p.pm;
+            plus_ok = !TEMP || gs / 2 >= int64_t(T1.list_cap);
             cl = s.u2.cl;
             lts = s.u1.lts;
         } else {
@@ -1927,7 +2233,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     const uint32_t bb = bloom_bit(f, bw);
                     atomicOr(&s.bloom[bb >> 5], 1u << (bb & 31));
                     if (TEMP) lts[q] = S.h_ts[f];
-                    if (!TEMP && order_key(kf, f) > key1) {
+                    if (plus_ok && order_key(kf, f) > key1) {
                         const int c = atomicAdd(&s.n_plus, 1);
                         pf[c] = f;
                         pm[c] = uint32_t(x) | (uint32_t(kf) << 16) | (changed_f ? 0x80000000u : 0u);
@@ -1987,25 +2293,30 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         s.hpos[l] = hpos;
                         s.hIn[l] = 0;
                         if (TEMP) s.u2.t.hts[l] = S.h_ts[h];
+                        // with the temporal family an N'(h) too long for
+                        // k_open_h (flag bit 1) has every pair above g1
+                        // visited here, the open ones classified (bit 4 of
+                        // the mode)
+                        const bool en = TEMP && (cs.nh_flag[li] & 2) != 0;
+                        const bool m1ok = plus_ok && !en;
                         int mode;
                         if (hpos >= 0) {
                             const int sfx = hnn - hpos - 1;
-                            // with the temporal family every pair above g1 is visited
-                            if (!TEMP && htcap > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
+                            if (m1ok && htcap > 0 && int64_t(n_plus) * 100 < int64_t(sfx) * cs.m1_pct) {
                                 mode = 1;
                                 work = n_plus;
                             } else {
                                 mode = 0;
                                 work = sfx;
                             }
-                        } else if (!TEMP && htcap > 0) {
+                        } else if (m1ok && htcap > 0) {
                             mode = 1;
                             work = n_plus;
                         } else {
                             mode = 3;
                             work = hnn;
                         }
-                        s.hmode[l] = mode;
+                        s.hmode[l] = mode | (en ? 16 : 0);
                     }
                     int inc = work;
 #pragma unroll
@@ -2090,10 +2401,8 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         const int cc = s.tb.cls30[mk];
                         const int c1 = s.tb.cls30[m1], c2 = s.tb.cls30[m2];
                         if (cc >= 0) atomicAdd(&hist[cc], 1u);
-                        if (!TEMP) {
-                            const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
-                            if (ch >= 0) atomicAdd(&hneg[ch], 1u);
-                        }
+                        const int ch = s.tb.cls30[open_at_h_mask(kh, xh1, xh2, k1, k2)];
+                        if (ch >= 0) atomicAdd(&hneg[ch], 1u);
                         if (c1 >= 0) atomicAdd(&hneg[c1], 1u);
                         if (c2 >= 0) atomicAdd(&hneg[c2], 1u);
                     }
@@ -2106,6 +2415,11 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         if (cc >= 0) atomicAdd(&s.u2.t.th[wid][cc], 1u);
                         if (p1 >= 0) atomicAdd(&s.u2.t.tn[p1], 1u);
                         if (p2 >= 0) atomicAdd(&s.u2.t.tn[p2], 1u);
+                        if (!(s.hmode[l] & 16)) {  // the open class k_open_h gave it at h
+                            const int p0 = temporal_class(s.tb, open_at_h_mask(kh, xh1, xh2, k1, k2), th, ts1, t2, h,
+                                                          g1, g2, delta);
+                            if (p0 >= 0) atomicAdd(&s.u2.t.tn[p0], 1u);
+                        }
                     }
                     if (fam & kFamV)
                         acc.v3 += (unsigned long long)xh1 * x12 * xh2 - (unsigned long long)t * (xh1 + x12 + xh2) +
@@ -2127,7 +2441,7 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     unsigned long long e0 = 0, e1 = 0;
                     do {
                     if (idx >= wtot) break;
-                    const int mode = s.hmode[l];
+                    const int mode = s.hmode[l] & 15;
                     int32_t g2;
                     int x12, xh2, k2;
                     int32_t vf2;
@@ -2148,9 +2462,10 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         chg2 = (m >> 31) != 0;
                         xh2 = int(uint32_t(xv2) & kXMask);
                         vf2 = int32_t(uint32_t(xv2 >> 32));
-                    } else if constexpr (TEMP) {
+                    } else if (TEMP && (s.hmode[l] & 16)) {
                         // every g2 of N'(h) above g1: closed pairs queued, open
-                        // ones (centred at h) classified here
+                        // ones (centred at h) get their temporal class here (the
+                        // static one is counted in aggregate by k_nh_build)
                         const int64_t at = s.hnb[l] + (mode == 0 ? s.hpos[l] + 1 + q : q);
                         g2 = cs.nh_g[at];
                         const uint64_t xv2 = cs.nh_xv[at];
@@ -2167,10 +2482,6 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         if (sl < 0) {
                             const int m = open_at_h_mask(s.hk[l], s.hx[l], xh2, k1, k2);
                             ++acc.n_tri;
-                            if (want_h) {
-                                const int c = s.tb.cls30[m];
-                                if (c >= 0) atomicAdd(&hist[c], 1u);
-                            }
                             const int c96 = temporal_class(s.tb, m, s.u2.t.hts[l], ts1, cs.nh_ts[at], h, g1, g2, delta);
                             if (c96 >= 0) atomicAdd(&s.u2.t.th[wid][c96], 1u);
                             break;
@@ -2232,61 +2543,263 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                     // triple fits the window; a warp per h counts its f by
                     // (position, bucket).  Those f that meet h (closed triples)
                     // are taken back when their closed pair is classified.
-                    if (tid == 0) acc.w[5] += (unsigned long long)nh * n1;
-                    for (int l = wid; l < nh; l += NW_C) {
-                        const int32_t h = s.hh[l];
-                        const int xh1 = s.hx[l], xstar = k1 - xh1;
-                        const int64_t th = s.u2.t.hts[l];
-                        const bool h_first = th < ts1 || (th == ts1 && h < g1);
-                        const int64_t tp = h_first ? th : ts1, tq = h_first ? ts1 : th;
-                        const int32_t ip = h_first ? h : g1, iq = h_first ? g1 : h;
-                        uint32_t cst[4] = {0, 0, 0, 0};
-                        uint32_t ctm[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-                        for (int q = lane; q < n1; q += 32) {
-                            const int sl = T1.list[q];
-                            const int32_t f = T1.keys[sl];
-                            if (f == h) continue;
-                            const int32_t meta = lk[q];
-                            if (meta < 0 && f < h) continue;
-                            const int x = int(T1.vals[sl]);
-                            const int b = (x != xstar ? 2 : 0) | ((meta & 0x7fffffff) > x ? 1 : 0);
-                            const int64_t tf = lts[q];
-                            int r;  // position in time, -1: outside the window
-                            if (tf < tp || (tf == tp && f < ip)) r = tq - tf <= delta ? 0 : -1;
-                            else if (tf < tq || (tf == tq && f < iq)) r = tq - tp <= delta ? 1 : -1;
-                            else r = tf - tp <= delta ? 2 : -1;
-                            // constant indices keep the counters in registers
-#pragma unroll
-                            for (int bb = 0; bb < 4; ++bb) {
-                                cst[bb] += b == bb ? 1u : 0u;
-#pragma unroll
-                                for (int rr = 0; rr < 3; ++rr) ctm[rr][bb] += (b == bb && r == rr) ? 1u : 0u;
-                            }
-                        }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                            for (int b = 0; b < 4; ++b) {
-                                cst[b] += __shfl_xor_sync(0xffffffffu, cst[b], o);
-#pragma unroll
-                                for (int r = 0; r < 3; ++r) ctm[r][b] += __shfl_xor_sync(0xffffffffu, ctm[r][b], o);
-                            }
-                        }
-                        if (lane == 0) {
-                            const int A_bit = s.hk[l] > xh1 ? 1 : 0;
-                            // labels 0 = h, 1 = g1, 2 = f; p and q are h and g1 in time order
-                            const int lp = h_first ? 0 : 1, lq = h_first ? 1 : 0;
-                            for (int b = 0; b < 4; ++b) {
-                                const int m = A_bit | ((b >> 1) << 1) | ((b & 1) << 2) | (1 << 3) | (1 << 4);
-                                acc.n_tri += cst[b];
-                                if (want_h && cst[b] && s.tb.cls30[m] >= 0) atomicAdd(&hist[s.tb.cls30[m]], cst[b]);
-                                for (int r = 0; r < 3; ++r) {
-                                    if (!ctm[r][b]) continue;
-                                    const int o0 = r == 0 ? 2 : lp, o1 = r == 0 ? lp : (r == 1 ? 2 : lq);
-                                    const int c = s.tb.cls96[s.tb.perm[perm_index(o0, o1)][m]];
-                                    if (c >= 0) atomicAdd(&s.u2.t.th[wid][c], ctm[r][b]);
+                    if (nh < kSweepMin) {
+                        if (tid == 0) acc.w[5] += (unsigned long long)nh * n1;
+                        for (int l = wid; l < nh; l += NW_C) {
+                            const int32_t h = s.hh[l];
+                            const int xh1 = s.hx[l], xstar = k1 - xh1;
+                            const int64_t th = s.u2.t.hts[l];
+                            const bool h_first = th < ts1 || (th == ts1 && h < g1);
+                            const int64_t tp = h_first ? th : ts1, tq = h_first ? ts1 : th;
+                            const int32_t ip = h_first ? h : g1, iq = h_first ? g1 : h;
+                            uint32_t cst[4] = {0, 0, 0, 0};
+                            uint32_t ctm[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+                            for (int q = lane; q < n1; q += 32) {
+                                const int sl = T1.list[q];
+                                const int32_t f = T1.keys[sl];
+                                if (f == h) continue;
+                                const int32_t meta = lk[q];
+                                if (meta < 0 && f < h) continue;
+                                const int x = int(T1.vals[sl]);
+                                const int b = (x != xstar ? 2 : 0) | ((meta & 0x7fffffff) > x ? 1 : 0);
+                                const int64_t tf = lts[q];
+                                int r;  // position in time, -1: outside the window
+                                if (tf < tp || (tf == tp && f < ip)) r = tq - tf <= delta ? 0 : -1;
+                                else if (tf < tq || (tf == tq && f < iq)) r = tq - tp <= delta ? 1 : -1;
+                                else r = tf - tp <= delta ? 2 : -1;
+                                // constant indices keep the counters in registers
+    #pragma unroll
+                                for (int bb = 0; bb < 4; ++bb) {
+                                    cst[bb] += b == bb ? 1u : 0u;
+    #pragma unroll
+                                    for (int rr = 0; rr < 3; ++rr) ctm[rr][bb] += (b == bb && r == rr) ? 1u : 0u;
                                 }
                             }
+    #pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+    #pragma unroll
+                                for (int b = 0; b < 4; ++b) {
+                                    cst[b] += __shfl_xor_sync(0xffffffffu, cst[b], o);
+    #pragma unroll
+                                    for (int r = 0; r < 3; ++r) ctm[r][b] += __shfl_xor_sync(0xffffffffu, ctm[r][b], o);
+                                }
+                            }
+                            if (lane == 0) {
+                                const int A_bit = s.hk[l] > xh1 ? 1 : 0;
+                                // labels 0 = h, 1 = g1, 2 = f; p and q are h and g1 in time order
+                                const int lp = h_first ? 0 : 1, lq = h_first ? 1 : 0;
+                                for (int b = 0; b < 4; ++b) {
+                                    const int m = A_bit | ((b >> 1) << 1) | ((b & 1) << 2) | (1 << 3) | (1 << 4);
+                                    acc.n_tri += cst[b];
+                                    if (want_h && cst[b] && s.tb.cls30[m] >= 0) atomicAdd(&hist[s.tb.cls30[m]], cst[b]);
+                                    for (int r = 0; r < 3; ++r) {
+                                        if (!ctm[r][b]) continue;
+                                        const int o0 = r == 0 ? 2 : lp, o1 = r == 0 ? lp : (r == 1 ? 2 : lq);
+                                        const int c = s.tb.cls96[s.tb.perm[perm_index(o0, o1)][m]];
+                                        if (c >= 0) atomicAdd(&s.u2.t.th[wid][c], ctm[r][b]);
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+                        // The chunk's h sorted by (t, ID) and by (|h & g1|, t,
+                        // ID); each f of N(g1) then adds one to a few
+                        // contiguous ranges of h in those orders (difference
+                        // arrays by time position r and C): where f falls
+                        // against h and g1 and whether the window holds are
+                        // monotone in th.  The ranges of the x-order cover the
+                        // h with |h & g1| = |g1| - |g1 & f|, for which B = 0.
+                        // A changed f is taken per h (it counts only for h < f).
+                        if (tid == 0) acc.w[5] += (unsigned long long)n1;
+                        auto& T = s.u2.t;
+                        if (wid == 0) {
+                            const bool in = lane < nh;
+                            const int64_t tl = in ? T.hts[lane] : 0;
+                            const int32_t il = in ? s.hh[lane] : 0;
+                            const int xl = in ? s.hx[lane] : 0;
+                            int rt = 0, rx = 0;
+                            for (int m = 0; m < nh; ++m) {
+                                const int64_t tm = T.hts[m];
+                                const int32_t im = s.hh[m];
+                                const int xm = s.hx[m];
+                                const bool lt = tm < tl || (tm == tl && im < il);
+                                rt += lt ? 1 : 0;
+                                rx += (xm < xl || (xm == xl && lt)) ? 1 : 0;
+                            }
+                            if (in) {
+                                T.ot_t[rt] = tl;
+                                T.ot_i[rt] = il;
+                                T.pt[lane] = rt;
+                                T.ox_t[rx] = tl;
+                                T.ox_i[rx] = il;
+                                T.ox_x[rx] = xl;
+                                T.px[lane] = rx;
+                            }
+                            const unsigned bef = __ballot_sync(0xffffffffu, in && (tl < ts1 || (tl == ts1 && il < g1)));
+                            if (lane == 0) T.n_before = __popc(bef);
+                        }
+                        for (int i = tid; i < 8 * (LCH + 1); i += NT_C) {
+                            (&T.dT[0][0])[i] = 0;
+                            (&T.dX[0][0])[i] = 0;
+                        }
+                        __syncthreads();
+                        const int s1 = T.n_before;
+                        // counts at the places every f meets in the (t, ID)
+                        // order -- 0 and s1 -- are kept per thread and added
+                        // once (the end nh needs nothing: no prefix reads it)
+                        int at0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                        for (int q = tid; q < n1; q += NT_C) {
+                            const int sl = T1.list[q];
+                            const int32_t f = T1.keys[sl];
+                            const int32_t meta = lk[q];
+                            const int x = int(T1.vals[sl]);
+                            const int C = (meta & 0x7fffffff) > x ? 1 : 0;
+                            const int64_t tf = lts[q];
+                            if (meta < 0) {
+                                for (int l = 0; l < nh; ++l) {
+                                    const int32_t h = s.hh[l];
+                                    if (f <= h) continue;  // f = h, or a changed f < h: its triads belong to f
+                                    const int xh1 = s.hx[l];
+                                    const int m = (s.hk[l] > xh1 ? 1 : 0) | (x != k1 - xh1 ? 2 : 0) | (C << 2) | 8 | 16;
+                                    ++acc.n_tri;
+                                    if (want_h) {
+                                        const int c = s.tb.cls30[m];
+                                        if (c >= 0) atomicAdd(&hist[c], 1u);
+                                    }
+                                    const int c96 = temporal_class(s.tb, m, T.hts[l], ts1, tf, h, g1, f, delta);
+                                    if (c96 >= 0) atomicAdd(&T.th[wid][c96], 1u);
+                                }
+                                continue;
+                            }
+                            const bool fb = tf < ts1 || (tf == ts1 && f < g1);
+                            // places in [lo, hi) of an order: the first not before
+                            // (t, id); the first at time >= t; the first at time > t
+                            auto first_not_before = [](const int64_t* ta, const int32_t* ia, int lo, int hi, int64_t t,
+                                                       int32_t id) {
+                                while (lo < hi) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (ta[mid] < t || (ta[mid] == t && ia[mid] < id)) lo = mid + 1;
+                                    else hi = mid;
+                                }
+                                return lo;
+                            };
+                            auto first_ge = [](const int64_t* ta, int lo, int hi, int64_t t) {
+                                while (lo < hi) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (ta[mid] < t) lo = mid + 1;
+                                    else hi = mid;
+                                }
+                                return lo;
+                            };
+                            auto first_gt = [](const int64_t* ta, int lo, int hi, int64_t t) {
+                                while (lo < hi) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (ta[mid] <= t) lo = mid + 1;
+                                    else hi = mid;
+                                }
+                                return lo;
+                            };
+                            // the h of [lo, hi) (split: the first after g1) that f
+                            // meets at each time position r within the window
+                            auto ranges = [&](int32_t (*d)[LCH + 1], const int64_t* ta, const int32_t* ia, int lo, int hi,
+                                              int split) {
+                                const bool t_order = d == T.dT;
+                                auto add = [&](int r, int a, int b) {
+                                    if (a >= b) return;
+                                    const int k = r * 2 + C;
+#pragma unroll
+                                    for (int kk = 0; kk < 8; ++kk)
+                                        if (kk == k) {
+                                            if (t_order && a == 0) ++at0[kk];
+                                            else if (t_order && a == s1) ++ats[kk];
+                                            else atomicAdd(&d[kk][a], 1);
+                                            if (t_order && b == s1) --ats[kk];
+                                            else if (!(t_order && b == nh)) atomicAdd(&d[kk][b], -1);
+                                        }
+                                };
+                                const int pos = first_not_before(ta, ia, lo, hi, tf, f);
+                                if (fb) {  // f before g1
+                                    if (ts1 - tf <= delta) add(0, pos, split);               // h before g1, after f
+                                    add(1, first_ge(ta, lo, hi, sat_sub(ts1, delta)), pos);   // h before f, th >= ts1 - delta
+                                    add(0, split, max(split, first_gt(ta, lo, hi, sat_add(tf, delta))));  // h after g1, th <= tf + delta
+                                } else {   // f after g1
+                                    add(2, first_ge(ta, lo, hi, sat_sub(tf, delta)), split);  // h before g1, th >= tf - delta
+                                    add(1, pos, max(pos, first_gt(ta, lo, hi, sat_add(ts1, delta))));  // h after f, th <= ts1 + delta
+                                    if (tf - ts1 <= delta) add(2, split, pos);               // h after g1, before f
+                                }
+                                add(3, lo, hi);  // static classes: every h
+                            };
+                            ranges(T.dT, T.ot_t, T.ot_i, 0, nh, s1);
+                            const int xs = k1 - x;
+                            int ga = 0, gb = nh;  // the h with |h & g1| = xs
+                            {
+                                int lo = 0, hi = nh;
+                                while (lo < hi) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (T.ox_x[mid] < xs) lo = mid + 1;
+                                    else hi = mid;
+                                }
+                                ga = lo;
+                                hi = nh;
+                                while (lo < hi) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (T.ox_x[mid] <= xs) lo = mid + 1;
+                                    else hi = mid;
+                                }
+                                gb = lo;
+                            }
+                            if (ga < gb)
+                                ranges(T.dX, T.ox_t, T.ox_i, ga, gb, first_not_before(T.ox_t, T.ox_i, ga, gb, ts1, g1));
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            int a = at0[k], b = ats[k];
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) {
+                                a += __shfl_xor_sync(0xffffffffu, a, o);
+                                b += __shfl_xor_sync(0xffffffffu, b, o);
+                            }
+                            if (lane == 0) {
+                                if (a) atomicAdd(&T.dT[k][0], a);
+                                if (b) atomicAdd(&T.dT[k][s1], b);
+                            }
+                        }
+                        __syncthreads();
+                        if (tid < 16) {  // inclusive prefix sums: the ranges holding each place
+                            int32_t* d = tid < 8 ? T.dT[tid] : T.dX[tid - 8];
+                            int run = 0;
+                            for (int i = 0; i < nh; ++i) {
+                                run += d[i];
+                                d[i] = run;
+                            }
+                        }
+                        __syncthreads();
+                        if (wid == 0 && lane < nh) {
+                            const int l = lane;
+                            const int xh1 = s.hx[l];
+                            const int A_bit = s.hk[l] > xh1 ? 1 : 0;
+                            const bool h_first = T.hts[l] < ts1 || (T.hts[l] == ts1 && s.hh[l] < g1);
+                            // labels 0 = h, 1 = g1, 2 = f; p and q are h and g1 in time order
+                            const int lp = h_first ? 0 : 1, lq = h_first ? 1 : 0;
+                            const int ptl = T.pt[l], pxl = T.px[l];
+                            for (int r = 0; r < 4; ++r)
+                                for (int C = 0; C < 2; ++C) {
+                                    const int n_all = T.dT[r * 2 + C][ptl], n_b0 = T.dX[r * 2 + C][pxl];
+                                    for (int B = 0; B < 2; ++B) {
+                                        const int n = B ? n_all - n_b0 : n_b0;
+                                        if (n <= 0) continue;
+                                        const int m = A_bit | (B << 1) | (C << 2) | (1 << 3) | (1 << 4);
+                                        if (r == 3) {
+                                            acc.n_tri += (unsigned long long)n;
+                                            const int c = s.tb.cls30[m];
+                                            if (want_h && c >= 0) atomicAdd(&hist[c], uint32_t(n));
+                                        } else {
+                                            const int o0 = r == 0 ? 2 : lp, o1 = r == 0 ? lp : (r == 1 ? 2 : lq);
+                                            const int c = s.tb.cls96[s.tb.perm[perm_index(o0, o1)][m]];
+                                            if (c >= 0) atomicAdd(&T.th[wid][c], uint32_t(n));
+                                        }
+                                    }
+                                }
                         }
                     }
                 }
@@ -2492,6 +3005,7 @@ __global__ void k_scan_apply(const In* in, int64_t n_host, const int32_t* n_dev,
 __global__ void k_run_begin(Scalars* sc, int side) {
     sc->r_used[side] = 0;
     sc->qnh[side] = 0;
+    sc->qoh[side] = 0;
     sc->queue[side] = 0;
     sc->n_d[side] = 0;
     sc->items[side] = 0;
@@ -2635,6 +3149,7 @@ void count_prepare() {
                          int(sizeof(SmemC<512, 4096>)));
     cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(SmemC<256, 2048>)));
+    cudaFuncSetAttribute(k_open_h, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemOH)));
 #define ESC_CO_ATTR(NT, TS, MB)                                                                          \
     cudaFuncSetAttribute(k_center_o<NT, TS, MB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                          int(sizeof(SmemCO<NT, TS>)));                                                      \
@@ -2672,6 +3187,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_apply<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, n_run, cs.block_sums, cs.opre);
     k_order_place<<<capped(blocks_for(nmax, 256)), 256, 0, st>>>(A);
     k_nh_build<<<cs.n_cta_nh, NT_NH, sizeof(SmemNH), st>>>(A);
+    if (orient && temp) k_open_h<<<cs.n_cta_c, kOhNT, sizeof(SmemOH), st>>>(A);
     cudaMemsetAsync(cs.block_sums, 0, sizeof(int64_t) * kOrderBuckets, st);
     k_dsort_count<<<ge, 256, 0, st>>>(A);
     k_dsort_scan<<<1, 32, 0, st>>>(A);
@@ -2712,7 +3228,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     }
     if (timed) cudaEventRecord(cs.cev[2 * (*cs.n_cev)++ + 1], st);
     k_d_clean<<<ge, 256, 0, st>>>(A);
-    lc.total += orient ? 23 : 22;
+    lc.total += (orient ? 23 : 22) + (orient && temp ? 1 : 0);
     lc.count += 2;
     return cudaGetLastError();
 }

@@ -93,6 +93,7 @@ struct CountScratch {
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 3 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     bool orient = true;              // search closed pairs in (|g|, g) order (not with restricted lists)
+    int oh_max = 8192;               // temporal family: longest N'(h) whose open triads k_open_h counts
     // work split of one hypergraph across ranks: count_launch counts only
     // this rank's contiguous share (by neighbourhood size) of a side
     int split_rank = 0, split_world = 1;

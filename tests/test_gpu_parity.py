@@ -206,14 +206,19 @@ def test_both_centre_kernels_without_temporal(E, monkeypatch, orient):
     run_stream(E, s, 3, 0)
 
 
-@pytest.mark.parametrize("orient,coarse", [("0", 1), ("1", 1), ("1", 2000)])
-def test_both_centre_kernels_with_temporal(E, monkeypatch, orient, coarse):
+@pytest.mark.parametrize("orient,coarse,open_max", [("0", 1, None), ("1", 1, None), ("1", 2000, None),
+                                                    ("1", 1, "16"), ("1", 2000, "0")])
+def test_both_centre_kernels_with_temporal(E, monkeypatch, orient, coarse, open_max):
     """All three families through both centre kernels.  The oriented one
-    classifies the open triads centred at h as it visits N'(h) and counts
-    those centred at g1 per h by their place in time; closed triads take
-    back what those counts gave them.  Timestamps divided by `coarse` make
-    many ties (ordered by ID), and the window cuts part of the triads."""
+    counts the open triads centred at h from the time order of N'(h)
+    (k_open_h), or, for a list longer than ESC_COUNT_OPEN_MAX, classifies
+    each as it visits N'(h); those centred at g1 are counted per chunk by a
+    sweep over N(g1); closed triads take back what those counts gave them.
+    Timestamps divided by `coarse` make many ties (ordered by ID), and the
+    window cuts part of the triads."""
     monkeypatch.setenv("ESC_COUNT_ORIENT", orient)
+    if open_max is not None:
+        monkeypatch.setenv("ESC_COUNT_OPEN_MAX", open_max)
     s = gen.random_small(31, 400, 600, 2, 30, n_batches=3, n_ins=60, n_del=60, membership="zipf", card="zipf")
     if coarse > 1:
         s.initial.timestamps[:] //= coarse
