@@ -78,10 +78,13 @@
  *   ESC_COUNT_M1PCT=p         weight (percent) of a visit of N(g1) against a
  *                             visit of N(h) in the per-pair choice of which
  *                             side to scan.
- *   ESC_COUNT_OPEN_MAX=n      temporal family: longest N'(h) (0..8192) whose
- *                             open triads centred at h are counted from its
- *                             time order; longer ones have every pair
+ *   ESC_COUNT_OPEN_MAX=n      temporal family: longest N'(h) (0..65536)
+ *                             whose open triads centred at h are counted from
+ *                             its time order; longer ones have every pair
  *                             classified by the centre kernel.
+ *   ESC_COUNT_OPEN_SMEM=n     temporal family: longest N'(h) (0..8192) sorted
+ *                             in shared memory for that count; longer ones are
+ *                             sorted in global scratch.
  *   ESC_CENTER_SMALL=s        centre-kernel launch shape, as
  *                             esc_tune_result.center_shape (0..3).
  *   ESC_CALL_GRAPH=1          graph launch on from creation (as
@@ -505,7 +508,7 @@ esc_status esc_server_destroy(esc_server* srv);
  * its status back) and returns once out_counts is written.
  *
  * It calls no cudaMalloc or cudaFree: its temporary buffers live in one
- * fixed array of device memory (80 MiB) that every GPU which loads the
+ * fixed array of device memory (128 MiB) that every GPU which loads the
  * library holds until the process exits.  The first call on a device looks
  * up that array's device address.  All calls share the array and every call
  * resets what it needs, so calls whose GPU work overlaps race on it:
@@ -560,21 +563,33 @@ esc_status esc_set_split(esc_graph* g, int32_t rank, int32_t world);
 esc_status esc_group_set_split(esc_group* grp, int32_t rank, int32_t world);
 
 /* ------------------------------------------------------------------------
- * Autotuning.  The counter's launch shape (centre blocks per SM x threads:
- * 0: 1 x 512, 1: 2 x 256, 2: 2 x 512, 3: 3 x 256) and, without the temporal
- * family, whether large neighbourhoods get restricted incidence lists, are
- * timed on the graph's own data: the triads holding a sample of live
- * hyperedges (ids: that graph's IDs, host or device memory) are counted and
- * discarded, `reps` timed runs per candidate after one warm-up run, and the
- * fastest candidate is kept for later calls.  Counts and store are left
- * unchanged.  The paper fixes no such choice; it is a property of this
- * implementation.  Errors: INVALID_ARG, NOT_FOUND (an ID not live), CUDA.
+ * Autotuning.  Timed on the graph's own data -- the triads holding a sample
+ * of live hyperedges (ids: that graph's IDs, host or device memory) are
+ * counted and discarded, `reps` timed runs per candidate after one warm-up
+ * run -- the fastest candidate of each choice is kept for later calls:
+ *   1. the counter's launch shape (centre blocks per SM x threads: 0: 1 x 512,
+ *      1: 2 x 256, 2: 2 x 512, 3: 3 x 256) and, without the temporal family,
+ *      whether large neighbourhoods get restricted incidence lists;
+ *   2. with that shape, the intersection strategy by neighbourhood size: the
+ *      N(h) size from which N(h) gets a hash table and a membership filter
+ *      (below it a pair (h, g1) can only scan N(h) against N(g1)'s table;
+ *      above it, it may probe N(h)'s filter and table with N(g1)'s list
+ *      instead) -- 256, 512 or 1024 entries;
+ *   3. with those, the weight of a visit of N(g1) against a visit of N(h) in
+ *      that per-pair choice -- 50%, 100% or 200%.
+ * Counts and store are left unchanged.  The paper fixes no such choice; it
+ * is a property of this implementation.  Errors: INVALID_ARG, NOT_FOUND (an
+ * ID not live), CUDA.
  * ------------------------------------------------------------------------ */
 typedef struct {
     int32_t center_shape;  /* the chosen shape, 0..3 as above                    */
     int32_t restricted;    /* 1: restricted lists chosen                          */
     float ms[8];           /* best time of each candidate: shapes 0..3 without,
                               then with restricted lists (-1: not run)            */
+    int32_t table_from;    /* the chosen N(h) size for a table and filter         */
+    int32_t m1_pct;        /* the chosen weight of an N(g1) visit, percent        */
+    float ms_table[3];     /* best time with table_from 256, 512, 1024            */
+    float ms_m1[3];        /* best time with m1_pct 50, 100, 200                  */
 } esc_tune_result;
 
 esc_status esc_autotune(esc_graph* g, int64_t n_ids, const int32_t* ids, int32_t reps, esc_tune_result* out);

@@ -18,9 +18,10 @@
 
 namespace esc {
 
-namespace {
-
+// the message of the last failed call without a handle (esc_last_error(NULL))
 thread_local std::string t_create_error;
+
+namespace {
 
 // 0: pageable host memory, 1: page-locked host memory, 2: device memory
 int ptr_kind(const void* p) {
@@ -386,7 +387,11 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
     if (const char* env = getenv("ESC_COUNT_ORIENT")) E->cs.orient = atoi(env) != 0;
     if (const char* env = getenv("ESC_COUNT_OPEN_MAX")) {
         long long v = atoll(env);
-        if (v >= 0 && v <= 8192) E->cs.oh_max = int(v);
+        if (v >= 0 && v <= 65536) E->cs.oh_max = int(v);
+    }
+    if (const char* env = getenv("ESC_COUNT_OPEN_SMEM")) {
+        long long v = atoll(env);
+        if (v >= 0 && v <= 8192) E->cs.oh_smem = int(v);
     }
     if (const char* env = getenv("ESC_COUNT_SMEM_SLOTS")) {
         long long v = atoll(env);
@@ -1107,6 +1112,7 @@ static esc_status autotune(Engine* E, int64_t n, const int32_t* ids, int32_t rep
         }
     }
     for (int k = 0; k < 8; ++k) out->ms[k] = -1.f;
+    for (int k = 0; k < 3; ++k) out->ms_table[k] = out->ms_m1[k] = -1.f;
     float best = 3.4e38f;
     int best_shape = cs.center_small, best_r = r_cap0 > 0 ? 1 : 0;
     for (int r = 0; r < 2; ++r) {
@@ -1137,19 +1143,64 @@ static esc_status autotune(Engine* E, int64_t n, const int32_t* ids, int32_t rep
         if (r == 0) cs.r_cap = cap_now;
     }
     cs.center_small = best_shape;
+    if (best_r == 1) {
+        if (extra) E->allocs.push_back(extra);  // kept for the engine's life
+        extra = nullptr;
+    } else {
+        cs.r_cap = r_cap0;
+        cs.r_pool = r_pool0;
+    }
+    // the intersection strategy by neighbourhood size, then the per-pair
+    // side weight, each with the choices made so far
+    auto time_now = [&](float* best_ms) -> esc_status {
+        float t = 3.4e38f;
+        for (int rep = 0; rep <= reps; ++rep) {
+            float ms = 0.f;
+            esc_status s = local_triads(E, n, ids, nullptr, nullptr, nullptr, &ms);
+            if (s != ESC_OK) return s;
+            if (rep > 0) t = std::min(t, ms);
+        }
+        *best_ms = t;
+        return ESC_OK;
+    };
+    const int tables[3] = {256, 512, 1024}, m1s[3] = {50, 100, 200};
+    float bt = 3.4e38f, bm = 3.4e38f;
+    int64_t best_table = cs.big_nh, best_m1 = cs.m1_pct;
+    for (int k = 0; k < 3; ++k) {
+        cs.big_nh = tables[k];
+        esc_status s = time_now(&out->ms_table[k]);
+        if (s != ESC_OK) {
+            if (extra) cudaFree(extra);
+            return s;
+        }
+        if (out->ms_table[k] < bt) {
+            bt = out->ms_table[k];
+            best_table = tables[k];
+        }
+    }
+    cs.big_nh = best_table;
+    for (int k = 0; k < 3; ++k) {
+        cs.m1_pct = m1s[k];
+        esc_status s = time_now(&out->ms_m1[k]);
+        if (s != ESC_OK) {
+            if (extra) cudaFree(extra);
+            return s;
+        }
+        if (out->ms_m1[k] < bm) {
+            bm = out->ms_m1[k];
+            best_m1 = m1s[k];
+        }
+    }
+    cs.m1_pct = best_m1;
+    if (extra) cudaFree(extra);
     if (E->gexec) {  // a captured sequence holds the old shape
         cudaGraphExecDestroy(E->gexec);
         E->gexec = nullptr;
     }
-    if (best_r == 1) {
-        if (extra) E->allocs.push_back(extra);  // kept for the engine's life
-    } else {
-        cs.r_cap = r_cap0;
-        cs.r_pool = r_pool0;
-        if (extra) cudaFree(extra);
-    }
     out->center_shape = best_shape;
     out->restricted = best_r;
+    out->table_from = int32_t(best_table);
+    out->m1_pct = int32_t(best_m1);
     return ESC_OK;
 }
 

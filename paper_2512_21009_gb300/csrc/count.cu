@@ -1608,18 +1608,22 @@ __device__ __forceinline__ int64_t sat_sub(int64_t a, int64_t b) { return a < IN
 // Pairs inside a range are counted per later member from prefix counts of C;
 // those with x_a + x_b = |h| from a second order by (x, place): the members
 // with x = |h| - x_b and places in [L, b) are one stretch of it.  Work per h
-// is O(n log n) (two bitonic sorts) instead of one visit per pair.  A list
-// longer than kOhMax (or the lower cs.oh_max) is left to the centre kernel,
-// which then classifies every pair of it (flag bit 1 of nh_flag).
+// is O(n log^2 n) (two bitonic sorts) instead of one visit per pair.  A list
+// of at most kOhMax entries (cs.oh_smem) is sorted in shared memory, a longer
+// one of at most cs.oh_cap in the block's global scratch (the same code on
+// L2-resident arrays); one longer still (or than cs.oh_max) is left to the
+// centre kernel, which then classifies every pair of it (flag bit 1 of
+// nh_flag).
 constexpr int kOhNT = 1024;
-constexpr int kOhMax = 8192;  // entries of N'(h) sorted in shared memory, at most
+constexpr int kOhMax = 8192;   // entries of N'(h) sorted in shared memory, at most
+constexpr int kOhBig = 65536;  // entries sorted in the block's global scratch, at most
 
 struct SmemOH {
     Tables tb;
     int64_t t[kOhMax];         // timestamp of each entry (sorted with id and pay)
     int32_t id[kOhMax];
     int32_t pay[kOhMax];       // x | C << 15
-    int32_t key[kOhMax];       // x << 14 | place << 1 | C, sorted
+    uint32_t key[kOhMax];      // x << ksh | place << 1 | C, sorted
     uint16_t p1[kOhMax + 1];   // entries with C = 1 among the first i, in (t, ID) order
     uint16_t pc[kOhMax + 1];   // the same in key order
     unsigned long long cnt[24];
@@ -1629,15 +1633,13 @@ struct SmemOH {
 };
 
 // out[i] = number of the first i of n entries with bit(i) set, and out[n]
-template <typename F>
-__device__ __forceinline__ void oh_prefix(F bit, uint16_t* out, int n, int* wsum) {
-    constexpr int PER = kOhMax / kOhNT;
+template <typename PT, typename F>
+__device__ __forceinline__ void oh_prefix(F bit, PT* out, int n, int* wsum) {
     const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
-    const int q0 = tid * PER;
+    const int per = (n + kOhNT - 1) / kOhNT;
+    const int q0 = tid * per, q1 = min(q0 + per, n);
     int c = 0;
-#pragma unroll
-    for (int k = 0; k < PER; ++k)
-        if (q0 + k < n) c += bit(q0 + k);
+    for (int q = q0; q < q1; ++q) c += bit(q);
     int inc = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1655,16 +1657,14 @@ __device__ __forceinline__ void oh_prefix(F bit, uint16_t* out, int n, int* wsum
             if (lane >= o) x += v;
         }
         wsum[lane] = x - own;
-        if (lane == 31) out[n] = uint16_t(x);
+        if (lane == 31) out[n] = PT(x);
     }
     __syncthreads();
     int run = wsum[w] + inc - c;
-#pragma unroll
-    for (int k = 0; k < PER; ++k)
-        if (q0 + k < n) {
-            out[q0 + k] = uint16_t(run);
-            run += bit(q0 + k);
-        }
+    for (int q = q0; q < q1; ++q) {
+        out[q] = PT(run);
+        run += bit(q);
+    }
     __syncthreads();
 }
 
@@ -1689,15 +1689,173 @@ __device__ __forceinline__ void oh_add(unsigned (&c)[24], int cas, bool later, i
     }
 }
 
+// The open triads centred at h over the n entries of N'(h) loaded into
+// (T, I, P), in shared memory or the block's global scratch: sorted, ranked
+// and counted into s.cnt, then added to graph g's temporal bins.  ksh: the
+// key shift (places < 1 << (ksh - 1)).
+template <typename PT>
+__device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32_t* I, int32_t* P, uint32_t* K,
+                         PT* P1, PT* PC, int ksh, int kh, int64_t th, int32_t h, int g) {
+    const int tid = threadIdx.x, lane = lane_id();
+    const int64_t delta = A.S.delta;
+    int n2 = 2;
+    while (n2 < n) n2 <<= 1;
+    for (int q = n + tid; q < n2; q += kOhNT) {
+        T[q] = INT64_MAX;
+        I[q] = INT_MAX;
+        P[q] = 0;
+    }
+    __syncthreads();
+    // bitonic sort by (t, ID)
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int u = tid; u < (n2 >> 1); u += kOhNT) {
+                const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
+                const int64_t ta = T[a], tb = T[b];
+                const int32_t ia = I[a], ib = I[b];
+                if ((ta > tb || (ta == tb && ia > ib)) == ((a & k) == 0)) {
+                    T[a] = tb;
+                    T[b] = ta;
+                    I[a] = ib;
+                    I[b] = ia;
+                    const int32_t pa = P[a];
+                    P[a] = P[b];
+                    P[b] = pa;
+                }
+            }
+            __syncthreads();
+        }
+    for (int q = tid; q < n2; q += kOhNT)
+        K[q] = q < n ? (uint32_t(P[q] & 0x7fff) << ksh) | (uint32_t(q) << 1) | uint32_t((P[q] >> 15) & 1) : UINT32_MAX;
+    oh_prefix<PT>([&](int q) { return (P[q] >> 15) & 1; }, P1, n, s.wsum);
+    // bitonic sort of the keys
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int u = tid; u < (n2 >> 1); u += kOhNT) {
+                const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
+                const uint32_t ka = K[a], kb = K[b];
+                if ((ka > kb) == ((a & k) == 0)) {
+                    K[a] = kb;
+                    K[b] = ka;
+                }
+            }
+            __syncthreads();
+        }
+    oh_prefix<PT>([&](int q) { return int(K[q] & 1u); }, PC, n, s.wsum);
+    if (tid == 0) {
+        // h's place, the first member within delta before it, the end of
+        // the members within delta after it
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T[mid] < th || (T[mid] == th && I[mid] < h)) lo = mid + 1;
+            else hi = mid;
+        }
+        const int sp = lo;
+        lo = 0;
+        hi = sp;
+        const int64_t tlo = sat_sub(th, delta), thi = sat_add(th, delta);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T[mid] < tlo) lo = mid + 1;
+            else hi = mid;
+        }
+        s.l0 = lo;
+        lo = sp;
+        hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (T[mid] <= thi) lo = mid + 1;
+            else hi = mid;
+        }
+        s.r1 = lo;
+        s.s_pos = sp;
+    }
+    __syncthreads();
+    const int sp = s.s_pos, l0 = s.l0, r1 = s.r1;
+    // the first key at or above v (targets are formed in 64 bits: with the
+    // place n << 1 they reach the first key of the next x)
+    auto key_lb = [&](uint64_t v) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (uint64_t(K[mid]) < v) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    unsigned c[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) c[k] = 0;
+    for (int e = tid; e < n; e += kOhNT) {
+        const int xe = P[e] & 0x7fff;
+        const int ce = (P[e] >> 15) & 1;
+        const int xs = kh - xe;  // the x of a partner that completes h
+        // members in places [L, R) with x = xs: how many, and with C = 1
+        auto match = [&](int L, int Rr, int& m, int& m1) {
+            m = m1 = 0;
+            if (xs < 1 || L >= Rr) return;
+            const int i0 = key_lb((uint64_t(xs) << ksh) + (uint64_t(L) << 1));
+            const int i1 = key_lb((uint64_t(xs) << ksh) + (uint64_t(Rr) << 1));
+            m = i1 - i0;
+            m1 = int(PC[i1]) - int(PC[i0]);
+        };
+        auto range = [&](int cas, bool later, int L, int Rr) {
+            if (L >= Rr) return;
+            int m, m1;
+            match(L, Rr, m, m1);
+            const int tot = Rr - L, t1 = int(P1[Rr]) - int(P1[L]);
+            if (ce) oh_add<1>(c, cas, later, tot, t1, m, m1);
+            else oh_add<0>(c, cas, later, tot, t1, m, m1);
+        };
+        if (e >= l0 && e < sp) range(0, true, l0, e);   // h last: a in [l0, e)
+        if (e >= sp && e < r1) range(1, true, sp, e);   // h first: a in [sp, e)
+        if (e < sp) {                                   // h middle: b after h within delta of e
+            const int64_t tb = sat_add(T[e], delta);
+            int lo = sp, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (T[mid] <= tb) lo = mid + 1;
+                else hi = mid;
+            }
+            range(2, false, sp, lo);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+        unsigned v = c[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v) atomicAdd(&s.cnt[k], (unsigned long long)v);
+    }
+    __syncthreads();
+    if (tid < 24 && s.cnt[tid]) {
+        const int cas = tid >> 3, E = (tid >> 2) & 1, ca = (tid >> 1) & 1, cb = tid & 1;
+        // labels 0 = h, 1 = a, 2 = b; order: h last (a, b, h), first (h, a, b), middle (a, h, b)
+        const int m = (E ? 0 : 1) | (ca ? 2 : 0) | (cb ? 4 : 0) | (1 << 3) | (1 << 5);
+        const int pi = cas == 0 ? perm_index(1, 2) : cas == 1 ? perm_index(0, 1) : perm_index(1, 0);
+        const int cl = s.tb.cls96[s.tb.perm[pi][m]];
+        if (cl >= 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(g) * kCStride + kOffT + cl]), s.cnt[tid]);
+    }
+}
+
 __global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemOH& s = *reinterpret_cast<SmemOH*>(smem_raw);
     const Store& S = A.S;
     if (A.sc->gate) return;
     const CountScratch& cs = A.cs;
-    const int tid = threadIdx.x, lane = lane_id();
-    const int64_t delta = S.delta;
+    const int tid = threadIdx.x;
     const RunRange R = run_of(A);
+    const int smem_max = min(kOhMax, cs.oh_smem);
+    const int64_t gstride = cs.oh_cap + 1;
+    int64_t* gT = cs.oh_t + blockIdx.x * gstride;
+    int32_t* gI = cs.oh_i + blockIdx.x * gstride;
+    int32_t* gP = cs.oh_p + blockIdx.x * gstride;
+    uint32_t* gK = cs.oh_k + blockIdx.x * gstride;
+    uint32_t* gP1 = cs.oh_p1 + blockIdx.x * gstride;
+    uint32_t* gPC = cs.oh_pc + blockIdx.x * gstride;
     load_tables(s.tb, kOhNT);
     for (;;) {
         __syncthreads();
@@ -1716,163 +1874,36 @@ __global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
         const int kh = S.h_card[h];
         const int64_t th = S.h_ts[h];
         const int64_t base = cs.nh_off[i] - R.base;
-        for (int q = tid; q < nn; q += kOhNT) {
-            const int32_t gg = cs.nh_g[base + q];
-            const uint64_t xv = cs.nh_xv[base + q];
-            if (gg < h && ((xv >> 31) & 1u)) continue;  // changed below h: its triads belong to gg
-            const int p = atomicAdd(&s.n, 1);
-            if (p < kOhMax) {
-                const int x = int(xv & kXMask), kg = int((xv >> 16) & 0x7fffu);
-                s.t[p] = cs.nh_ts[base + q];
-                s.id[p] = gg;
-                s.pay[p] = x | (kg > x ? 1 << 15 : 0);
-            }
-        }
-        __syncthreads();
-        const int n = s.n;
-        if (n > cs.oh_max) {  // left to the centre kernel
-            if (tid == 0) cs.nh_flag[i] |= 2;
-            continue;
-        }
-        if (n < 2) continue;
-        int n2 = 2;
-        while (n2 < n) n2 <<= 1;
-        for (int q = n + tid; q < n2; q += kOhNT) {
-            s.t[q] = INT64_MAX;
-            s.id[q] = INT_MAX;
-            s.pay[q] = 0;
-        }
-        __syncthreads();
-        // bitonic sort by (t, ID)
-        for (int k = 2; k <= n2; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int u = tid; u < (n2 >> 1); u += kOhNT) {
-                    const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
-                    const int64_t ta = s.t[a], tb = s.t[b];
-                    const int32_t ia = s.id[a], ib = s.id[b];
-                    if ((ta > tb || (ta == tb && ia > ib)) == ((a & k) == 0)) {
-                        s.t[a] = tb;
-                        s.t[b] = ta;
-                        s.id[a] = ib;
-                        s.id[b] = ia;
-                        const int32_t pa = s.pay[a];
-                        s.pay[a] = s.pay[b];
-                        s.pay[b] = pa;
-                    }
+        // N'(h), into shared memory while it fits, else into the block's
+        // global scratch while that fits
+        auto load = [&](int64_t* T, int32_t* I, int32_t* P, int cap) {
+            for (int q = tid; q < nn; q += kOhNT) {
+                const int32_t gg = cs.nh_g[base + q];
+                const uint64_t xv = cs.nh_xv[base + q];
+                if (gg < h && ((xv >> 31) & 1u)) continue;  // changed below h: its triads belong to gg
+                const int p = atomicAdd(&s.n, 1);
+                if (p < cap) {
+                    const int x = int(xv & kXMask), kg = int((xv >> 16) & 0x7fffu);
+                    T[p] = cs.nh_ts[base + q];
+                    I[p] = gg;
+                    P[p] = x | (kg > x ? 1 << 15 : 0);
                 }
-                __syncthreads();
             }
-        for (int q = tid; q < n2; q += kOhNT)
-            s.key[q] = q < n ? ((s.pay[q] & 0x7fff) << 14) | (q << 1) | ((s.pay[q] >> 15) & 1) : INT_MAX;
-        oh_prefix([&](int q) { return (s.pay[q] >> 15) & 1; }, s.p1, n, s.wsum);
-        // bitonic sort of the keys
-        for (int k = 2; k <= n2; k <<= 1)
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int u = tid; u < (n2 >> 1); u += kOhNT) {
-                    const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
-                    const int32_t ka = s.key[a], kb = s.key[b];
-                    if ((ka > kb) == ((a & k) == 0)) {
-                        s.key[a] = kb;
-                        s.key[b] = ka;
-                    }
-                }
-                __syncthreads();
-            }
-        oh_prefix([&](int q) { return s.key[q] & 1; }, s.pc, n, s.wsum);
-        if (tid == 0) {
-            // h's place, the first member within delta before it, the end of
-            // the members within delta after it
-            int lo = 0, hi = n;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s.t[mid] < th || (s.t[mid] == th && s.id[mid] < h)) lo = mid + 1;
-                else hi = mid;
-            }
-            const int sp = lo;
-            lo = 0;
-            hi = sp;
-            const int64_t tlo = sat_sub(th, delta), thi = sat_add(th, delta);
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s.t[mid] < tlo) lo = mid + 1;
-                else hi = mid;
-            }
-            s.l0 = lo;
-            lo = sp;
-            hi = n;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s.t[mid] <= thi) lo = mid + 1;
-                else hi = mid;
-            }
-            s.r1 = lo;
-            s.s_pos = sp;
-        }
-        __syncthreads();
-        const int sp = s.s_pos, l0 = s.l0, r1 = s.r1;
-        auto key_lb = [&](int32_t v) {
-            int lo = 0, hi = n;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (s.key[mid] < v) lo = mid + 1;
-                else hi = mid;
-            }
-            return lo;
+            __syncthreads();
         };
-        unsigned c[24];
-#pragma unroll
-        for (int k = 0; k < 24; ++k) c[k] = 0;
-        for (int e = tid; e < n; e += kOhNT) {
-            const int xe = s.pay[e] & 0x7fff;
-            const int ce = (s.pay[e] >> 15) & 1;
-            const int xs = kh - xe;  // the x of a partner that completes h
-            // members in places [L, R) with x = xs: how many, and with C = 1
-            auto match = [&](int L, int Rr, int& m, int& m1) {
-                m = m1 = 0;
-                if (xs < 1 || L >= Rr) return;
-                // places are < kOhMax = 1 << 13, so (xs << 14) + (kOhMax << 1)
-                // is the first key of x = xs + 1
-                const int i0 = key_lb((xs << 14) + (L << 1)), i1 = key_lb((xs << 14) + (Rr << 1));
-                m = i1 - i0;
-                m1 = int(s.pc[i1]) - int(s.pc[i0]);
-            };
-            auto range = [&](int cas, bool later, int L, int Rr) {
-                if (L >= Rr) return;
-                int m, m1;
-                match(L, Rr, m, m1);
-                const int tot = Rr - L, t1 = int(s.p1[Rr]) - int(s.p1[L]);
-                if (ce) oh_add<1>(c, cas, later, tot, t1, m, m1);
-                else oh_add<0>(c, cas, later, tot, t1, m, m1);
-            };
-            if (e >= l0 && e < sp) range(0, true, l0, e);   // h last: a in [l0, e)
-            if (e >= sp && e < r1) range(1, true, sp, e);   // h first: a in [sp, e)
-            if (e < sp) {                                   // h middle: b after h within delta of e
-                const int64_t tb = sat_add(s.t[e], delta);
-                int lo = sp, hi = n;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (s.t[mid] <= tb) lo = mid + 1;
-                    else hi = mid;
-                }
-                range(2, false, sp, lo);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            unsigned v = c[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && v) atomicAdd(&s.cnt[k], (unsigned long long)v);
-        }
-        __syncthreads();
-        if (tid < 24 && s.cnt[tid]) {
-            const int cas = tid >> 3, E = (tid >> 2) & 1, ca = (tid >> 1) & 1, cb = tid & 1;
-            // labels 0 = h, 1 = a, 2 = b; order: h last (a, b, h), first (h, a, b), middle (a, h, b)
-            const int m = (E ? 0 : 1) | (ca ? 2 : 0) | (cb ? 4 : 0) | (1 << 3) | (1 << 5);
-            const int pi = cas == 0 ? perm_index(1, 2) : cas == 1 ? perm_index(0, 1) : perm_index(1, 0);
-            const int cl = s.tb.cls96[s.tb.perm[pi][m]];
-            if (cl >= 0)
-                atomicAdd(reinterpret_cast<unsigned long long*>(&A.dc[int64_t(g) * kCStride + kOffT + cl]), s.cnt[tid]);
+        load(s.t, s.id, s.pay, smem_max);
+        const int n = s.n;
+        if (n < 2) continue;
+        if (n <= smem_max) {
+            oh_count<uint16_t>(s, A, n, s.t, s.id, s.pay, s.key, s.p1, s.pc, 14, kh, th, h, g);
+        } else if (n <= cs.oh_max && n <= cs.oh_cap) {
+            __syncthreads();
+            if (tid == 0) s.n = 0;
+            __syncthreads();
+            load(gT, gI, gP, int(cs.oh_cap));
+            oh_count<uint32_t>(s, A, n, gT, gI, gP, gK, gP1, gPC, 17, kh, th, h, g);
+        } else if (tid == 0) {
+            cs.nh_flag[i] |= 2;  // left to the centre kernel
         }
     }
 }
@@ -3041,6 +3072,11 @@ size_t count_scratch_bytes(const CountShape& sh) {
     b += 3 * al(sizeof(int32_t) * rn * sh.gs_nh) + al(sizeof(int32_t) * rn * (sh.gs_nh / 2));
     b += 3 * al(sizeof(int32_t) * rc * sh.gs_c) + 5 * al(sizeof(int32_t) * rc * (sh.gs_c / 2)) +
          al(sizeof(int64_t) * rc * (sh.gs_c / 2));
+    const int64_t oh = open_h_cap(sh);
+    if (oh > 0) {
+        const size_t nb = size_t(sh.n_cta_c) * size_t(oh + 1);
+        b += al(sizeof(int64_t) * nb) + 5 * al(sizeof(int32_t) * nb);
+    }
     return b + 4096;
 }
 
@@ -3111,6 +3147,16 @@ cudaError_t count_scratch_init(CountScratch* cs, void* mem, const CountShape& sh
     cs->oc_lkey = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_pf = static_cast<int32_t*>(take(sizeof(int32_t) * rc * (sh.gs_c / 2)));
     cs->oc_pm = static_cast<uint32_t*>(take(sizeof(uint32_t) * rc * (sh.gs_c / 2)));
+    cs->oh_cap = open_h_cap(sh);
+    if (cs->oh_cap > 0) {
+        const size_t nb = size_t(sh.n_cta_c) * size_t(cs->oh_cap + 1);
+        cs->oh_t = static_cast<int64_t*>(take(sizeof(int64_t) * nb));
+        cs->oh_i = static_cast<int32_t*>(take(sizeof(int32_t) * nb));
+        cs->oh_p = static_cast<int32_t*>(take(sizeof(int32_t) * nb));
+        cs->oh_k = static_cast<uint32_t*>(take(sizeof(uint32_t) * nb));
+        cs->oh_p1 = static_cast<uint32_t*>(take(sizeof(uint32_t) * nb));
+        cs->oh_pc = static_cast<uint32_t*>(take(sizeof(uint32_t) * nb));
+    }
     cs->h_total = pinned_word;
     cudaError_t e;
     if ((e = cudaMemsetAsync(cs->lcnt, 0, sizeof(int32_t) * sh.e_cap, st))) return e;

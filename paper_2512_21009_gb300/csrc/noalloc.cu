@@ -20,12 +20,14 @@
 // overlaps (two streams, two host threads) race on it and must be serialised
 // by the caller.
 #include <mutex>
+#include <string>
 
 #include "escher.h"
 #include "escher_internal.cuh"
 #include "store_api.cuh"
 
 namespace esc {
+extern thread_local std::string t_create_error;  // api.cu: esc_last_error(NULL)
 
 namespace {
 
@@ -35,7 +37,7 @@ constexpr int64_t kNAMaxVertices = int64_t(1) << 19;
 constexpr int kNABlocks = 64;           // blocks of each counting kernel
 constexpr int64_t kNATableSlots = 2048; // per counter overflow table
 constexpr int64_t kNAListEntries = int64_t(1) << 19;  // neighbour-list entries per counting run
-constexpr size_t kNoAllocBytes = size_t(80) << 20;
+constexpr size_t kNoAllocBytes = size_t(128) << 20;
 
 CountShape na_shape() {
     CountShape sh;
@@ -46,6 +48,10 @@ CountShape na_shape() {
     sh.n_cta_nh = sh.n_cta_c = kNABlocks;
     sh.r_cap = 0;  // no restricted lists
     sh.with_ts = true;
+    // no global sort scratch for long lists: their open triads at h are
+    // classified pair by pair by the centre kernel (the fixed array holds
+    // no room for it)
+    sh.open_global = false;
     sh.c_per_sm = 2;
     return sh;
 }
@@ -154,7 +160,11 @@ __global__ void k_na_out(const uint64_t* dc, uint64_t* out, const Scalars* sc) {
     if (i < kNCount) out[i] = sc->status ? 0 : dc[i];
 }
 
-esc_status na_fail(esc_status s, const char*) { return s; }
+// the reason of a failed call, for esc_last_error(NULL)
+esc_status na_fail(esc_status s, const std::string& why) {
+    t_create_error = "esc_count_static_noalloc: " + why;
+    return s;
+}
 
 bool on_device(const void* p) {
     cudaPointerAttributes a;
@@ -266,6 +276,9 @@ extern "C" esc_status esc_count_static_noalloc(int32_t n_vertices, int64_t n_he,
     ok(cudaMemcpyAsync(&h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
     ok(cudaStreamSynchronize(st));
     if (e != cudaSuccess) return na_fail(ESC_ERR_CUDA, cudaGetErrorString(e));
-    return esc_status(h.status);
+    if (h.status != 0)
+        return na_fail(esc_status(h.status), "device check " + std::to_string(h.detail[0]) + " failed (" +
+                                                 std::to_string(h.detail[1]) + ", " + std::to_string(h.detail[2]) + ")");
+    return ESC_OK;
 }
 

@@ -2,6 +2,8 @@
 // kernels, called by the C ABI layer (api.cu).
 #pragma once
 
+#include <algorithm>
+
 #include "escher_internal.cuh"
 
 namespace esc {
@@ -93,7 +95,20 @@ struct CountScratch {
     int64_t smem_slots = 1 << 30;    // cap on shared-memory table sizes (tests lower it)
     int center_small = 3;            // centre blocks per SM x threads: 3: 3 x 256, 1: 2 x 256, 0: 1 x 512, 2: 2 x 512
     bool orient = true;              // search closed pairs in (|g|, g) order (not with restricted lists)
-    int oh_max = 8192;               // temporal family: longest N'(h) whose open triads k_open_h counts
+    // temporal family, open triads centred at h (k_open_h): lists of at most
+    // oh_smem entries are sorted in shared memory, longer ones of at most
+    // min(oh_max, oh_cap) in the block's global scratch (oh_cap a power of
+    // two, the arrays strided by oh_cap + 1); longer ones are left to the
+    // centre kernel
+    int oh_smem = 8192;
+    int oh_max = 65536;
+    int64_t oh_cap = 0;
+    int64_t* oh_t = nullptr;
+    int32_t* oh_i = nullptr;
+    int32_t* oh_p = nullptr;
+    uint32_t* oh_k = nullptr;
+    uint32_t* oh_p1 = nullptr;
+    uint32_t* oh_pc = nullptr;
     // work split of one hypergraph across ranks: count_launch counts only
     // this rank's contiguous share (by neighbourhood size) of a side
     int split_rank = 0, split_world = 1;
@@ -114,6 +129,7 @@ struct CountShape {
     int64_t r_cap;      // int32 entries of the restricted-list pool (0: none)
     bool with_ts;       // keep the neighbours' timestamps in the lists (temporal family)
     int c_per_sm;       // centre blocks per SM the overflow tables are sized for (2 or 3)
+    bool open_global = true;  // temporal family: global scratch for k_open_h's long lists
 };
 
 // pairs.cu: vertex-pair statistics for incident-vertex types 1 and 2
@@ -148,6 +164,16 @@ cudaError_t pairs_update(const Store& S, const Call& C, const PairTable& P, int 
 inline int64_t count_max_u(const CountShape& sh) {
     // a neighbourhood takes at most 5 u list entries (list + table)
     return sh.list_cap / 8;
+}
+
+// entries of the per-block global scratch of k_open_h (0: none)
+inline int64_t open_h_cap(const CountShape& sh) {
+    if (!sh.with_ts || !sh.open_global) return 0;
+    const int64_t want = std::min<int64_t>(count_max_u(sh), 65536);
+    if (want <= 8192) return 0;
+    int64_t c = 8192;
+    while (c < want) c <<= 1;
+    return c;
 }
 
 size_t count_scratch_bytes(const CountShape& sh);

@@ -86,7 +86,9 @@ class esc_server_stats(C.Structure):
 
 
 class esc_tune_result(C.Structure):
-    _fields_ = [("center_shape", C.c_int32), ("restricted", C.c_int32), ("ms", C.c_float * 8)]
+    _fields_ = [("center_shape", C.c_int32), ("restricted", C.c_int32), ("ms", C.c_float * 8),
+                ("table_from", C.c_int32), ("m1_pct", C.c_int32), ("ms_table", C.c_float * 3),
+                ("ms_m1", C.c_float * 3)]
 
 
 _lib = None
@@ -446,7 +448,8 @@ def esc_group_launch_count(grp: int) -> int:
 
 
 def _tune_dict(r: "esc_tune_result") -> dict:
-    return {"center_shape": r.center_shape, "restricted": r.restricted, "ms": list(r.ms)}
+    return {"center_shape": r.center_shape, "restricted": r.restricted, "ms": list(r.ms),
+            "table_from": r.table_from, "m1_pct": r.m1_pct, "ms_table": list(r.ms_table), "ms_m1": list(r.ms_m1)}
 
 
 def esc_autotune(h: int, ids, reps: int = 2) -> dict:
@@ -629,7 +632,7 @@ def esc_count_static_noalloc(n_vertices: int, offsets, members, timestamps, fami
     rc = L.esc_count_static_noalloc(int(n_vertices), n_he, po, pm, pt, int(families), int(delta),
                                     out_counts.data_ptr(), _stream_ptr(stream))
     if rc != 0:
-        raise EscError(rc, "esc_count_static_noalloc failed")
+        raise EscError(rc, L.esc_last_error(None).decode())
 
 
 # ---------------------------------------------------------------------------

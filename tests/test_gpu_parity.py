@@ -206,19 +206,23 @@ def test_both_centre_kernels_without_temporal(E, monkeypatch, orient):
     run_stream(E, s, 3, 0)
 
 
-@pytest.mark.parametrize("orient,coarse,open_max", [("0", 1, None), ("1", 1, None), ("1", 2000, None),
-                                                    ("1", 1, "16"), ("1", 2000, "0")])
-def test_both_centre_kernels_with_temporal(E, monkeypatch, orient, coarse, open_max):
+@pytest.mark.parametrize("orient,coarse,open_max,open_smem", [
+    ("0", 1, None, None), ("1", 1, None, None), ("1", 2000, None, None),
+    ("1", 1, "16", None), ("1", 2000, "0", None), ("1", 1, None, "16"), ("1", 2000, "64", "8")])
+def test_both_centre_kernels_with_temporal(E, monkeypatch, orient, coarse, open_max, open_smem):
     """All three families through both centre kernels.  The oriented one
     counts the open triads centred at h from the time order of N'(h)
-    (k_open_h), or, for a list longer than ESC_COUNT_OPEN_MAX, classifies
-    each as it visits N'(h); those centred at g1 are counted per chunk by a
-    sweep over N(g1); closed triads take back what those counts gave them.
-    Timestamps divided by `coarse` make many ties (ordered by ID), and the
-    window cuts part of the triads."""
+    (k_open_h: sorted in shared memory up to ESC_COUNT_OPEN_SMEM entries,
+    in the block's global scratch above), or, for a list longer than
+    ESC_COUNT_OPEN_MAX, classifies each as it visits N'(h); those centred at
+    g1 are counted per chunk by a sweep over N(g1); closed triads take back
+    what those counts gave them.  Timestamps divided by `coarse` make many
+    ties (ordered by ID), and the window cuts part of the triads."""
     monkeypatch.setenv("ESC_COUNT_ORIENT", orient)
     if open_max is not None:
         monkeypatch.setenv("ESC_COUNT_OPEN_MAX", open_max)
+    if open_smem is not None:
+        monkeypatch.setenv("ESC_COUNT_OPEN_SMEM", open_smem)
     s = gen.random_small(31, 400, 600, 2, 30, n_batches=3, n_ins=60, n_del=60, membership="zipf", card="zipf")
     if coarse > 1:
         s.initial.timestamps[:] //= coarse
