@@ -551,10 +551,11 @@ COUNT_SRC = os.path.join(ROOT, "paper_2512_21009_gb300", "csrc", "count.cu")
 
 def centre_traffic(args, alg_bytes_per_launch):
     """DRAM bytes (read + write) of one centre-kernel launch: the ratio of
-    DRAM bytes to algorithmic bytes that an ncu capture of a smaller case of
-    the same workload measured, times this launch's algorithmic bytes.  Only
-    when the summary was taken on the kernel source that is built now (its
-    sha256 is recorded there); otherwise None."""
+    DRAM bytes to algorithmic bytes that a one-pass ncu capture of this
+    workload at full size measured (both sides of one step), times this
+    launch's algorithmic bytes.  Only when the summary was taken on the
+    kernel source that is built now (its sha256 is recorded there);
+    otherwise None."""
     import hashlib
     if args.workload != "large_uniform" or not os.path.exists(TRAFFIC_SUMMARY):
         return None, "no capture of this workload"
@@ -571,9 +572,10 @@ def centre_traffic(args, alg_bytes_per_launch):
             src = line.split(":", 1)[1].strip().strip("`")
     if ratio is None or src != sha:
         return None, "the centre kernel changed since the last ncu capture"
-    return ratio * alg_bytes_per_launch, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller case of "
-                                          "this workload on this kernel source, scaled by algorithmic bytes "
-                                          f"({ratio:.3f} DRAM bytes per algorithmic byte; {TRAFFIC_SUMMARY[len(ROOT) + 1:]})")
+    return ratio * alg_bytes_per_launch, ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a one-pass capture of "
+                                          "this workload at full size on this kernel source, as DRAM bytes per "
+                                          "algorithmic byte, times this run's algorithmic bytes per launch "
+                                          f"({ratio:.3f}; {TRAFFIC_SUMMARY[len(ROOT) + 1:]})")
 
 
 # ---------------------------------------------------------------------------
@@ -979,20 +981,43 @@ def _group_cfgs(E, streams, delta, fam, max_bh, max_bi):
 
 
 def _load_group(E, grp, streams, max_bh, max_bi):
-    """Initial hyperedges of every graph, in calls that fit the staging limits."""
-    todo = list(range(len(streams)))
+    """Initial hyperedges of every graph, in calls that fit the staging
+    limits: a graph larger than one call is loaded in pieces, in order, one
+    piece of it per call (with no deletes the ID rule gives fresh IDs
+    upward, so its hyperedges keep the IDs 0..n-1)."""
+    pieces = []
+    for st in streams:
+        off, n, lo, mine = st.initial.offsets, st.initial.n, 0, []
+        while lo < n:
+            hi = lo
+            while hi < n and hi - lo < max_bh and off[hi + 1] - off[lo] <= max_bi:
+                hi += 1
+            if hi == lo:
+                raise SystemExit("bench: a hyperedge has more members than max_batch_incidences")
+            mine.append((lo, hi))
+            lo = hi
+        pieces.append(mine)
+    nxt = [0] * len(streams)
+    todo = [i for i in range(len(streams)) if pieces[i]]
     while todo:
-        call, nh, ni = [], 0, 0
-        while todo:
-            st = streams[todo[0]]
-            if call and (nh + st.initial.n > max_bh or ni + st.initial.nnz > max_bi):
-                break
-            i = todo.pop(0)
-            nh += st.initial.n
-            ni += st.initial.nnz
-            call.append(dict(graph=i, ins_offsets=st.initial.offsets, ins_members=st.initial.members,
-                             ins_timestamps=st.initial.timestamps, del_ids=None))
+        call, nh, ni, rest = [], 0, 0, []
+        for i in todo:
+            st = streams[i]
+            lo, hi = pieces[i][nxt[i]]
+            a, b = int(st.initial.offsets[lo]), int(st.initial.offsets[hi])
+            if call and (nh + hi - lo > max_bh or ni + b - a > max_bi):
+                rest.append(i)
+                continue
+            nh += hi - lo
+            ni += b - a
+            call.append(dict(graph=i, ins_offsets=st.initial.offsets[lo:hi + 1] - a,
+                             ins_members=st.initial.members[a:b], ins_timestamps=st.initial.timestamps[lo:hi],
+                             del_ids=None))
+            nxt[i] += 1
+            if nxt[i] < len(pieces[i]):
+                rest.append(i)
         E.esc_group_apply(grp, call)
+        todo = rest
 
 
 def run_batched(args):
