@@ -1313,7 +1313,7 @@ def run_serving(args):
     by_size = np.argsort([st.initial.n for st in all_streams])[::-1]
     shard_graphs = [list(by_size[k::n_sh]) for k in range(n_sh)]
     reserve = 16 << 30
-    cap_bytes = 120 << 30
+    cap_bytes = 200 << 30
     cuda_streams = [torch.cuda.Stream() for _ in range(n_sh)]
     streams, cfgs, groups, refused = [], [], [], 0
     models, nvs = [], []

@@ -63,8 +63,11 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
 }
 
 // Slot of a pair key; absent keys are added when `add` (the inserted side),
-// otherwise -1 is returned (the deleted side always finds its keys).
-__device__ __forceinline__ int64_t pair_slot(const PairTable& P, uint64_t key, bool add, Scalars* sc) {
+// otherwise -1 is returned (the deleted side always finds its keys).  A key
+// this call added counts one in `fresh` (added to the table's count once
+// per warp: a single counter taking one atomic per new key would serialise).
+__device__ __forceinline__ int64_t pair_slot(const PairTable& P, uint64_t key, bool add, Scalars* sc,
+                                             unsigned long long& fresh) {
     uint64_t s = fmix64(key) & P.mask;
     volatile unsigned long long* kv = P.kv;
     for (uint64_t probe = 0; probe <= P.mask; ++probe) {
@@ -74,7 +77,7 @@ __device__ __forceinline__ int64_t pair_slot(const PairTable& P, uint64_t key, b
             if (!add) break;
             const unsigned long long old = atomicCAS(&P.kv[2 * s], kPairEmpty, (unsigned long long)key);
             if (old == kPairEmpty) {
-                atomicAdd(P.used, 1ull);
+                ++fresh;
                 return int64_t(s);
             }
             if (old == key) return int64_t(s);
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(kPairNT) k_pairs(Store S, Call C, PairTable P)
     }
     int64_t j0 = lo, start0 = P.poff[lo];
     int key = -1;
-    unsigned long long t2 = 0;
+    unsigned long long t2 = 0, fresh = 0;
     for (; p0 < p_end; p0 += 32) {
         // lane i's pair p lies in hyperedge jl, which starts at sl: the
         // boundaries poff[jw + 1 ..] after the window base are read 32 at a
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(kPairNT) k_pairs(Store S, Call C, PairTable P)
             int a, b;
             pair_of(p - sl, ch.k, a, b);
             const uint64_t pk = (uint64_t(uint32_t(ch.m[a])) << 32) | uint64_t(uint32_t(ch.m[b]));
-            const int64_t slot = pair_slot(P, pk, ch.side == 1, C.sc);
+            const int64_t slot = pair_slot(P, pk, ch.side == 1, C.sc, fresh);
             if (slot >= 0) {
                 const unsigned long long inc = (1ull << 40) + (unsigned long long)ch.k;
                 const unsigned long long old = atomicAdd(&P.kv[2 * slot + 1], ch.side ? inc : 0ull - inc);
@@ -329,6 +332,9 @@ __global__ void __launch_bounds__(kPairNT) k_pairs(Store S, Call C, PairTable P)
         start0 = __shfl_sync(0xffffffffu, sl, 31);
     }
     warp_flush(S, key, t2, 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+    if (lane == 0 && fresh) atomicAdd(P.used, fresh);
 }
 
 // Admission, before anything changes: the keys the inserted hyperedges

@@ -455,8 +455,10 @@ def test_large_overlaps(E, families):
 @pytest.mark.parametrize("families", [3, ALL])
 def test_autotune_keeps_counts_exact(E, families):
     """The autotuner times every launch shape (and, without the temporal
-    family, restricted lists) on a sample of live hyperedges and keeps the
-    fastest; counts are untouched by it and stay exact afterwards."""
+    family, restricted lists), then the neighbourhood size from which N(h)
+    gets a table and filter and the per-pair side weight, on a sample of
+    live hyperedges, and keeps the fastest of each; counts are untouched by
+    it and stay exact afterwards, under the chosen strategy."""
     s = gen.random_small(31, 500, 700, 2, 12, membership="zipf", n_batches=2, n_ins=60, n_del=60)
     init = s.initial
     og = OracleHypergraph(s.n_vertices, init.offsets, init.members, init.timestamps)
@@ -469,6 +471,8 @@ def test_autotune_keeps_counts_exact(E, families):
     assert all(m >= 0 for m in res["ms"][:4])
     if families & 4:
         assert res["restricted"] == 0 and all(m == -1 for m in res["ms"][4:])
+    assert res["table_from"] in (256, 512, 1024) and res["m1_pct"] in (50, 100, 200)
+    assert all(m >= 0 for m in res["ms_table"]) and all(m >= 0 for m in res["ms_m1"])
     assert_counts_equal(g.counts(), before, "after tuning")
     live = GpuLive(init.n, init.timestamps)
     for b in s.batches:
