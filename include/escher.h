@@ -89,6 +89,11 @@
  *                             esc_tune_result.center_shape (0..3).
  *   ESC_CALL_GRAPH=1          graph launch on from creation (as
  *                             esc_set_graph_launch).
+ *   ESC_STATS_JSONL=path      append one JSON line per call of every graph
+ *                             or group created afterwards: call number,
+ *                             batches, inserts, deletes, status, kernels
+ *                             launched, and, with profiling on, the stage
+ *                             times and counter work of esc_batch_stats.
  */
 #ifndef ESCHER_H
 #define ESCHER_H
@@ -111,7 +116,9 @@ typedef enum {
                                   no kernel of this build waits on the device,
                                   so no call returns it)                      */
     ESC_ERR_CUDA = 6,          /* a CUDA runtime call failed                 */
-    ESC_ERR_BUSY = 7           /* a server's queue is full; nothing was kept */
+    ESC_ERR_BUSY = 7,          /* a server's queue is full; nothing was kept */
+    ESC_ERR_INTERNAL = 8       /* debug mode: a store invariant was found
+                                  broken after the call (esc_config.debug)   */
 } esc_status;
 
 typedef enum {
@@ -154,7 +161,13 @@ typedef struct {
     int64_t max_batch_incidences;   /* inserted members of one call, at most       */
     uint32_t families;              /* ESC_FAMILY_* bits of the families to keep   */
     int64_t delta;                  /* temporal window (timestamp units)           */
-    int32_t debug;                  /* 0; reserved                                  */
+    int32_t debug;                  /* 1: after every successful call, check the
+                                       store's invariants on the device (the two
+                                       views agree, members sorted and in range,
+                                       degrees within slabs, live counts); a
+                                       violation fails the call with
+                                       ESC_ERR_INTERNAL.  Reads the whole store:
+                                       for tests.  0: off                          */
     int64_t capacity_vertex_pairs;  /* ESC_FAMILY_VERTEX12: distinct vertex pairs
                                        (pairs of members of one hyperedge) the
                                        graph may hold at once; 0 otherwise.  A

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libescher.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "store.cu", "count.cu", "tables.cu", "noalloc.cu", "serve.cu", "pairs.cu"]
+SOURCES = ["api.cu", "store.cu", "count.cu", "tables.cu", "noalloc.cu", "serve.cu", "pairs.cu", "debug.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

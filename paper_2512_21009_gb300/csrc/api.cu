@@ -52,6 +52,9 @@ struct Engine {
     int64_t inc_cap = 0;  // incidences of all graphs (capacity)
     Store S{};
     std::vector<void*> allocs;
+    unsigned long long* d_dbg = nullptr;  // debug mode: per-graph sums of the invariant check
+    FILE* jsonl = nullptr;                // ESC_STATS_JSONL: one record per call
+    int64_t n_calls = 0;
     // call staging
     Call C{};
     int64_t max_ins = 0, max_nnz = 0;
@@ -119,6 +122,7 @@ struct Engine {
 
     ~Engine() {
         if (st) cudaStreamSynchronize(st);
+        if (jsonl) fclose(jsonl);
         for (void* p : allocs) cudaFree(p);
         if (h_batches) cudaFreeHost(h_batches);
         if (h_lo) cudaFreeHost(h_lo);
@@ -164,6 +168,7 @@ static esc_status check_cfg(const esc_config* c, bool per_graph_only) {
     if (c->families == 0 || (c->families & ~15u)) return ESC_ERR_INVALID_ARG;
     if ((c->families & kFamV) && (c->families & kFamV12)) return ESC_ERR_INVALID_ARG;
     if (c->delta < 0) return ESC_ERR_INVALID_ARG;
+    if (c->debug != 0 && c->debug != 1) return ESC_ERR_INVALID_ARG;
     return ESC_OK;
 }
 
@@ -404,6 +409,9 @@ static esc_status build_engine(Engine* E, const esc_config& shared, int32_t G, c
         ESC_CU(pair_table_init(&E->pairs, pm, pair_cap, E->max_ins, st), "pair table init");
     }
     ESC_CU(upload_tables(st), "tables");
+    if (shared.debug) ESC_CU(E->alloc(&E->d_dbg, 3 * int64_t(G)), "alloc");
+    if (const char* env = getenv("ESC_STATS_JSONL"))
+        if (*env) E->jsonl = fopen(env, "a");
     for (auto& e : E->ev) ESC_CU(cudaEventCreate(&e), "event");
     for (auto& e : E->cev) ESC_CU(cudaEventCreate(&e), "event");
     E->cs.max_cev = 16;
@@ -755,9 +763,36 @@ static esc_status run_call(Engine* E, int n, const esc_batch* bs, const int32_t*
     E->last.alg_closed = int64_t(E->h_sc->stats[13]);
     E->last.alg_build = int64_t(E->h_sc->stats[14]);
     E->last.alg_store = int64_t(E->h_sc->stats[15]);
-    if (E->h_sc->status != 0) {
-        E->err = describe(*E->h_sc);
-        return esc_status(E->h_sc->status);
+    int status = E->h_sc->status;
+    if (status == 0 && E->d_dbg) {
+        // debug mode: the store's invariants after the call
+        ESC_CU(cudaMemsetAsync(E->d_sc, 0, sizeof(Scalars), st), "memset");
+        ESC_CU(store_debug_check(E->S, E->d_sc, E->d_dbg, E->sm_count, st), "debug check");
+        ESC_CU(cudaMemcpyAsync(E->h_sc, E->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st), "status");
+        ESC_CU(cudaStreamSynchronize(st), "sync");
+        status = E->h_sc->status;
+    }
+    ++E->n_calls;
+    if (E->jsonl) {
+        const esc_batch_stats& L = E->last;
+        fprintf(E->jsonl,
+                "{\"call\": %lld, \"batches\": %d, \"inserts\": %lld, \"deletes\": %lld, \"status\": %d, "
+                "\"launches\": %lld",
+                (long long)E->n_calls, n, (long long)tot_ins, (long long)tot_del, status, (long long)lc.total);
+        if (prof)
+            fprintf(E->jsonl,
+                    ", \"ms_total\": %.4f, \"ms_ingest\": %.4f, \"ms_count_del\": %.4f, \"ms_store\": %.4f, "
+                    "\"ms_count_ins\": %.4f, \"ms_center\": %.4f, \"triads\": %lld, \"work\": [%lld, %lld, %lld, "
+                    "%lld, %lld, %lld]",
+                    L.ms_total, L.ms_ingest, L.ms_count_del, L.ms_store, L.ms_count_ins, L.ms_center,
+                    (long long)L.triads, (long long)L.work[0], (long long)L.work[1], (long long)L.work[2],
+                    (long long)L.work[3], (long long)L.work[4], (long long)L.work[5]);
+        fprintf(E->jsonl, "}\n");
+        fflush(E->jsonl);
+    }
+    if (status != 0) {
+        E->err = status == kErrInternal ? "store invariant check failed: " + describe(*E->h_sc) : describe(*E->h_sc);
+        return esc_status(status);
     }
     for (int b = 0; b < n; ++b) {
         const esc_batch& x = bs[b];

@@ -36,7 +36,7 @@ constexpr uint32_t kFamH = 1u, kFamV = 2u, kFamT = 4u, kFamV12 = 8u;
 
 // status codes, identical to esc_status
 constexpr int kOk = 0, kErrInvalid = 1, kErrNotFound = 2, kErrNoMem = 3, kErrUnsupported = 4,
-              kErrTimeout = 5, kErrCuda = 6;
+              kErrTimeout = 5, kErrCuda = 6, kErrInternal = 8;
 // internal: the neighbour lists of a side needed more count runs than a
 // fixed launch sequence holds; nothing changed and the call is run again
 // with runs planned on the host (never returned to a caller)

@@ -159,6 +159,9 @@ cudaError_t pairs_check(const PairTable& P, const Call& C, cudaStream_t st, Laun
 cudaError_t pairs_update(const Store& S, const Call& C, const PairTable& P, int sm_count, cudaStream_t st,
                          LaunchCounter& lc);
 
+// debug.cu: the store's invariants (esc_config.debug); acc: 3 * n_graphs words
+cudaError_t store_debug_check(const Store& S, Scalars* sc, unsigned long long* acc, int sm_count, cudaStream_t st);
+
 // Largest neighbour-entry count sum(deg) of a changed hyperedge the counter
 // accepts with the given shape.
 inline int64_t count_max_u(const CountShape& sh) {

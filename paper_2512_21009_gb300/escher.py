@@ -27,7 +27,8 @@ FAMILY_VERTEX12 = 8
 TRIAD_HYPEREDGE, TRIAD_VERTEX, TRIAD_TEMPORAL = 0, 1, 2
 N_CLASSES = {TRIAD_HYPEREDGE: 30, TRIAD_VERTEX: 3, TRIAD_TEMPORAL: 96}
 STATUS = {0: "ESC_OK", 1: "ESC_ERR_INVALID_ARG", 2: "ESC_ERR_NOT_FOUND", 3: "ESC_ERR_OUT_OF_MEMORY",
-          4: "ESC_ERR_UNSUPPORTED", 5: "ESC_ERR_TIMEOUT", 6: "ESC_ERR_CUDA", 7: "ESC_ERR_BUSY"}
+          4: "ESC_ERR_UNSUPPORTED", 5: "ESC_ERR_TIMEOUT", 6: "ESC_ERR_CUDA", 7: "ESC_ERR_BUSY",
+          8: "ESC_ERR_INTERNAL"}
 ESC_ERR_BUSY = 7
 
 # every symbol the header declares (checked by the CPU test suite)
@@ -641,9 +642,9 @@ def esc_count_static_noalloc(n_vertices: int, offsets, members, timestamps, fami
 
 def make_config(n_vertices: int, capacity_hyperedges: int, capacity_incidences: int,
                 max_batch_hyperedges: int, max_batch_incidences: int, families: int,
-                delta: int = 0, capacity_vertex_pairs: int = 0) -> esc_config:
+                delta: int = 0, capacity_vertex_pairs: int = 0, debug: int = 0) -> esc_config:
     return esc_config(int(n_vertices), int(capacity_hyperedges), int(capacity_incidences),
-                      int(max_batch_hyperedges), int(max_batch_incidences), int(families), int(delta), 0,
+                      int(max_batch_hyperedges), int(max_batch_incidences), int(families), int(delta), int(debug),
                       int(capacity_vertex_pairs))
 
 
@@ -653,12 +654,12 @@ class Graph:
     def __init__(self, n_vertices: int, offsets=None, members=None, timestamps=None, *,
                  capacity_hyperedges: int, capacity_incidences: int, max_batch_hyperedges: int,
                  max_batch_incidences: int, families: int, delta: int = 0, stream=None,
-                 capacity_vertex_pairs: int = 0):
+                 capacity_vertex_pairs: int = 0, debug: int = 0):
         self.n_vertices = int(n_vertices)
         self.families = families
         self.delta = int(delta)
         self.cfg = make_config(n_vertices, capacity_hyperedges, capacity_incidences, max_batch_hyperedges,
-                               max_batch_incidences, families, delta, capacity_vertex_pairs)
+                               max_batch_incidences, families, delta, capacity_vertex_pairs, debug)
         if offsets is None:
             offsets = np.zeros(1, np.int64)
             members = np.zeros(0, np.int32)

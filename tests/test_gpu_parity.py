@@ -566,3 +566,40 @@ def test_hub_vertex_lists_rewritten_by_blocks(E):
         assert np.array_equal(ids_g, ids_o), f"batch {k}"
         assert_store_equal(g, og)
     g.close()
+
+
+def test_debug_mode_checks_the_store_after_every_call(E, tmp_path, monkeypatch):
+    """esc_config.debug = 1 checks the store's invariants on the device after
+    every call (the two views agree, members sorted and in range, degrees
+    within their slabs, live counts); a stream with hub vertices and
+    single-member hyperedges passes every check with counts and store equal
+    to the oracle's.  ESC_STATS_JSONL records one line per call.  A debug
+    value other than 0 or 1 is refused."""
+    import json
+    path = tmp_path / "calls.jsonl"
+    monkeypatch.setenv("ESC_STATS_JSONL", str(path))
+    s = gen.random_small(33, 300, 400, 1, 20, n_batches=3, n_ins=80, n_del=80, membership="zipf", card="zipf")
+    init = s.initial
+    delta = int(init.timestamps[-1] // 3)
+    og = OracleHypergraph(s.n_vertices, init.offsets, init.members, init.timestamps)
+    g = E.Graph(s.n_vertices, init.offsets, init.members, init.timestamps, families=ALL, delta=delta, debug=1,
+                **caps_for(s.n_vertices, 2000, 20000, 1000, 20000))
+    g.set_profiling(True)
+    live = GpuLive(init.n, init.timestamps)
+    for b in s.batches:
+        dels_o = og.resolve_ranks(b.del_ranks)
+        dels_g = live.resolve(b.del_ranks)
+        ids_o = og.apply_batch(b.inserts.offsets, b.inserts.members, b.inserts.timestamps, dels_o)
+        ids_g = g.apply_batch(b.inserts.offsets, b.inserts.members, b.inserts.timestamps, dels_g.astype(np.int32))
+        assert np.array_equal(ids_g, ids_o)
+        live.apply(dels_g, ids_g, b.inserts.timestamps)
+        assert_counts_equal(g.counts(), O.counts(og, ALL, delta), "debug mode")
+        assert_store_equal(g, og)
+    g.close()
+    rec = [json.loads(line) for line in open(path)]
+    assert len(rec) >= 1 + len(s.batches)
+    for r, b in zip(rec[-len(s.batches):], s.batches):
+        assert r["status"] == 0 and r["inserts"] == b.inserts.n and r["deletes"] == len(b.del_ranks)
+        assert r["launches"] > 0 and r["ms_total"] > 0 and len(r["work"]) == 6
+    with pytest.raises(E.EscError):
+        E.Graph(10, None, None, None, families=1, debug=2, **caps_for(10, 64, 1024, 64, 1024))
