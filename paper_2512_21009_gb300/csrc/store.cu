@@ -565,6 +565,7 @@ __global__ void k_vfilter(Store S, Call C) {
 // safe: every thread has loaded its entries of a chunk before the scan's
 // barrier, and the chunk's writes land below the chunk's end.
 constexpr int kVNT = 512, kVPer = 8, kVChunk = kVNT * kVPer;
+static_assert(kVPer == 8 && (1 << kMinSlabLog) % kVPer == 0, "two 16-byte loads per thread, slab-aligned");
 
 __global__ void __launch_bounds__(kVNT) k_vfilter_big(Store S, Call C) {
     __shared__ int wsum[kVNT / 32];
@@ -586,10 +587,18 @@ __global__ void __launch_bounds__(kVNT) k_vfilter_big(Store S, Call C) {
                 int32_t val[kVPer];
                 unsigned keep = 0;
                 int cnt = 0;
+                const int e0 = base + tid * kVPer;
+                if (e0 + kVPer <= deg) {
+                    // every slab offset is a multiple of 8 slots (slabs are
+                    // 8 << c slots, handed out whole), and so is e0: two
+                    // aligned 16-byte loads
+                    const int4* src = reinterpret_cast<const int4*>(S.vp.arena + off + e0);
+                    const int4 a = src[0], b = src[1];
+                    val[0] = a.x; val[1] = a.y; val[2] = a.z; val[3] = a.w;
+                    val[4] = b.x; val[5] = b.y; val[6] = b.z; val[7] = b.w;
+                } else {
 #pragma unroll
-                for (int i = 0; i < kVPer; ++i) {
-                    const int e = base + tid * kVPer + i;
-                    val[i] = e < deg ? S.vp.arena[off + e] : 0;
+                    for (int i = 0; i < kVPer; ++i) val[i] = e0 + i < deg ? S.vp.arena[off + e0 + i] : 0;
                 }
 #pragma unroll
                 for (int i = 0; i < kVPer; ++i) {
