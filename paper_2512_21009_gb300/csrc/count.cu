@@ -1617,26 +1617,34 @@ __device__ __forceinline__ int64_t sat_sub(int64_t a, int64_t b) { return a < IN
 constexpr int kOhNT = 1024;
 constexpr int kOhMax = 8192;   // entries of N'(h) sorted in shared memory, at most
 constexpr int kOhBig = 65536;  // entries sorted in the block's global scratch, at most
+// short lists (at most kOsMax entries, most of them on sparse graphs) go to
+// kOsNT-thread blocks with shared arrays for kOsMax entries, several per SM:
+// a sort over a few hundred entries then waits at barriers of 8 warps, not 32
+constexpr int kOsNT = 256;
+constexpr int kOsMax = 1024;
 
-struct SmemOH {
+template <int NT, int MAXN>
+struct SmemOHT {
     Tables tb;
-    int64_t t[kOhMax];         // timestamp of each entry (sorted with id and pay)
-    int32_t id[kOhMax];
-    int32_t pay[kOhMax];       // x | C << 15
-    uint32_t key[kOhMax];      // x << ksh | place << 1 | C, sorted
-    uint16_t p1[kOhMax + 1];   // entries with C = 1 among the first i, in (t, ID) order
-    uint16_t pc[kOhMax + 1];   // the same in key order
+    int64_t t[MAXN];           // timestamp of each entry (sorted with id and pay)
+    int32_t id[MAXN];
+    int32_t pay[MAXN];         // x | C << 15
+    uint32_t key[MAXN];        // x << ksh | place << 1 | C, sorted
+    uint16_t p1[MAXN + 1];     // entries with C = 1 among the first i, in (t, ID) order
+    uint16_t pc[MAXN + 1];     // the same in key order
     unsigned long long cnt[24];
-    int wsum[kOhNT / 32];
+    int wsum[NT / 32];
     long long item;
     int n, s_pos, l0, r1;
 };
+using SmemOH = SmemOHT<kOhNT, kOhMax>;
+using SmemOS = SmemOHT<kOsNT, kOsMax>;
 
 // out[i] = number of the first i of n entries with bit(i) set, and out[n]
-template <typename PT, typename F>
+template <int NT, typename PT, typename F>
 __device__ __forceinline__ void oh_prefix(F bit, PT* out, int n, int* wsum) {
     const int tid = threadIdx.x, lane = lane_id(), w = warp_id();
-    const int per = (n + kOhNT - 1) / kOhNT;
+    const int per = (n + NT - 1) / NT;
     const int q0 = tid * per, q1 = min(q0 + per, n);
     int c = 0;
     for (int q = q0; q < q1; ++q) c += bit(q);
@@ -1649,14 +1657,14 @@ __device__ __forceinline__ void oh_prefix(F bit, PT* out, int n, int* wsum) {
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
     if (w == 0) {
-        int x = wsum[lane];  // kOhNT / 32 == 32 warps
+        int x = lane < NT / 32 ? wsum[lane] : 0;
         const int own = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += v;
         }
-        wsum[lane] = x - own;
+        if (lane < NT / 32) wsum[lane] = x - own;
         if (lane == 31) out[n] = PT(x);
     }
     __syncthreads();
@@ -1693,14 +1701,14 @@ __device__ __forceinline__ void oh_add(unsigned (&c)[24], int cas, bool later, i
 // (T, I, P), in shared memory or the block's global scratch: sorted, ranked
 // and counted into s.cnt, then added to graph g's temporal bins.  ksh: the
 // key shift (places < 1 << (ksh - 1)).
-template <typename PT>
-__device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32_t* I, int32_t* P, uint32_t* K,
-                         PT* P1, PT* PC, int ksh, int kh, int64_t th, int32_t h, int g) {
+template <int NT, int MAXN, typename PT>
+__device__ void oh_count(SmemOHT<NT, MAXN>& s, const CountArgs& A, int n, int64_t* T, int32_t* I, int32_t* P,
+                         uint32_t* K, PT* P1, PT* PC, int ksh, int kh, int64_t th, int32_t h, int g) {
     const int tid = threadIdx.x, lane = lane_id();
     const int64_t delta = A.S.delta;
     int n2 = 2;
     while (n2 < n) n2 <<= 1;
-    for (int q = n + tid; q < n2; q += kOhNT) {
+    for (int q = n + tid; q < n2; q += NT) {
         T[q] = INT64_MAX;
         I[q] = INT_MAX;
         P[q] = 0;
@@ -1709,7 +1717,7 @@ __device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32
     // bitonic sort by (t, ID)
     for (int k = 2; k <= n2; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int u = tid; u < (n2 >> 1); u += kOhNT) {
+            for (int u = tid; u < (n2 >> 1); u += NT) {
                 const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
                 const int64_t ta = T[a], tb = T[b];
                 const int32_t ia = I[a], ib = I[b];
@@ -1725,13 +1733,13 @@ __device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32
             }
             __syncthreads();
         }
-    for (int q = tid; q < n2; q += kOhNT)
+    for (int q = tid; q < n2; q += NT)
         K[q] = q < n ? (uint32_t(P[q] & 0x7fff) << ksh) | (uint32_t(q) << 1) | uint32_t((P[q] >> 15) & 1) : UINT32_MAX;
-    oh_prefix<PT>([&](int q) { return (P[q] >> 15) & 1; }, P1, n, s.wsum);
+    oh_prefix<NT, PT>([&](int q) { return (P[q] >> 15) & 1; }, P1, n, s.wsum);
     // bitonic sort of the keys
     for (int k = 2; k <= n2; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int u = tid; u < (n2 >> 1); u += kOhNT) {
+            for (int u = tid; u < (n2 >> 1); u += NT) {
                 const int a = ((u & ~(j - 1)) << 1) | (u & (j - 1)), b = a + j;
                 const uint32_t ka = K[a], kb = K[b];
                 if ((ka > kb) == ((a & k) == 0)) {
@@ -1741,7 +1749,7 @@ __device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32
             }
             __syncthreads();
         }
-    oh_prefix<PT>([&](int q) { return int(K[q] & 1u); }, PC, n, s.wsum);
+    oh_prefix<NT, PT>([&](int q) { return int(K[q] & 1u); }, PC, n, s.wsum);
     if (tid == 0) {
         // h's place, the first member within delta before it, the end of
         // the members within delta after it
@@ -1787,7 +1795,7 @@ __device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32
     unsigned c[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) c[k] = 0;
-    for (int e = tid; e < n; e += kOhNT) {
+    for (int e = tid; e < n; e += NT) {
         const int xe = P[e] & 0x7fff;
         const int ce = (P[e] >> 15) & 1;
         const int xs = kh - xe;  // the x of a partner that completes h
@@ -1840,15 +1848,20 @@ __device__ void oh_count(SmemOH& s, const CountArgs& A, int n, int64_t* T, int32
     }
 }
 
-__global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
+// SHORT: the kOsNT-thread variant, for lists of at most short_cap entries
+// (before the changed g < h are dropped); the other takes the longer ones.
+// Both walk all of the run's changed h, each through its own queue.
+template <int NT, int MAXN, int MINB, bool SHORT>
+__global__ void __launch_bounds__(NT, MINB) k_open_h(CountArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemOH& s = *reinterpret_cast<SmemOH*>(smem_raw);
+    SmemOHT<NT, MAXN>& s = *reinterpret_cast<SmemOHT<NT, MAXN>*>(smem_raw);
     const Store& S = A.S;
     if (A.sc->gate) return;
     const CountScratch& cs = A.cs;
     const int tid = threadIdx.x;
     const RunRange R = run_of(A);
-    const int smem_max = min(kOhMax, cs.oh_smem);
+    const int short_cap = min(kOsMax, cs.oh_smem);
+    const int smem_max = min(MAXN, cs.oh_smem);
     const int64_t gstride = cs.oh_cap + 1;
     int64_t* gT = cs.oh_t + blockIdx.x * gstride;
     int32_t* gI = cs.oh_i + blockIdx.x * gstride;
@@ -1856,11 +1869,12 @@ __global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
     uint32_t* gK = cs.oh_k + blockIdx.x * gstride;
     uint32_t* gP1 = cs.oh_p1 + blockIdx.x * gstride;
     uint32_t* gPC = cs.oh_pc + blockIdx.x * gstride;
-    load_tables(s.tb, kOhNT);
+    unsigned long long* queue = SHORT ? &A.sc->qos[A.side] : &A.sc->qoh[A.side];
+    load_tables(s.tb, NT);
     for (;;) {
         __syncthreads();
         if (tid == 0) {
-            s.item = (long long)atomicAdd(&A.sc->qoh[A.side], 1ull);
+            s.item = (long long)atomicAdd(queue, 1ull);
             s.n = 0;
         }
         if (tid < 24) s.cnt[tid] = 0;
@@ -1869,6 +1883,7 @@ __global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
         const int64_t i = cs.order[s.item];
         const int nn = cs.nh_n[i];
         if (nn < 2) continue;
+        if (SHORT != (nn <= short_cap)) continue;  // the other variant's
         const int32_t h = A.changed[A.lo + i];
         const int g = A.changed_g ? A.changed_g[A.lo + i] : 0;
         const int kh = S.h_card[h];
@@ -1877,7 +1892,7 @@ __global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
         // N'(h), into shared memory while it fits, else into the block's
         // global scratch while that fits
         auto load = [&](int64_t* T, int32_t* I, int32_t* P, int cap) {
-            for (int q = tid; q < nn; q += kOhNT) {
+            for (int q = tid; q < nn; q += NT) {
                 const int32_t gg = cs.nh_g[base + q];
                 const uint64_t xv = cs.nh_xv[base + q];
                 if (gg < h && ((xv >> 31) & 1u)) continue;  // changed below h: its triads belong to gg
@@ -1894,14 +1909,16 @@ __global__ void __launch_bounds__(kOhNT, 1) k_open_h(CountArgs A) {
         load(s.t, s.id, s.pay, smem_max);
         const int n = s.n;
         if (n < 2) continue;
-        if (n <= smem_max) {
-            oh_count<uint16_t>(s, A, n, s.t, s.id, s.pay, s.key, s.p1, s.pc, 14, kh, th, h, g);
-        } else if (n <= cs.oh_max && n <= cs.oh_cap) {
+        if (n > cs.oh_max) {
+            if (tid == 0) cs.nh_flag[i] |= 2;  // left to the centre kernel
+        } else if (n <= smem_max) {
+            oh_count<NT, MAXN, uint16_t>(s, A, n, s.t, s.id, s.pay, s.key, s.p1, s.pc, 14, kh, th, h, g);
+        } else if (!SHORT && n <= cs.oh_cap) {
             __syncthreads();
             if (tid == 0) s.n = 0;
             __syncthreads();
             load(gT, gI, gP, int(cs.oh_cap));
-            oh_count<uint32_t>(s, A, n, gT, gI, gP, gK, gP1, gPC, 17, kh, th, h, g);
+            oh_count<NT, MAXN, uint32_t>(s, A, n, gT, gI, gP, gK, gP1, gPC, 17, kh, th, h, g);
         } else if (tid == 0) {
             cs.nh_flag[i] |= 2;  // left to the centre kernel
         }
@@ -1965,6 +1982,8 @@ __device__ __forceinline__ int triple_size_o(int xh1, int32_t vf1, int xh2, int3
     return triple_size(xh1, vf1, xh2, vf2, g1m, k1, g2mem, k2, hmem, kh, hI, nI, slow);
 }
 
+constexpr int kXG = 64;  // |h & g1| values whose place in the sweep's x order is tabulated
+
 template <int NT_C, int T1_S>
 struct SmemCO {
     static constexpr int NW_C = NT_C / 32;
@@ -1999,6 +2018,7 @@ struct SmemCO {
             int32_t ot_i[LCH], ox_i[LCH], ox_x[LCH];
             int32_t pt[LCH], px[LCH];
             int32_t dT[8][LCH + 1], dX[8][LCH + 1];
+            uint8_t xg[2][kXG];      //   the h with |h & g1| = x (x < kXG): [xg[0][x], xg[1][x]) of the x order
             int n_before;            //   the chunk's h before g1 in (t, ID) order
         } t;
     } u2;
@@ -2668,6 +2688,16 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                             }
                             const unsigned bef = __ballot_sync(0xffffffffu, in && (tl < ts1 || (tl == ts1 && il < g1)));
                             if (lane == 0) T.n_before = __popc(bef);
+                            // where each small x starts and ends in the x order
+                            for (int x = lane; x < kXG; x += 32) {
+                                int lo = 0, hi = 0;
+                                for (int m = 0; m < nh; ++m) {
+                                    lo += s.hx[m] < x ? 1 : 0;
+                                    hi += s.hx[m] <= x ? 1 : 0;
+                                }
+                                T.xg[0][x] = uint8_t(lo);
+                                T.xg[1][x] = uint8_t(hi);
+                            }
                         }
                         for (int i = tid; i < 8 * (LCH + 1); i += NT_C) {
                             (&T.dT[0][0])[i] = 0;
@@ -2763,7 +2793,10 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                             ranges(T.dT, T.ot_t, T.ot_i, 0, nh, s1);
                             const int xs = k1 - x;
                             int ga = 0, gb = nh;  // the h with |h & g1| = xs
-                            {
+                            if (xs >= 0 && xs < kXG) {
+                                ga = T.xg[0][xs];
+                                gb = T.xg[1][xs];
+                            } else {
                                 int lo = 0, hi = nh;
                                 while (lo < hi) {
                                     const int mid = (lo + hi) >> 1;
@@ -3037,6 +3070,7 @@ __global__ void k_run_begin(Scalars* sc, int side) {
     sc->r_used[side] = 0;
     sc->qnh[side] = 0;
     sc->qoh[side] = 0;
+    sc->qos[side] = 0;
     sc->queue[side] = 0;
     sc->n_d[side] = 0;
     sc->items[side] = 0;
@@ -3195,7 +3229,10 @@ void count_prepare() {
                          int(sizeof(SmemC<512, 4096>)));
     cudaFuncSetAttribute(k_center<256, 2048, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(SmemC<256, 2048>)));
-    cudaFuncSetAttribute(k_open_h, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(SmemOH)));
+    cudaFuncSetAttribute(k_open_h<kOhNT, kOhMax, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemOH)));
+    cudaFuncSetAttribute(k_open_h<kOsNT, kOsMax, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(SmemOS)));
 #define ESC_CO_ATTR(NT, TS, MB)                                                                          \
     cudaFuncSetAttribute(k_center_o<NT, TS, MB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                          int(sizeof(SmemCO<NT, TS>)));                                                      \
@@ -3233,7 +3270,10 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     k_scan_apply<int32_t><<<gn, kScanNT, 0, st>>>(cs.oflag, n, n_run, cs.block_sums, cs.opre);
     k_order_place<<<capped(blocks_for(nmax, 256)), 256, 0, st>>>(A);
     k_nh_build<<<cs.n_cta_nh, NT_NH, sizeof(SmemNH), st>>>(A);
-    if (orient && temp) k_open_h<<<cs.n_cta_c, kOhNT, sizeof(SmemOH), st>>>(A);
+    if (orient && temp) {
+        k_open_h<kOsNT, kOsMax, 4, true><<<cs.n_cta_c * 4, kOsNT, sizeof(SmemOS), st>>>(A);
+        k_open_h<kOhNT, kOhMax, 1, false><<<cs.n_cta_c, kOhNT, sizeof(SmemOH), st>>>(A);
+    }
     cudaMemsetAsync(cs.block_sums, 0, sizeof(int64_t) * kOrderBuckets, st);
     k_dsort_count<<<ge, 256, 0, st>>>(A);
     k_dsort_scan<<<1, 32, 0, st>>>(A);
@@ -3274,7 +3314,7 @@ static cudaError_t count_run(const Store& S, Scalars* sc, const int32_t* changed
     }
     if (timed) cudaEventRecord(cs.cev[2 * (*cs.n_cev)++ + 1], st);
     k_d_clean<<<ge, 256, 0, st>>>(A);
-    lc.total += (orient ? 23 : 22) + (orient && temp ? 1 : 0);
+    lc.total += (orient ? 23 : 22) + (orient && temp ? 2 : 0);
     lc.count += 2;
     return cudaGetLastError();
 }

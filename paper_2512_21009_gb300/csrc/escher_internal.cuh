@@ -75,7 +75,8 @@ struct Scalars {
     int32_t need_v[kNumClasses];
     unsigned long long queue[2];  // centre work queues (deleted side, inserted side)
     unsigned long long qnh[2];    // neighbourhood-build queues
-    unsigned long long qoh[2];    // queues of the temporal open-at-h counts
+    unsigned long long qoh[2];    // queues of the temporal open-at-h counts (long lists)
+    unsigned long long qos[2];    // ... and of the short lists
     int64_t items[2];     // centre work items
     int32_t n_d[2];       // distinct candidate neighbours g1 of one count run
     unsigned long long r_used[2];  // int32 entries of the restricted-list pool taken in this run
