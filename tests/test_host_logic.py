@@ -146,3 +146,31 @@ def test_vertex_types_1_2_from_pair_statistics_match_the_oracle():
         off2 = np.concatenate([[0], np.cumsum([len(e) for e in keep])]).astype(np.int64)
         mem2 = np.concatenate([np.array(e, np.int32) for e in keep])
         assert acc == int(O.count_vertex(off2, mem2, nv, "literal")[1])
+
+
+def test_group_loading_in_pieces_keeps_every_graph_whole_and_in_order():
+    """bench's group loader: a graph larger than one call's limits is loaded
+    in pieces, in order, at most one piece of a graph per call, every call
+    within both limits (hyperedges, members), and each graph's hyperedges
+    arrive exactly once (so under the ID rule they keep IDs 0..n-1)."""
+    import types
+    import bench
+    calls = []
+    fake = types.SimpleNamespace(esc_group_apply=lambda grp, call: calls.append(call))
+    ms = gen.resident_graphs(seed=5, n_graphs=12, e_hi=3e4)
+    bench._load_group(fake, None, ms.graphs, 5000, 60000)
+    got = {}
+    for c in calls:
+        assert sum(len(x["ins_offsets"]) - 1 for x in c) <= 5000
+        assert sum(len(x["ins_members"]) for x in c) <= 60000
+        gs = [x["graph"] for x in c]
+        assert len(gs) == len(set(gs))
+        for x in c:
+            got.setdefault(x["graph"], []).append(x)
+    assert len(calls) > len(ms.graphs) // 2 and max(st.initial.n for st in ms.graphs) > 5000
+    for i, st in enumerate(ms.graphs):
+        parts = got[i]
+        assert np.array_equal(np.concatenate([x["ins_members"] for x in parts]), st.initial.members)
+        assert np.array_equal(np.concatenate([x["ins_timestamps"] for x in parts]), st.initial.timestamps)
+        assert np.array_equal(np.concatenate([np.diff(x["ins_offsets"]) for x in parts]),
+                              np.diff(st.initial.offsets))
