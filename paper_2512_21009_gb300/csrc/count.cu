@@ -2709,29 +2709,46 @@ __global__ void __launch_bounds__(NT_C, MINB) k_center_o(CountArgs A) {
                         // order -- 0 and s1 -- are kept per thread and added
                         // once (the end nh needs nothing: no prefix reads it)
                         int at0[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                        for (int q = tid; q < n1; q += NT_C) {
-                            const int sl = T1.list[q];
-                            const int32_t f = T1.keys[sl];
-                            const int32_t meta = lk[q];
-                            const int x = int(T1.vals[sl]);
-                            const int C = (meta & 0x7fffffff) > x ? 1 : 0;
-                            const int64_t tf = lts[q];
-                            if (meta < 0) {
-                                for (int l = 0; l < nh; ++l) {
-                                    const int32_t h = s.hh[l];
-                                    if (f <= h) continue;  // f = h, or a changed f < h: its triads belong to f
-                                    const int xh1 = s.hx[l];
-                                    const int m = (s.hk[l] > xh1 ? 1 : 0) | (x != k1 - xh1 ? 2 : 0) | (C << 2) | 8 | 16;
-                                    ++acc.n_tri;
-                                    if (want_h) {
-                                        const int c = s.tb.cls30[m];
-                                        if (c >= 0) atomicAdd(&hist[c], 1u);
-                                    }
-                                    const int c96 = temporal_class(s.tb, m, T.hts[l], ts1, tf, h, g1, f, delta);
-                                    if (c96 >= 0) atomicAdd(&T.th[wid][c96], 1u);
-                                }
-                                continue;
+                        // a warp takes 32 consecutive f; a changed f is taken by the
+                        // whole warp at once, a lane per h (a lane looping over
+                        // the chunk's h alone would hold its warp)
+                        for (int q0 = wid * 32; q0 < n1; q0 += NT_C) {
+                            const int q = q0 + lane;
+                            const bool act = q < n1;
+                            int32_t f = 0, meta = 0;
+                            int x = 0, C = 0;
+                            int64_t tf = 0;
+                            if (act) {
+                                const int sl = T1.list[q];
+                                f = T1.keys[sl];
+                                meta = lk[q];
+                                x = int(T1.vals[sl]);
+                                C = (meta & 0x7fffffff) > x ? 1 : 0;
+                                tf = lts[q];
                             }
+                            for (unsigned chm = __ballot_sync(0xffffffffu, act && meta < 0); chm; chm &= chm - 1) {
+                                const int b = __ffs(chm) - 1;
+                                const int32_t fc = __shfl_sync(0xffffffffu, f, b);
+                                const int xc = __shfl_sync(0xffffffffu, x, b), cc = __shfl_sync(0xffffffffu, C, b);
+                                const int64_t tc = __shfl_sync(0xffffffffu, tf, b);
+                                if (lane < nh) {
+                                    const int32_t h = s.hh[lane];
+                                    // f = h, or a changed f < h: its triads belong to f
+                                    if (fc > h) {
+                                        const int xh1 = s.hx[lane];
+                                        const int m = (s.hk[lane] > xh1 ? 1 : 0) | (xc != k1 - xh1 ? 2 : 0) | (cc << 2) |
+                                                      8 | 16;
+                                        ++acc.n_tri;
+                                        if (want_h) {
+                                            const int c = s.tb.cls30[m];
+                                            if (c >= 0) atomicAdd(&hist[c], 1u);
+                                        }
+                                        const int c96 = temporal_class(s.tb, m, T.hts[lane], ts1, tc, h, g1, fc, delta);
+                                        if (c96 >= 0) atomicAdd(&T.th[wid][c96], 1u);
+                                    }
+                                }
+                            }
+                            if (!act || meta < 0) continue;
                             const bool fb = tf < ts1 || (tf == ts1 && f < g1);
                             // places in [lo, hi) of an order: the first not before
                             // (t, id); the first at time >= t; the first at time > t
